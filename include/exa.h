@@ -1,0 +1,161 @@
+/*
+ * exa.h -- C ABI of the GB300 exact Matérn Gaussian log-likelihood library.
+ *
+ * The library evaluates, on one GPU, the log-likelihood of zero-mean Gaussian
+ * data z observed at n two-dimensional locations s_1..s_n (Section I, Eq. 2
+ * with mu = 0):
+ *
+ *     l(theta) = -n/2 log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 z^T Sigma(theta)^-1 z
+ *
+ * where Sigma is the isotropic Matérn covariance of Section I, Eq. 3,
+ *
+ *     Sigma_ij = sigma^2 / (2^(nu-1) Gamma(nu)) (r_ij/beta)^nu K_nu(r_ij/beta),
+ *     r_ij = ||s_i - s_j|| (Euclidean),  Sigma_ii = sigma^2,
+ *
+ * theta = (sigma^2, beta, nu), all > 0.  As Section I states, log|Sigma| and
+ * Sigma^-1 z come from the Cholesky factor Sigma = L L^T, which dominates the
+ * cost (O(n^3) flops, O(n^2) memory).  The mixed-precision form follows the
+ * MP variant of Section II-A (Fig. 1(d)): diagonal tiles stay FP64, off-diagonal
+ * updates run in reduced precision.  The gradient and the batched form are
+ * extensions of the same evaluation (the paper's optimiser, BOBYQA of Section
+ * II-B, needs no derivatives).
+ *
+ * Conventions for every entry point:
+ *   - Pointers prefixed d_ are DEVICE pointers on the context's device; h_
+ *     or unprefixed pointers are HOST pointers.  The caller owns all inputs
+ *     and outputs; the library never frees them.
+ *   - Locations are n x 2 FP64, interleaved (x_0, y_0, x_1, y_1, ...).
+ *     Observations z are n FP64.  Both must be 8-byte aligned.
+ *   - Work is issued on the context's CUDA stream.  Entry points returning a
+ *     host value synchronise that stream before returning; the batched form
+ *     is stream-asynchronous.
+ *   - Every entry point returns an exa_status.  On any error other than
+ *     EXA_ERR_NOT_SPD the outputs are left unspecified; exa_last_error()
+ *     gives a message.  A non-positive or non-finite Cholesky pivot gives
+ *     EXA_ERR_NOT_SPD with loglik = NaN and the 0-based failing row in
+ *     exa_last_pivot() (Section III, Example 2: Sigma is numerically singular
+ *     when two locations nearly coincide).
+ *   - Functions are not thread-safe on one context; use one context per
+ *     host thread.
+ */
+#ifndef EXA_H
+#define EXA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EXA_OK = 0,
+  EXA_ERR_ARG = 1,        /* bad argument: n < 1, null pointer, theta <= 0 or non-finite, bad enum */
+  EXA_ERR_NOT_SPD = 2,    /* Cholesky pivot <= 0 or non-finite: Sigma(theta) not numerically SPD */
+  EXA_ERR_NOMEM = 3,      /* workspace would exceed the context limit, or cudaMalloc failed */
+  EXA_ERR_CUDA = 4,       /* a CUDA runtime or driver call failed */
+  EXA_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (batched scheduler) */
+  EXA_ERR_IR_NOCONV = 6   /* mixed precision: iterative refinement did not reach its tolerance */
+} exa_status;
+
+/* Arithmetic of the Cholesky updates.  In every mode the covariance
+ * generation, the diagonal-tile factorisation (POTRF), the log-determinant
+ * and the triangular solves are FP64.                                      */
+typedef enum {
+  EXA_FP64 = 0,          /* all tiles FP64 (the exact variant, Fig. 1(a)) */
+  EXA_MIXED_TF32X3 = 1,  /* off-diagonal TRSM/GEMM/SYRK products as 3 TF32 tensor-core products, FP32 accumulate */
+  EXA_MIXED_BF16X3 = 2   /* off-diagonal TRSM/GEMM/SYRK products as 3 BF16 tensor-core products, FP32 accumulate */
+} exa_prec;
+
+typedef struct exa_ctx exa_ctx;
+
+/* Detailed result of one evaluation (exa_loglik_ex).                       */
+typedef struct {
+  double loglik;      /* l(theta) */
+  double logdet;      /* log|Sigma| = 2 sum log L_ii */
+  double quad;        /* z^T Sigma^-1 z */
+  double ir_resid;    /* mixed: final ||z - Sigma x||_2 / ||z||_2; FP64: 0 */
+  int32_t ir_iters;   /* mixed: refinement steps taken; FP64: 0 */
+  int32_t tile_nb;    /* tile size used by the factorisation */
+  float ms_gen;       /* device time of the covariance generation (ms) */
+  float ms_chol;      /* device time of the Cholesky factorisation (ms) */
+  float ms_solve;     /* device time of log-det + solve (+ refinement) (ms) */
+  float ms_total;     /* device time of the whole evaluation (ms) */
+} exa_result;
+
+/* Create a context on the current CUDA device.
+ *   cuda_stream      cudaStream_t to issue work on (NULL: the legacy default stream).
+ *   workspace_bytes  upper bound on device memory the context may hold (0: no bound).
+ *   tile_nb          FP64 tile size, a multiple of 64 and <= 128 (0: library default).
+ * Returns EXA_ERR_ARG on a bad tile size, EXA_ERR_CUDA if no device is usable. */
+exa_status exa_ctx_create(exa_ctx** ctx, void* cuda_stream, size_t workspace_bytes, int tile_nb);
+
+/* Free every device buffer the context holds and the context itself.       */
+void exa_ctx_destroy(exa_ctx* ctx);
+
+/* Replace the stream work is issued on.                                    */
+exa_status exa_ctx_set_stream(exa_ctx* ctx, void* cuda_stream);
+
+/* Message describing the last error on this context ("" if none).  The
+ * string is owned by the context and valid until its next call.           */
+const char* exa_last_error(const exa_ctx* ctx);
+
+/* 0-based row of the failing pivot of the last EXA_ERR_NOT_SPD, else -1.   */
+int64_t exa_last_pivot(const exa_ctx* ctx);
+
+/* Device memory currently held by the context, in bytes.                   */
+size_t exa_workspace_bytes(const exa_ctx* ctx);
+
+/* Step a1 alone: write the lower triangle (diagonal included) of the n x n
+ * Matérn covariance Sigma(theta) (Eq. 3) into the caller's column-major
+ * device matrix d_sigma with leading dimension ld >= n: entry (i, j), i >= j,
+ * lands at d_sigma[i + j * ld].  The strict upper triangle is not written.
+ * theta is a host array {sigma^2, beta, nu}.                               */
+exa_status exa_covariance(exa_ctx* ctx, const double* d_locs, int64_t n, const double theta[3], double* d_sigma,
+                          int64_t ld);
+
+/* Step a2 alone: in-place FP64 Cholesky of the caller's column-major SPD
+ * matrix (lower triangle read, factor L written to the lower triangle; the
+ * strict upper triangle is left untouched).  ld >= n.  Returns
+ * EXA_ERR_NOT_SPD on a non-positive or non-finite pivot.                    */
+exa_status exa_potrf(exa_ctx* ctx, double* d_a, int64_t n, int64_t ld);
+
+/* Steps a1-a5: log-likelihood l(theta) (Eq. 2) at host theta {sigma^2, beta, nu}.
+ * *loglik (host) receives l, or NaN with EXA_ERR_NOT_SPD.                  */
+exa_status exa_loglik(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                      exa_prec prec, double* loglik);
+
+/* As exa_loglik, with the log-determinant, the quadratic form, refinement
+ * statistics and per-phase device timings in *out (host).                  */
+exa_status exa_loglik_ex(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                         exa_prec prec, exa_result* out);
+
+/* Log-likelihood and its gradient dl/d(sigma^2, beta, nu), FP64:
+ *   dl/dtheta_k = 1/2 a^T (dSigma/dtheta_k) a - 1/2 tr(Sigma^-1 dSigma/dtheta_k),  a = Sigma^-1 z.
+ * grad (host, 3 doubles).  Only EXA_FP64 is accepted for prec.              */
+exa_status exa_loglik_grad(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                           exa_prec prec, double* loglik, double grad[3]);
+
+/* Batched evaluation of nrep independent replicate fields of uneven sizes.
+ *   h_n       host array of nrep sizes (each >= 1).
+ *   d_locs    host array of nrep DEVICE pointers, replicate r has h_n[r] x 2 locations.
+ *   d_z       host array of nrep DEVICE pointers, h_n[r] observations each.
+ *   d_theta   DEVICE array nrep x 3 (sigma^2, beta, nu per replicate), read at execution time,
+ *             so a captured graph can be replayed with new parameters.
+ *   d_loglik  DEVICE output, nrep values (NaN where the replicate is not SPD).
+ *   d_status  DEVICE output, nrep exa_status codes.
+ * Stream-asynchronous: returns once the work is enqueued.                   */
+exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, const double* const* d_locs,
+                              const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
+                              int32_t* d_status);
+
+/* Exact synthetic realisation (Section III, Example 1, simulate_obs_exact):
+ * d_z = L d_eps with L L^T = Sigma(theta), both n FP64 device vectors.       */
+exa_status exa_simulate(exa_ctx* ctx, const double* d_locs, const double* d_eps, const double theta[3], int64_t n,
+                        exa_prec prec, double* d_z);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXA_H */

@@ -1,0 +1,245 @@
+"""GB300 exact Matérn Gaussian log-likelihood (the ExaGeoStat MLE hot path).
+
+Thin ctypes binding over ``libexa.so`` (declared in ``include/exa.h``): every
+function marshals torch device pointers, host scalars and the current CUDA
+stream into the C ABI of the same name.  All arithmetic runs in the CUDA
+kernels of the library; there is no CPU or PyTorch fallback, and every call
+raises if the library is missing or returns an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "EXA_OK", "EXA_ERR_ARG", "EXA_ERR_NOT_SPD", "EXA_ERR_NOMEM", "EXA_ERR_CUDA", "EXA_ERR_TIMEOUT",
+    "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "ExaError", "Context", "lib",
+    "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
+    "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC",
+]
+
+EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
+EXA_FP64, EXA_MIXED_TF32X3, EXA_MIXED_BF16X3 = 0, 1, 2
+PREC = {"fp64": EXA_FP64, "tf32x3": EXA_MIXED_TF32X3, "bf16x3": EXA_MIXED_BF16X3}
+_STATUS = {0: "EXA_OK", 1: "EXA_ERR_ARG", 2: "EXA_ERR_NOT_SPD", 3: "EXA_ERR_NOMEM", 4: "EXA_ERR_CUDA",
+           5: "EXA_ERR_TIMEOUT", 6: "EXA_ERR_IR_NOCONV"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libexa.so")
+
+
+class ExaError(RuntimeError):
+    def __init__(self, status: int, msg: str, pivot: int = -1):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+        self.pivot = pivot
+
+
+class ExaResult(ctypes.Structure):
+    _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
+                ("ir_resid", ctypes.c_double), ("ir_iters", ctypes.c_int32), ("tile_nb", ctypes.c_int32),
+                ("ms_gen", ctypes.c_float), ("ms_chol", ctypes.c_float), ("ms_solve", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PD = ctypes.POINTER(ctypes.c_double)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libexa.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libexa.so is not built (%s): run paper_1908_06936_gb300.build.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            sig = {
+                "exa_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_size_t, ctypes.c_int]),
+                "exa_ctx_destroy": (None, [_P]),
+                "exa_ctx_set_stream": (ctypes.c_int, [_P, _P]),
+                "exa_last_error": (ctypes.c_char_p, [_P]),
+                "exa_last_pivot": (_I64, [_P]),
+                "exa_workspace_bytes": (ctypes.c_size_t, [_P]),
+                "exa_covariance": (ctypes.c_int, [_P, _P, _I64, _PD, _P, _I64]),
+                "exa_potrf": (ctypes.c_int, [_P, _P, _I64, _I64]),
+                "exa_loglik": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _PD]),
+                "exa_loglik_ex": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, ctypes.POINTER(ExaResult)]),
+                "exa_loglik_grad": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _PD, _PD]),
+                "exa_loglik_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                                      ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P]),
+                "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _theta(theta) -> ctypes.Array:
+    t = [float(v) for v in theta]
+    if len(t) != 3:
+        raise ValueError("theta must have 3 components (sigma^2, beta, nu)")
+    return (ctypes.c_double * 3)(*t)
+
+
+def _dev_ptr(t, name: str, n_expected: int | None = None) -> int:
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n_expected is not None and t.numel() != n_expected:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), n_expected))
+    return t.data_ptr()
+
+
+class Context:
+    """Owns an exa_ctx bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None, workspace_bytes: int = 0, tile_nb: int = 0):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.handle = exa_ctx_create(stream.cuda_stream, workspace_bytes, tile_nb)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            exa_ctx_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def check(self, status: int):
+        if status != EXA_OK:
+            raise ExaError(status, exa_last_error(self.handle), exa_last_pivot(self.handle))
+
+    # convenience wrappers (tensors in, Python values out)
+    def covariance(self, locs, theta, out=None):
+        import torch
+
+        n = locs.shape[0]
+        if out is None:
+            out = torch.zeros((n, n), dtype=torch.float64, device=locs.device)
+        # the library writes column-major (i + j*ld); a row-major torch (n, n) buffer viewed
+        # as column-major is its transpose, so the lower triangle lands in out.T
+        self.check(exa_covariance(self.handle, locs, n, theta, out, n))
+        return out
+
+    def loglik(self, locs, z, theta, prec=EXA_FP64) -> float:
+        return self.loglik_ex(locs, z, theta, prec)["loglik"]
+
+    def loglik_ex(self, locs, z, theta, prec=EXA_FP64) -> dict:
+        r = ExaResult()
+        st = exa_loglik_ex(self.handle, locs, z, theta, locs.shape[0], prec, r)
+        d = r.as_dict()
+        d["status"] = st
+        self.check(st)
+        return d
+
+    def loglik_grad(self, locs, z, theta, prec=EXA_FP64):
+        g = (ctypes.c_double * 3)()
+        l = ctypes.c_double()
+        self.check(exa_loglik_grad(self.handle, locs, z, theta, locs.shape[0], prec, l, g))
+        return l.value, np.array(g[:])
+
+    def simulate(self, locs, eps, theta, prec=EXA_FP64):
+        import torch
+
+        z = torch.empty_like(eps)
+        self.check(exa_simulate(self.handle, locs, eps, theta, locs.shape[0], prec, z))
+        return z
+
+
+# --- C-ABI functions, same names --------------------------------------------------
+
+def exa_ctx_create(cuda_stream: int = 0, workspace_bytes: int = 0, tile_nb: int = 0) -> int:
+    h = _P()
+    st = lib().exa_ctx_create(ctypes.byref(h), _P(cuda_stream or None), int(workspace_bytes), int(tile_nb))
+    if st != EXA_OK:
+        raise ExaError(st, "exa_ctx_create failed")
+    return h.value
+
+
+def exa_ctx_destroy(ctx: int) -> None:
+    lib().exa_ctx_destroy(_P(ctx))
+
+
+def exa_ctx_set_stream(ctx: int, cuda_stream: int) -> int:
+    return lib().exa_ctx_set_stream(_P(ctx), _P(cuda_stream or None))
+
+
+def exa_last_error(ctx: int) -> str:
+    s = lib().exa_last_error(_P(ctx))
+    return s.decode() if s else ""
+
+
+def exa_last_pivot(ctx: int) -> int:
+    return int(lib().exa_last_pivot(_P(ctx)))
+
+
+def exa_workspace_bytes(ctx: int) -> int:
+    return int(lib().exa_workspace_bytes(_P(ctx)))
+
+
+def exa_covariance(ctx: int, locs, n: int, theta, sigma, ld: int) -> int:
+    return lib().exa_covariance(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), n, _theta(theta),
+                                _P(_dev_ptr(sigma, "sigma")), ld)
+
+
+def exa_potrf(ctx: int, a, n: int, ld: int) -> int:
+    return lib().exa_potrf(_P(ctx), _P(_dev_ptr(a, "a")), n, ld)
+
+
+def exa_loglik(ctx: int, locs, z, theta, n: int, prec: int, loglik: ctypes.c_double) -> int:
+    return lib().exa_loglik(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(z, "z", n)), _theta(theta), n,
+                            int(prec), ctypes.byref(loglik))
+
+
+def exa_loglik_ex(ctx: int, locs, z, theta, n: int, prec: int, out: ExaResult) -> int:
+    return lib().exa_loglik_ex(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(z, "z", n)), _theta(theta),
+                               n, int(prec), ctypes.byref(out))
+
+
+def exa_loglik_grad(ctx: int, locs, z, theta, n: int, prec: int, loglik: ctypes.c_double, grad) -> int:
+    return lib().exa_loglik_grad(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(z, "z", n)),
+                                 _theta(theta), n, int(prec), ctypes.byref(loglik), grad)
+
+
+def exa_loglik_batched(ctx: int, nrep: int, ns, locs_list, z_list, theta_dev, prec: int, loglik_dev,
+                       status_dev) -> int:
+    h_n = (_I64 * nrep)(*[int(v) for v in ns])
+    pl = (_P * nrep)(*[_dev_ptr(t, "locs[%d]" % i, 2 * int(ns[i])) for i, t in enumerate(locs_list)])
+    pz = (_P * nrep)(*[_dev_ptr(t, "z[%d]" % i, int(ns[i])) for i, t in enumerate(z_list)])
+    return lib().exa_loglik_batched(_P(ctx), nrep, h_n, pl, pz, _P(_dev_ptr(theta_dev, "theta", 3 * nrep)),
+                                    int(prec), _P(_dev_ptr(loglik_dev, "loglik", nrep)),
+                                    _P(status_dev.data_ptr()))
+
+
+def exa_simulate(ctx: int, locs, eps, theta, n: int, prec: int, z) -> int:
+    return lib().exa_simulate(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(eps, "eps", n)),
+                              _theta(theta), n, int(prec), _P(_dev_ptr(z, "z", n)))

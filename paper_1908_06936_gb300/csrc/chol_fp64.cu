@@ -1,0 +1,271 @@
+// Step a2 (FP64): right-looking tiled Cholesky, Sigma = L L^T (Section I;
+// the tile decomposition of Section II-A, Fig. 1(a)).
+//
+// For tile column k (k0 = k nb):
+//   potrf_diag  : L_kk = chol(A_kk) and W_k = L_kk^-1, in shared memory (one CTA).
+//   trsm_panel  : L_ik = A_ik L_kk^-T = A_ik W_k^T for all rows below (DMMA GEMM),
+//                 written in place and to a row-major panel copy P.
+//   syrk_update : A_ij -= L_ik L_jk^T over the trailing lower triangle (DMMA GEMM).
+// The matrix is column-major with leading dimension ld, padded to a multiple
+// of nb with an identity block, so every tile is full.
+//
+// FP64 tensor-core MMA on sm_103a is the warp-level mma.sync .f64 (DMMA): the
+// chip's FP64 rate (~1.05 TFLOP/s measured, all DMMA shapes alike) is so low
+// that a shared-memory-staged m8n8k4 kernel keeps the pipe busy.
+#include <math.h>
+
+#include "exa_internal.cuh"
+
+namespace exa {
+
+// D (8x8) += A (8x4, row) * B (4x8, col).  Fragments (g = lane/4, q = lane%4):
+//   a = A[g][q], b = B[q][g], d = {D[g][2q], D[g][2q+1]}.
+__device__ __forceinline__ void dmma_884(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ bool failed(const DevStatus* st) { return *(volatile const int32_t*)&st->info != 0; }
+
+// ---------------------------------------------------------------------------
+// potrf_diag: one CTA of 256 threads, the nb x nb diagonal tile in shared memory
+// (row stride nb + 1).  Unblocked right-looking Cholesky, then in-place
+// triangular inversion (column by column from the last), W written row-major.
+// logdet_part[k] = sum_i log L_ii over the tile, summed in row order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a, int64_t ld, int64_t k0, int nb,
+                                                         double* __restrict__ w_out, double* __restrict__ logdet_part,
+                                                         DevStatus* st) {
+  extern __shared__ double sm[];
+  const int sd = nb + 1;
+  double* S = sm;               // nb x sd
+  double* tmp = sm + nb * sd;   // nb
+  const int tid = threadIdx.x;
+  const int k = (int)(k0 / nb);
+  if (failed(st)) return;
+  double* A = a + k0 + k0 * ld;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, j = idx / nb;
+    S[i * sd + j] = (i >= j) ? A[i + (int64_t)j * ld] : 0.0;
+  }
+  __syncthreads();
+  int bad = -1;
+  for (int j = 0; j < nb; ++j) {
+    const double d = S[j * sd + j];
+    if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
+      bad = j;
+      break;
+    }
+    const double lj = sqrt(d);
+    const double inv = 1.0 / lj;
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i * sd + j] *= inv;
+    __syncthreads();
+    if (tid == 0) S[j * sd + j] = lj;
+    const int m = nb - j - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = j + 1 + idx % m, l = j + 1 + idx / m;
+      if (l <= i) S[i * sd + l] = fma(-S[i * sd + j], S[l * sd + j], S[i * sd + l]);
+    }
+    __syncthreads();
+  }
+  if (bad >= 0) {
+    if (tid == 0) {
+      atomicMin(&st->pivot, (long long)(k0 + bad));
+      atomicExch(&st->info, 1);
+    }
+    return;
+  }
+  // write L back (lower triangle of the tile)
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, j = idx / nb;
+    if (i >= j) A[i + (int64_t)j * ld] = S[i * sd + j];
+  }
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += log(S[i * sd + i]);
+    logdet_part[k] = s;
+  }
+  __syncthreads();
+  // in-place inversion: column j of W from the already-inverted trailing block
+  //   W_jj = 1 / L_jj,  W_ij = -W_jj * sum_{l=j+1..i} W_il L_lj  (i > j)
+  for (int j = nb - 1; j >= 0; --j) {
+    const double wjj = 1.0 / S[j * sd + j];  // read before anyone overwrites it below
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
+      double t = 0.0;
+      for (int l = j + 1; l <= i; ++l) t = fma(S[i * sd + l], S[l * sd + j], t);
+      tmp[i] = t;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i * sd + j] = -tmp[i] * wjj;
+    if (tid == 0) S[j * sd + j] = wjj;
+    __syncthreads();
+  }
+  double* W = w_out + (int64_t)k * nb * nb;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx % nb;
+    W[idx] = (c <= r) ? S[r * sd + c] : 0.0;
+  }
+}
+
+cudaError_t launch_potrf_diag(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, double* w_out,
+                              double* logdet_part, DevStatus* st) {
+  const size_t smem = (size_t)(nb * (nb + 1) + nb) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((128 * 129 + 128) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  potrf_diag_kernel<<<1, 256, smem, s>>>(a, ld, k0, nb, w_out, logdet_part, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// trsm_panel: rows [k0+nb, k0+nb+m), one CTA per 32-row strip, nb/32 warps,
+// warp w owns output columns [32w, 32w+32).  out = A_strip * W^T with K = nb,
+// staged through shared memory in K-chunks of 32 (row stride 36 doubles).
+// ---------------------------------------------------------------------------
+constexpr int kKC = 32;      // K chunk
+constexpr int kSS = kKC + 4; // padded row stride (doubles) of staged chunks
+
+__global__ void __launch_bounds__(128) trsm_panel_kernel(double* __restrict__ a, int64_t ld, int64_t k0, int nb,
+                                                         const double* __restrict__ w, double* __restrict__ p,
+                                                         const DevStatus* st) {
+  __shared__ double As[32 * kSS];
+  __shared__ double Ws[128 * kSS];
+  if (failed(st)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int64_t r0 = k0 + nb + (int64_t)blockIdx.x * 32;
+  const double* Wk = w + (int64_t)(k0 / nb) * nb * nb;
+  double acc[4][4][2];
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+  for (int t0 = 0; t0 < nb; t0 += kKC) {
+    for (int idx = tid; idx < 32 * kKC; idx += blockDim.x) {
+      const int r = idx & 31, t = idx >> 5;
+      As[r * kSS + t] = a[(r0 + r) + (k0 + t0 + t) * ld];
+    }
+    for (int idx = tid; idx < nb * kKC; idx += blockDim.x) {
+      const int c = idx / kKC, t = idx % kKC;
+      Ws[c * kSS + t] = Wk[(int64_t)c * nb + t0 + t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKC; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) af[mi] = As[(mi * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) bf[ni] = Ws[(warp * 32 + ni * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) dmma_884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+  // every read of this strip is done: write L_ik in place and to P (row-major, nb wide)
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t row = r0 + mi * 8 + g;
+        const int col = warp * 32 + ni * 8 + 2 * q + e;
+        const double v = acc[mi][ni][e];
+        a[row + (k0 + col) * ld] = v;
+        p[(row - (k0 + nb)) * nb + col] = v;
+      }
+}
+
+cudaError_t launch_trsm_panel(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, int64_t m,
+                              const double* w, double* p, const DevStatus* st) {
+  if (m <= 0) return cudaSuccess;
+  trsm_panel_kernel<<<(unsigned)(m / 32), nb, 0, s>>>(a, ld, k0, nb, w, p, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// syrk_update: trailing matrix rows/cols [r0, r0+m), m a multiple of 64.  One
+// CTA per 64 x 64 lower tile (ti >= tj), 4 warps in a 2 x 2 arrangement of
+// 32 x 32 warp tiles:  C -= P_i P_j^T with K = nb.  Diagonal tiles store only
+// their lower triangle.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tri_decode_u(long long b, int& ti, int& tj) {
+  long long t = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while (t * (t + 1) / 2 > b) --t;
+  while ((t + 1) * (t + 2) / 2 <= b) ++t;
+  ti = (int)t;
+  tj = (int)(b - t * (t + 1) / 2);
+}
+
+__global__ void __launch_bounds__(128) syrk_update_kernel(double* __restrict__ a, int64_t ld, int64_t r0, int nb,
+                                                          const double* __restrict__ p, const DevStatus* st) {
+  __shared__ double Pi[64 * kSS];
+  __shared__ double Pj[64 * kSS];
+  if (failed(st)) return;
+  int ti, tj;
+  tri_decode_u(blockIdx.x, ti, tj);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const double* pi = p + (int64_t)ti * 64 * nb;
+  const double* pj = p + (int64_t)tj * 64 * nb;
+  double acc[4][4][2];
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+  for (int t0 = 0; t0 < nb; t0 += kKC) {
+    for (int idx = tid; idx < 64 * kKC; idx += blockDim.x) {
+      const int r = idx / kKC, t = idx % kKC;
+      Pi[r * kSS + t] = pi[(int64_t)r * nb + t0 + t];
+      Pj[r * kSS + t] = pj[(int64_t)r * nb + t0 + t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKC; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) af[mi] = Pi[(wm * 32 + mi * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) bf[ni] = Pj[(wn * 32 + ni * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) dmma_884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+  const bool diag = (ti == tj);
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int li = wm * 32 + mi * 8 + g;
+        const int lj = wn * 32 + ni * 8 + 2 * q + e;
+        if (diag && lj > li) continue;
+        const int64_t row = r0 + (int64_t)ti * 64 + li;
+        const int64_t col = r0 + (int64_t)tj * 64 + lj;
+        double* c = a + row + col * ld;
+        *c -= acc[mi][ni][e];
+      }
+}
+
+cudaError_t launch_syrk_update(cudaStream_t s, double* a, int64_t ld, int64_t r0, int64_t m, int nb,
+                               const double* p, const DevStatus* st) {
+  if (m <= 0) return cudaSuccess;
+  const long long t = m / 64;
+  syrk_update_kernel<<<(unsigned)(t * (t + 1) / 2), 128, 0, s>>>(a, ld, r0, nb, p, st);
+  return cudaGetLastError();
+}
+
+}  // namespace exa

@@ -1,0 +1,68 @@
+// The opaque exa_ctx and the host-side helpers shared by the driver files.
+#pragma once
+
+#include <stddef.h>
+
+#include "exa_internal.cuh"
+
+namespace exa {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+constexpr int kNumEvents = 8;
+constexpr int kRedPartials = 512;  // partial sums of one two-stage reduction
+
+inline int64_t kPartialDoubles(int64_t npad, int nb) { return 2 * kRedPartials + (npad / 1024 + 2) * (int64_t)nb; }
+
+}  // namespace exa
+
+struct exa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t ws_limit = 0;   // 0: unbounded
+  size_t held_bytes = 0;
+  int tile_nb = 128;     // FP64 tile
+  int64_t last_pivot = -1;
+  char err[512];
+  // workspace
+  exa::DevBuf mat;          // padded n x n FP64 matrix (column-major, ld = npad)
+  exa::DevBuf w_all;        // inverted diagonal tiles, T x nb x nb
+  exa::DevBuf panel;        // row-major panel copy, npad x nb
+  exa::DevBuf logdet_part;  // per-tile log-det sums
+  exa::DevBuf vec;          // n-vectors
+  exa::DevBuf partial;      // reduction partials
+  // mixed precision
+  exa::DevBuf mx_sigma;     // FP64 copy of Sigma for the refinement residual
+  exa::DevBuf mx_split;     // split-precision panel operands
+  exa::DevBuf mx_vec;       // refinement vectors
+  // gradient
+  exa::DevBuf gr_part;      // per-block gradient partials
+  // batched
+  exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work;
+  // status and small results
+  exa::DevStatus* d_status = nullptr;
+  exa::DevStatus* h_status = nullptr;  // pinned
+  double* d_scalars = nullptr;
+  double* h_scalars = nullptr;          // pinned
+  cudaEvent_t ev[exa::kNumEvents] = {};
+};
+
+namespace exa {
+
+exa_status set_err(exa_ctx* c, exa_status st, const char* fmt, ...);
+exa_status cuda_err(exa_ctx* c, cudaError_t e, const char* what);
+exa_status ensure(exa_ctx* c, DevBuf& b, size_t bytes, const char* name);
+exa_status check_theta(exa_ctx* c, const double theta[3]);
+exa_status reset_status(exa_ctx* c);
+exa_status read_status(exa_ctx* c);
+exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb);
+exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                       exa_result* out, double** keep_y);
+exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                        exa_prec prec, exa_result* out);
+void release_extra(exa_ctx* c);
+
+}  // namespace exa

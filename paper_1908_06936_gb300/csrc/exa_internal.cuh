@@ -1,0 +1,97 @@
+// Internal declarations shared by the CUDA translation units of libexa.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/exa.h"
+
+namespace exa {
+
+// ---------------------------------------------------------------------------
+// Matérn generation parameters (one per theta), computed on the host.
+// Eq. 3 is evaluated as  Sigma = sigma^2 * exp(logc + nu ln x) * K_nu(x),
+// logc = (1 - nu) ln 2 - ln Gamma(nu),  x = r / beta.
+// K_nu is reached from K_mu, K_{mu+1} (mu = nu - N, N = round(nu), |mu| <= 1/2)
+// by the forward recurrence K_{a+1} = K_{a-1} + (2a/x) K_a (DLMF 10.29.1).
+// K_mu, K_{mu+1} come from
+//   x <= 2: Temme's power series (N. M. Temme, J. Comput. Phys. 19, 1975),
+//   x >  2: the three-term recurrence of z_k = U(mu + 1/2 + k, 2 mu + 1, 2x)
+//           (DLMF 13.3.7) run backward from depth D(x) (Miller's algorithm),
+//           normalised by sum_k C_k z_k = (2x)^(-mu-1/2) (the identity behind
+//           the Thompson-Barnett / Steed CF2 method), with
+//           K_mu(x) = sqrt(pi) (2x)^mu e^-x z_0 (DLMF 13.18.9).
+// Per-theta constant tables remove every division from the inner loops.
+// ---------------------------------------------------------------------------
+constexpr int kTemmeTerms = 40;   // series terms kept in the tables
+constexpr int kMillerMax = 96;    // deepest backward recurrence (x just above 2)
+
+struct MaternParams {
+  double sigma2, beta, nu;
+  double logc;       // (1 - nu) ln 2 - lgamma(nu)
+  double mu;         // nu - N, in [-1/2, 1/2]
+  int N;             // round(nu)
+  int pad_;
+  // Temme series at order mu
+  double mupi_sin;   // mu pi / sin(mu pi)  (1 at mu = 0)
+  double gam1;       // Gamma_1(mu) = (1/Gamma(1-mu) - 1/Gamma(1+mu)) / (2 mu)
+  double gam2;       // Gamma_2(mu) = (1/Gamma(1-mu) + 1/Gamma(1+mu)) / 2
+  double gp;         // Gamma(1 + mu)
+  double gm;         // Gamma(1 - mu)
+  double t_k2[kTemmeTerms + 1];  // 1 / (k^2 - mu^2)
+  double t_km[kTemmeTerms + 1];  // 1 / (k - mu)
+  double t_kp[kTemmeTerms + 1];  // 1 / (k + mu)
+  // backward recurrence at order mu
+  double m_a[kMillerMax + 2];    // (k + 1/2)^2 - mu^2
+  double m_c[kMillerMax + 2];    // C_k,  C_0 = 1,  C_{k+1} = C_k ((k + 1/2)^2 - mu^2) / (k + 1)
+};
+
+// Host: fill the parameter block for theta (defined in matern.cu).
+void matern_params(const double theta[3], MaternParams* p);
+
+// Device status block (lives in device memory, one per context).
+struct DevStatus {
+  int32_t info;        // 0 ok; 1 not SPD
+  int32_t pad;
+  long long pivot;     // smallest failing global row (atomicMin), or LLONG_MAX
+  int32_t timeout;     // bounded wait expired
+  int32_t timeout_where;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (all asynchronous on `s`).
+// ---------------------------------------------------------------------------
+
+// Lower triangle (diagonal included) of Sigma for rows/cols < n into column-major
+// `a` (leading dim ld).  Rows/cols in [n, npad) are filled as the identity so
+// that a padded matrix factors as diag(L, I).
+cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
+                              double* a, int64_t ld);
+
+// FP64 tiled Cholesky steps (tile nb <= 128, multiple of 64; n multiple of nb).
+cudaError_t launch_potrf_diag(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, double* w_out,
+                              double* logdet_part, DevStatus* st);
+cudaError_t launch_trsm_panel(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, int64_t m,
+                              const double* w, double* p, const DevStatus* st);
+cudaError_t launch_syrk_update(cudaStream_t s, double* a, int64_t ld, int64_t r0, int64_t m, int nb,
+                               const double* p, const DevStatus* st);
+
+// Blocked forward solve y = L^-1 z using the stored inverted diagonal tiles
+// w_all (T tiles of nb x nb, row-major).  z is overwritten by y (length npad).
+cudaError_t launch_trsv_fwd_step(cudaStream_t s, const double* a, int64_t ld, int64_t npad, int nb, int k,
+                                 const double* w_all, double* y, double* tmp, const DevStatus* st);
+// Backward solve a = L^-T y (in place in y).
+cudaError_t launch_trsv_bwd_step(cudaStream_t s, const double* a, int64_t ld, int64_t npad, int nb, int k,
+                                 const double* w_all, double* y, double* tmp, const DevStatus* st);
+
+// Deterministic reductions: out[0] = sum(v[i]^2) ; out[0] = sum(v[i]) over n values.
+cudaError_t launch_sumsq(cudaStream_t s, const double* v, int64_t n, double* partial, double* out);
+cudaError_t launch_sum(cudaStream_t s, const double* v, int64_t n, double* partial, double* out);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace exa

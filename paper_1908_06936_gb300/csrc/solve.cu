@@ -1,0 +1,174 @@
+// Steps a3-a4: log-determinant and the triangular solve for the quadratic
+// form (Section I: |Sigma| and Sigma^-1 Z from the Cholesky factor),
+//   log|Sigma| = 2 sum_i log L_ii,   y = L^-1 z,   z^T Sigma^-1 z = y^T y.
+// Both are HBM-bound: the solve streams the lower triangle once.  All
+// reductions run in a fixed order, so FP64 results are bitwise reproducible.
+#include "exa_internal.cuh"
+
+namespace exa {
+
+__device__ __forceinline__ bool failed_s(const DevStatus* st) { return *(volatile const int32_t*)&st->info != 0; }
+
+// Forward block step k (right-looking):
+//   y_k = W_k z_k                        (W_k = L_kk^-1, row-major)
+//   z_r -= sum_t L[r][k0+t] y_k[t]       for every row r >= k0 + nb
+// Every block recomputes y_k from the (not yet overwritten) z_k; block 0 stores it.
+__global__ void __launch_bounds__(256) trsv_fwd_kernel(const double* __restrict__ a, int64_t ld, int64_t npad, int nb,
+                                                       int k, const double* __restrict__ w_all, double* __restrict__ z,
+                                                       double* __restrict__ y, const DevStatus* st) {
+  __shared__ double zk[128];
+  __shared__ double yk[128];
+  if (failed_s(st)) return;
+  const int tid = threadIdx.x;
+  const int64_t k0 = (int64_t)k * nb;
+  if (tid < nb) zk[tid] = z[k0 + tid];
+  __syncthreads();
+  const double* W = w_all + (int64_t)k * nb * nb;
+  if (tid < nb) {
+    double s = 0.0;
+    for (int t = 0; t <= tid; ++t) s = fma(W[(int64_t)tid * nb + t], zk[t], s);
+    yk[tid] = s;
+    if (blockIdx.x == 0) y[k0 + tid] = s;
+  }
+  __syncthreads();
+  const int64_t r = k0 + nb + (int64_t)blockIdx.x * blockDim.x + tid;
+  if (r < npad) {
+    double s = z[r];
+    const double* col = a + r + k0 * ld;
+    for (int t = 0; t < nb; ++t) s = fma(-col[(int64_t)t * ld], yk[t], s);
+    z[r] = s;
+  }
+}
+
+cudaError_t launch_trsv_fwd_step(cudaStream_t s, const double* a, int64_t ld, int64_t npad, int nb, int k,
+                                 const double* w_all, double* y, double* tmp, const DevStatus* st) {
+  // tmp holds the working right-hand side z (updated in place), y receives L^-1 z
+  const int64_t m = npad - (int64_t)(k + 1) * nb;
+  const unsigned blocks = (unsigned)(m > 0 ? (m + 255) / 256 : 1);
+  trsv_fwd_kernel<<<blocks, 256, 0, s>>>(a, ld, npad, nb, k, w_all, tmp, y, st);
+  return cudaGetLastError();
+}
+
+// Backward block step k (left-looking), a = L^-T y:
+//   s_t = sum_{r >= k0+nb} L[r][k0+t] a_r   (t < nb; partial sums per block)
+//   a_k = W_k^T (y_k - s)
+// Two kernels: column-panel reduction into fixed per-block partials, then one
+// block that finishes the sum in order and applies W_k^T.
+constexpr int kBwdRows = 1024;  // rows per partial
+
+__global__ void __launch_bounds__(128) trsv_bwd_partial_kernel(const double* __restrict__ a, int64_t ld, int64_t npad,
+                                                               int nb, int k, const double* __restrict__ y,
+                                                               double* __restrict__ part, const DevStatus* st) {
+  // block b: rows [k0+nb + b*kBwdRows, ...), thread t: column t of the panel
+  if (failed_s(st)) return;
+  const int t = threadIdx.x;
+  if (t >= nb) return;
+  const int64_t k0 = (int64_t)k * nb;
+  const int64_t rs = k0 + nb + (int64_t)blockIdx.x * kBwdRows;
+  int64_t re = rs + kBwdRows;
+  if (re > npad) re = npad;
+  const double* col = a + (k0 + t) * ld;
+  double s = 0.0;
+  for (int64_t r = rs; r < re; ++r) s = fma(col[r], y[r], s);
+  part[(int64_t)blockIdx.x * nb + t] = s;
+}
+
+__global__ void __launch_bounds__(128) trsv_bwd_finish_kernel(int64_t npad, int nb, int k, int nparts,
+                                                              const double* __restrict__ w_all,
+                                                              const double* __restrict__ part, double* __restrict__ y,
+                                                              const DevStatus* st) {
+  __shared__ double v[128];
+  if (failed_s(st)) return;
+  const int t = threadIdx.x;
+  const int64_t k0 = (int64_t)k * nb;
+  if (t < nb) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * nb + t];
+    v[t] = y[k0 + t] - s;
+  }
+  __syncthreads();
+  const double* W = w_all + (int64_t)k * nb * nb;
+  if (t < nb) {
+    // (W^T v)_t = sum_{c >= t} W[c][t] v_c
+    double s = 0.0;
+    for (int c = t; c < nb; ++c) s = fma(W[(int64_t)c * nb + t], v[c], s);
+    y[k0 + t] = s;
+  }
+}
+
+cudaError_t launch_trsv_bwd_step(cudaStream_t s, const double* a, int64_t ld, int64_t npad, int nb, int k,
+                                 const double* w_all, double* y, double* tmp, const DevStatus* st) {
+  const int64_t m = npad - (int64_t)(k + 1) * nb;
+  int nparts = 0;
+  if (m > 0) {
+    nparts = (int)((m + kBwdRows - 1) / kBwdRows);
+    trsv_bwd_partial_kernel<<<nparts, 128, 0, s>>>(a, ld, npad, nb, k, y, tmp, st);
+  }
+  trsv_bwd_finish_kernel<<<1, 128, 0, s>>>(npad, nb, k, nparts, w_all, tmp, y, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic two-stage reductions.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 512;
+
+__device__ __forceinline__ double block_reduce(double v, double* sh) {
+  const int tid = threadIdx.x;
+  sh[tid] = v;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+template <bool SQ>
+__global__ void __launch_bounds__(kRedThreads) reduce_stage1(const double* __restrict__ v, int64_t n, int64_t chunk,
+                                                             double* __restrict__ partial) {
+  __shared__ double sh[kRedThreads];
+  const int64_t start = (int64_t)blockIdx.x * chunk;
+  int64_t end = start + chunk;
+  if (end > n) end = n;
+  double s = 0.0;
+  for (int64_t i = start + threadIdx.x; i < end; i += kRedThreads) {
+    const double x = v[i];
+    s += SQ ? x * x : x;
+  }
+  const double r = block_reduce(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_stage2(const double* __restrict__ partial, int nb,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += kRedThreads) s += partial[i];
+  const double r = block_reduce(s, sh);
+  if (threadIdx.x == 0) *out = r;
+}
+
+template <bool SQ>
+static cudaError_t launch_reduce(cudaStream_t s, const double* v, int64_t n, double* partial, double* out) {
+  int64_t chunk = 4096;
+  int64_t blocks = (n + chunk - 1) / chunk;
+  if (blocks > kRedMaxBlocks) {
+    chunk = (n + kRedMaxBlocks - 1) / kRedMaxBlocks;
+    blocks = (n + chunk - 1) / chunk;
+  }
+  if (blocks < 1) blocks = 1;
+  reduce_stage1<SQ><<<(unsigned)blocks, kRedThreads, 0, s>>>(v, n, chunk, partial);
+  reduce_stage2<<<1, kRedThreads, 0, s>>>(partial, (int)blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(cudaStream_t s, const double* v, int64_t n, double* partial, double* out) {
+  return launch_reduce<true>(s, v, n, partial, out);
+}
+cudaError_t launch_sum(cudaStream_t s, const double* v, int64_t n, double* partial, double* out) {
+  return launch_reduce<false>(s, v, n, partial, out);
+}
+
+}  // namespace exa

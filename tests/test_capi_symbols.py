@@ -1,0 +1,38 @@
+"""The C-ABI library builds, loads and exports every function include/exa.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+from paper_1908_06936_gb300 import build as exa_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(exa_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["exa_loglik", "exa_loglik_grad", "exa_loglik_batched", "exa_ctx_create", "exa_ctx_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = exa_build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol():
+    import paper_1908_06936_gb300 as exa
+
+    missing = [n for n in declared_functions() if not callable(getattr(exa, n, None))]
+    assert not missing, missing
