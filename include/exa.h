@@ -149,6 +149,19 @@ exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, co
                               const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
                               int32_t* d_status);
 
+/* Products of step a2 on their own (component check of the tensor-core
+ * contractions used by the mixed-precision factorisation):
+ *   C = A B^T (store != 0)  or  C -= A B^T (store == 0)
+ * A is m x k and B is n x k, row-major FP64 device matrices; C is a column-
+ * major FP64 device matrix with leading dimension ldc >= m.  kind selects
+ * the arithmetic: EXA_GEMM_T3 (three TF32 products, FP32 accumulation) or
+ * EXA_GEMM_OZ (five exact 7-bit BF16 digit slices per row, exact FP32
+ * accumulation, FP64 combination).  Shapes: m % 128 == 0, k % 64 == 0,
+ * n % 128 == 0 (T3) or n % 32 == 0 (OZ), k <= 512, and k <= 256 for OZ.  */
+typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1 } exa_gemm_kind;
+exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
+                           const double* d_b, double* d_c, int64_t ldc, int store);
+
 /* Exact synthetic realisation (Section III, Example 1, simulate_obs_exact):
  * d_z = L d_eps with L L^T = Sigma(theta), both n FP64 device vectors.       */
 exa_status exa_simulate(exa_ctx* ctx, const double* d_locs, const double* d_eps, const double theta[3], int64_t n,

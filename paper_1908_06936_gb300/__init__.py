@@ -19,11 +19,12 @@ __all__ = [
     "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
-    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
 EXA_FP64, EXA_MIXED_TF32X3, EXA_MIXED_BF16X3 = 0, 1, 2
+EXA_GEMM_T3, EXA_GEMM_OZ = 0, 1
 PREC = {"fp64": EXA_FP64, "tf32x3": EXA_MIXED_TF32X3, "bf16x3": EXA_MIXED_BF16X3}
 _STATUS = {0: "EXA_OK", 1: "EXA_ERR_ARG", 2: "EXA_ERR_NOT_SPD", 3: "EXA_ERR_NOMEM", 4: "EXA_ERR_CUDA",
            5: "EXA_ERR_TIMEOUT", 6: "EXA_ERR_IR_NOCONV"}
@@ -80,6 +81,8 @@ def lib() -> ctypes.CDLL:
                 "exa_loglik_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                                       ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P]),
                 "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
+                "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
+                                                   ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -243,3 +246,8 @@ def exa_loglik_batched(ctx: int, nrep: int, ns, locs_list, z_list, theta_dev, pr
 def exa_simulate(ctx: int, locs, eps, theta, n: int, prec: int, z) -> int:
     return lib().exa_simulate(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(eps, "eps", n)),
                               _theta(theta), n, int(prec), _P(_dev_ptr(z, "z", n)))
+
+
+def exa_gemm_update(ctx: int, kind: int, m: int, n: int, k: int, a, b, c, ldc: int, store: int) -> int:
+    return lib().exa_gemm_update(_P(ctx), int(kind), m, n, k, _P(_dev_ptr(a, "a", m * k)), _P(_dev_ptr(b, "b", n * k)),
+                                 _P(_dev_ptr(c, "c")), ldc, int(store))

@@ -4,6 +4,7 @@
 #include <stddef.h>
 
 #include "exa_internal.cuh"
+#include "gemm_tc.cuh"
 
 namespace exa {
 
@@ -36,7 +37,9 @@ struct exa_ctx {
   exa::DevBuf partial;      // reduction partials
   // mixed precision
   exa::DevBuf mx_sigma;     // FP64 copy of Sigma for the refinement residual
-  exa::DevBuf mx_split;     // split-precision panel operands
+  exa::DevBuf mx_split;     // split-precision panel operands (A role)
+  exa::DevBuf mx_split_b;   // split-precision operands (B role: inverse diagonal block / test B)
+  exa::SplitOperand sp_a, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
   // gradient
   exa::DevBuf gr_part;      // per-block gradient partials
@@ -64,5 +67,7 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
 exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                         exa_prec prec, exa_result* out);
 void release_extra(exa_ctx* c);
+// Lay out a split operand of `rows` x K in `buf` (T3 planes and/or OZ digits) and build its TMA maps.
+exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz);
 
 }  // namespace exa

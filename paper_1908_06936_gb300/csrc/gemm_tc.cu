@@ -1,0 +1,634 @@
+// Step a2 (mixed precision): the Cholesky's dense contractions on the fifth-
+// generation tensor cores (tcgen05.mma, TMEM accumulators, TMA-staged tiles).
+//
+// The MP variant of Section II-A (Fig. 1(d)) keeps the tiles next to the
+// diagonal in double precision and lowers the precision of the rest.  Here
+// every operand is stored in FP64 and each product C -= A B^T runs as one of:
+//
+//  * T3 (off-band tiles): A = A_hi + A_lo with A_hi = tf32(A), A_lo = tf32(A - A_hi)
+//    (both rounded to nearest), C -= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
+//    accumulated in FP32 in TMEM (~22 significant bits per product).
+//  * OZ (band tiles, where the Schur complement cancels most): each row is scaled
+//    by a power of two 2^e_r so that |a| <= 1 and cut into S = 5 signed 7-bit
+//    integer digits held exactly in BF16, a = 2^e_r sum_s d_s 2^{-7(s+1)}.  Digit
+//    products are integers of at most 14 bits; with K <= 256 every partial sum
+//    of one slice-sum group g = s + t stays below 2^24, so FP32 accumulation in
+//    TMEM is exact.  The 15 products with g <= 4 go to five accumulators that
+//    the epilogue combines in FP64 (error ~2^-35 of the row maxima).
+//
+// Both kernels are persistent and warp-specialised: warp 0 issues TMA loads,
+// warp 1 owns TMEM and issues tcgen05.mma from one thread, warps 2-5 drain the
+// accumulators into the FP64 matrix.  Every wait is bounded; on time-out the
+// CTA records EXA_ERR_TIMEOUT, drains its in-flight copies, frees TMEM and exits.
+#include <cuda.h>
+#include <math.h>
+
+#include "ctx.cuh"
+#include "gemm_tc.cuh"
+#include "tc_common.cuh"
+
+namespace exa {
+
+using namespace tc;
+
+__device__ __forceinline__ void tile_tri_decode(long long b, int& ti, int& tj) {
+  long long t = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while (t * (t + 1) / 2 > b) --t;
+  while ((t + 1) * (t + 2) / 2 <= b) ++t;
+  ti = (int)t;
+  tj = (int)(b - t * (t + 1) / 2);
+}
+
+// Output-tile enumeration shared by all roles of a CTA.  Returns false if the
+// tile is to be skipped.  (bi, bj) are tile indices in units of (TM, TN).
+template <int TM, int TN>
+__device__ __forceinline__ bool decode_tile(const GemmArgs& g, long long t, int& bi, int& bj) {
+  if (g.enum_mode == kEnumFull) {
+    bi = (int)(t / g.nt);
+    bj = (int)(t % g.nt);
+    return true;
+  }
+  if (g.enum_mode == kEnumLowerOffBand) {  // TM == TN == 128, band measured in 256-wide tiles
+    tile_tri_decode(t, bi, bj);
+    return (bi / 2 - bj / 2) > g.band;
+  }
+  // kEnumBand: pairs (I, J) of 256-wide tiles with 0 <= I - J <= band, each split in
+  // (256/TM) x (256/TN) sub-tiles
+  constexpr int SI = 256 / TM, SJ = 256 / TN;
+  const long long pair = t / (SI * SJ);
+  const int sub = (int)(t % (SI * SJ));
+  const int b = g.band;
+  const long long head = (long long)b * (b + 1) / 2;
+  int I, J;
+  if (pair < head) {
+    tile_tri_decode(pair, I, J);
+  } else {
+    I = b + (int)((pair - head) / (b + 1));
+    J = I - b + (int)((pair - head) % (b + 1));
+  }
+  bi = I * SI + sub / SJ;
+  bj = J * SJ + sub % SJ;
+  // skip sub-tiles strictly above the diagonal
+  return (long long)bj * TN <= (long long)bi * TM + TM - 1;
+}
+
+__device__ __forceinline__ void record_timeout(DevStatus* st, int site) {
+  if (atomicExch(&st->timeout, 1) == 0) st->timeout_where = site;
+}
+
+// ===========================================================================
+// T3 kernel: tile 128 x 128, K chunks of 32 FP32 (TF32) values, 3 stages.
+// ===========================================================================
+namespace t3 {
+constexpr int TM = 128, TN = 128, KC = 32, STAGES = 3;
+constexpr int OP_BYTES = TM * KC * 4;           // 16 KB per operand tile
+constexpr int STAGE_BYTES = 4 * OP_BYTES;       // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t IDESC = idesc(kFmtTF32, TM, TN);
+constexpr int TMEM_COLS = 256;                  // 2 accumulator buffers x 128 columns
+}  // namespace t3
+
+__global__ void __launch_bounds__(192, 1)
+    gemm_t3_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                   const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                   const __grid_constant__ GemmArgs g) {
+  using namespace t3;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accfull = empty + STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int kchunks = g.K / KC;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    prefetch_tmap(&tA_hi);
+    prefetch_tmap(&tA_lo);
+    prefetch_tmap(&tB_hi);
+    prefetch_tmap(&tB_lo);
+    int stage = 0;
+    uint32_t phase = 0;
+    int last_par[STAGES];
+    for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + bj * TN;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 11);
+          break;
+        }
+        uint8_t* sb = smem + stage * STAGE_BYTES;
+        mbar_expect_tx(&full[stage], STAGE_BYTES);
+        tma_load_2d(sb, &tA_hi, &full[stage], kc * KC, ya);
+        tma_load_2d(sb + OP_BYTES, &tA_lo, &full[stage], kc * KC, ya);
+        tma_load_2d(sb + 2 * OP_BYTES, &tB_hi, &full[stage], kc * KC, yb);
+        tma_load_2d(sb + 3 * OP_BYTES, &tB_lo, &full[stage], kc * KC, yb);
+        last_par[stage] = (int)phase;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (*abort) {  // let every copy this thread issued land before the CTA exits
+      for (int s = 0; s < STAGES; ++s)
+        if (last_par[s] >= 0) {
+          volatile int never = 0;
+          mbar_wait(&full[s], (uint32_t)last_par[s], &never);
+        }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int it = 0;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accempty[b], ap ^ 1, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 12);
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + b * TN;
+      bool ok = true;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&full[stage], phase, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 13);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+        const uint64_t ahi = sdesc_sw128(sb), alo = sdesc_sw128(sb + OP_BYTES);
+        const uint64_t bhi = sdesc_sw128(sb + 2 * OP_BYTES), blo = sdesc_sw128(sb + 3 * OP_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < KC / 8; ++kk) {  // K = 8 per instruction: advance 32 bytes
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_tf32(d, ahi + o, bhi + o, IDESC, (kc | kk) ? 1u : 0u);
+          mma_tf32(d, ahi + o, blo + o, IDESC, 1u);
+          mma_tf32(d, alo + o, bhi + o, IDESC, 1u);
+        }
+        mma_commit(&empty[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&accfull[b]);
+      ++it;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> FP64 C ----------------
+    const int quad = warp & 3;  // TMEM lanes 32*quad .. 32*quad+31
+    const int r = quad * 32 + lane;
+    int it = 0;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accfull[b], ap, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 14);
+        break;
+      }
+      fence_after();
+      const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
+      const int64_t col0 = g.c_col0 + (int64_t)bj * TN;
+      const bool diag = g.lower_mask && (bi == bj);
+      double* cp = g.C + row + col0 * g.ldc;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        uint32_t acc[32];
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + b * TN + c * 32, acc);
+        double cv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(c * 32 + j) * g.ldc];
+        tmem_ld_wait();
+        if (c == 3) {
+          fence_before();
+          mbar_arrive(&accempty[b]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int cc = c * 32 + j;
+          if (diag && cc > r) continue;
+          const double v = (double)__uint_as_float(acc[j]);
+          cp[(int64_t)cc * g.ldc] = g.store ? v : cv[j] - v;
+        }
+      }
+      ++it;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ===========================================================================
+// OZ kernel: tile 128 x 32, K chunks of 64 BF16 digits, S = 5 slices, 2 stages.
+// ===========================================================================
+namespace oz {
+constexpr int TM = 128, TN = 32, KC = 64, STAGES = 2, S = kOzSlices;
+constexpr int A_BYTES = TM * KC * 2;   // 16 KB per slice
+constexpr int B_BYTES = TN * KC * 2;   // 4 KB per slice
+constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t IDESC = idesc(kFmtBF16, TM, TN);
+constexpr int GROUP_COLS = TN;          // one accumulator per slice-sum group
+constexpr int BUF_COLS = S * GROUP_COLS;
+constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a power of two
+}  // namespace oz
+
+__global__ void __launch_bounds__(192, 1) gemm_oz_kernel(const __grid_constant__ OzMaps ta,
+                                                         const __grid_constant__ OzMaps tb,
+                                                         const __grid_constant__ GemmArgs g) {
+  using namespace oz;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accfull = empty + STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int kchunks = g.K / KC;
+
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < S; ++s) {
+      prefetch_tmap(&ta.m[s]);
+      prefetch_tmap(&tb.m[s]);
+    }
+    int stage = 0;
+    uint32_t phase = 0;
+    int last_par[STAGES];
+    for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + bj * TN;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 21);
+          break;
+        }
+        uint8_t* sb = smem + stage * STAGE_BYTES;
+        mbar_expect_tx(&full[stage], STAGE_BYTES);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          tma_load_2d(sb + s * A_BYTES, &ta.m[s], &full[stage], kc * KC, ya);
+          tma_load_2d(sb + S * A_BYTES + s * B_BYTES, &tb.m[s], &full[stage], kc * KC, yb);
+        }
+        last_par[stage] = (int)phase;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (*abort) {
+      for (int s = 0; s < STAGES; ++s)
+        if (last_par[s] >= 0) {
+          volatile int never = 0;
+          mbar_wait(&full[s], (uint32_t)last_par[s], &never);
+        }
+    }
+  } else if (warp == 1 && lane == 0) {
+    int stage = 0;
+    uint32_t phase = 0;
+    int it = 0;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accempty[b], ap ^ 1, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 22);
+        break;
+      }
+      fence_after();
+      const uint32_t d0 = tmem + b * BUF_COLS;
+      bool ok = true;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&full[stage], phase, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 23);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < KC / 16; ++kk) {  // K = 16 per instruction: advance 32 bytes
+          const uint64_t o = (uint64_t)(kk * 2);
+#pragma unroll
+          for (int gs = 0; gs < S; ++gs) {       // slice-sum group
+#pragma unroll
+            for (int s = 0; s <= gs; ++s) {
+              const int t2 = gs - s;
+              const uint64_t a = sdesc_sw128(sb + s * A_BYTES) + o;
+              const uint64_t bb = sdesc_sw128(sb + S * A_BYTES + t2 * B_BYTES) + o;
+              mma_bf16(d0 + gs * GROUP_COLS, a, bb, IDESC, (kc | kk | s) ? 1u : 0u);
+            }
+          }
+        }
+        mma_commit(&empty[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&accfull[b]);
+      ++it;
+    }
+  } else if (warp >= 2) {
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    int it = 0;
+    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+      int bi, bj;
+      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accfull[b], ap, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 24);
+        break;
+      }
+      fence_after();
+      double v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0.0;
+#pragma unroll
+      for (int gs = S - 1; gs >= 0; --gs) {  // smallest group first
+        uint32_t acc[32];
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS, acc);
+        tmem_ld_wait();
+        const double sc = ldexp(1.0, -7 * (gs + 2));
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fma((double)__uint_as_float(acc[j]), sc, v[j]);
+      }
+      fence_before();
+      mbar_arrive(&accempty[b]);
+      const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
+      const int64_t col0 = g.c_col0 + (int64_t)bj * TN;
+      const int er = g.ea[g.a_row0 + bi * TM + r];
+      const bool lower = g.lower_mask != 0;
+      double* cp = g.C + row + col0 * g.ldc;
+      double cv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)j * g.ldc];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (lower && col0 + j > row) continue;
+        const int ec = g.eb[g.b_row0 + bj * TN + j];
+        const double x = ldexp(v[j], er + ec);
+        cp[(int64_t)j * g.ldc] = g.store ? x : cv[j] - x;
+      }
+      ++it;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ===========================================================================
+// Split kernel: FP64 rows -> T3 (tf32 hi/lo, row-major) and OZ digits.
+// One CTA per 32 rows; K <= 256.  src element (r, k) at src[r*rs + k*cs].
+// ===========================================================================
+__device__ __forceinline__ float tf32_rn(float f) {
+  uint32_t b = __float_as_uint(f);
+  b += 0xFFFu + ((b >> 13) & 1u);
+  return __uint_as_float(b & 0xFFFFE000u);
+}
+
+__global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                                         int rows, int K, float* __restrict__ hi,
+                                                         float* __restrict__ lo, __nv_bfloat16_raw* __restrict__ dig,
+                                                         int64_t dig_stride, int* __restrict__ ex, int out_row0) {
+  extern __shared__ double tile[];  // 32 x (K + 1)
+  const int r0 = blockIdx.x * 32;
+  const int tid = threadIdx.x;
+  const int ld = K + 1;
+  // coalesced along whichever source dimension is contiguous
+  if (cs == 1) {
+    for (int idx = tid; idx < 32 * K; idx += blockDim.x) {
+      const int rr = idx / K, k = idx % K;
+      tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + k] : 0.0;
+    }
+  } else {
+    for (int idx = tid; idx < 32 * K; idx += blockDim.x) {
+      const int rr = idx & 31, k = idx >> 5;
+      tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + (int64_t)k * cs] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int rr = warp; rr < 32; rr += blockDim.x / 32) {
+    const int row = r0 + rr;
+    if (row >= rows) break;
+    const int64_t orow = (int64_t)(out_row0 + row);
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(tile[rr * ld + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) {
+      frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |a| 2^-e <= 1
+    }
+    if (lane == 0 && ex) ex[orow] = e;
+    for (int k = lane; k < K; k += 32) {
+      const double a = tile[rr * ld + k];
+      if (hi) {
+        const float h = tf32_rn((float)a);
+        const float l = tf32_rn((float)(a - (double)h));
+        hi[orow * K + k] = h;
+        lo[orow * K + k] = l;
+      }
+      if (dig) {
+        double x = ldexp(a, -e);
+#pragma unroll
+        for (int s = 0; s < kOzSlices; ++s) {
+          const double d = rint(ldexp(x, 7 * (s + 1)));
+          x -= ldexp(d, -7 * (s + 1));
+          // |d| <= 128: exactly representable in BF16 (8-bit significand)
+          const float df = (float)d;
+          __nv_bfloat16_raw raw;
+          raw.x = (unsigned short)(__float_as_uint(df) >> 16);
+          dig[(int64_t)s * dig_stride + orow * K + k] = raw;
+        }
+      }
+    }
+  }
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D row-major tensor [rows][K] of 4-byte (fp32) or 2-byte (bf16) elements,
+// box = (box_k, box_rows), 128-byte swizzle.
+cudaError_t make_tmap(CUtensorMap* m, const void* base, int64_t rows, int K, int elem_bytes, int box_k, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) != 0 || ((int64_t)K * elem_bytes) % 16 != 0 || box_k * elem_bytes != 128)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_split_maps(SplitOperand& op) {
+  cudaError_t e = cudaSuccess;
+  if (op.hi) {
+    if ((e = make_tmap(&op.t_hi, op.hi, op.rows, op.K, 4, 32, 128)) != cudaSuccess) return e;
+    if ((e = make_tmap(&op.t_lo, op.lo, op.rows, op.K, 4, 32, 128)) != cudaSuccess) return e;
+  }
+  if (op.dig) {
+    for (int s = 0; s < kOzSlices; ++s) {
+      const void* base = (const uint8_t*)op.dig + (size_t)s * op.rows * op.K * 2;
+      if ((e = make_tmap(&op.oz_a.m[s], base, op.rows, op.K, 2, 64, 128)) != cudaSuccess) return e;
+      if ((e = make_tmap(&op.oz_b.m[s], base, op.rows, op.K, 2, 64, 32)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int64_t cs, int rows, int K,
+                              SplitOperand& op, int out_row0) {
+  if (rows <= 0) return cudaSuccess;
+  if (K > kSplitMaxK) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)32 * (K + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(split_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         32 * (kSplitMaxK + 1) * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  split_rows_kernel<<<(rows + 31) / 32, 256, smem, s>>>(src, rs, cs, rows, K, op.hi, op.lo,
+                                                        (__nv_bfloat16_raw*)op.dig, (int64_t)op.rows * op.K, op.ex,
+                                                        out_row0);
+  return cudaGetLastError();
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g) {
+  if (g.ntiles <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm_t3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = (int)(g.ntiles < num_sms() ? g.ntiles : num_sms());
+  gemm_t3_kernel<<<grid, 192, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g) {
+  if (g.ntiles <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = (int)(g.ntiles < num_sms() ? g.ntiles : num_sms());
+  GemmArgs g2 = g;
+  g2.ea = A.ex;
+  g2.eb = B.ex;
+  gemm_oz_kernel<<<grid, 192, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
+  return cudaGetLastError();
+}
+
+}  // namespace exa

@@ -1,0 +1,61 @@
+// Tensor-core (tcgen05) split-precision GEMM kernels and their operand formats.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "exa_internal.cuh"
+
+namespace exa {
+
+constexpr int kOzSlices = 5;  // 7-bit digits per value in the exact (band) products
+constexpr int kSplitMaxK = 512;  // longest row the split kernel converts
+
+// Tile enumeration of one launch.
+enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2 };
+
+struct OzMaps {
+  CUtensorMap m[kOzSlices];
+};
+
+// Kernel arguments (passed by value as a __grid_constant__).
+struct GemmArgs {
+  double* C;                  // FP64 output, column-major
+  int64_t ldc;
+  int64_t c_row0, c_col0;     // output origin
+  int a_row0, b_row0;         // operand row origins
+  int K;                      // reduction length (T3: % 32, OZ: % 64, <= 256 for OZ)
+  int enum_mode;              // kEnum*
+  int nt;                     // tiles along N (kEnumFull)
+  int band;                   // band width in 256-wide tiles (kEnumLowerOffBand / kEnumBand)
+  long long ntiles;           // number of enumerated tiles
+  int store;                  // 1: C = A B^T ; 0: C -= A B^T
+  int lower_mask;             // skip entries above the diagonal
+  const int* ea;              // OZ: per-row power-of-two exponents of A (set by the launcher)
+  const int* eb;              // OZ: per-row exponents of B
+  DevStatus* st;
+};
+
+// One split operand: `rows` x K values held as T3 (tf32 hi/lo, row-major) and/or
+// OZ digits (kOzSlices planes of rows x K BF16, row-major) with row exponents.
+struct SplitOperand {
+  int64_t rows = 0;
+  int K = 0;
+  float* hi = nullptr;
+  float* lo = nullptr;
+  void* dig = nullptr;
+  int* ex = nullptr;
+  CUtensorMap t_hi, t_lo;     // boxes 32 x 128
+  OzMaps oz_a;                // boxes 64 x 128 (A role)
+  OzMaps oz_b;                // boxes 64 x 32  (B role)
+};
+
+cudaError_t make_split_maps(SplitOperand& op);
+// rows [0, rows) of src (element (r, k) at src[r*rs + k*cs]) -> operand rows [out_row0, ...)
+cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int64_t cs, int rows, int K,
+                              SplitOperand& op, int out_row0);
+cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g);
+cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g);
+
+}  // namespace exa

@@ -1,0 +1,93 @@
+"""The tensor-core products of the mixed-precision factorisation (step a2), checked alone.
+
+C -= A B^T through the C ABI (exa_gemm_update) against the FP64 product, with
+bounds that follow from each kind's arithmetic:
+  T3: three TF32 products (hi/lo halves rounded to nearest, ~22 bits) and FP32
+      accumulation over k terms: |err_ij| <= 2^-19 sum_k |A_ik B_jk| is generous.
+  OZ: five 7-bit digits per value relative to the row maximum, exact integer
+      accumulation: |err_ij| <= k * 2^-33 * max_k|A_ik| * max_k|B_jk|.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1908_06936_gb300 as exa
+
+    c = exa.Context()
+    yield c
+    c.close()
+
+
+def operands(m, n, k, seed, spread):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-spread, spread, (m, 1))
+    B = rng.standard_normal((n, k)) * 10.0 ** rng.uniform(-spread, spread, (n, 1))
+    # some exact zeros and a zero row
+    A[3, :] = 0.0
+    A[rng.integers(0, m, 20), rng.integers(0, k, 20)] = 0.0
+    return A, B
+
+
+def run(ctx, kind, A, B, C0, store):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    m, k = A.shape
+    n = B.shape[0]
+    dA = torch.as_tensor(A, device="cuda")
+    dB = torch.as_tensor(B, device="cuda")
+    # column-major C (m x n, ldc = m) held as a row-major (n, m) buffer
+    dC = torch.as_tensor(np.ascontiguousarray(C0.T), device="cuda")
+    ctx.check(exa.exa_gemm_update(ctx.handle, kind, m, n, k, dA, dB, dC, m, store))
+    return dC.cpu().numpy().T
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (256, 384, 256), (384, 128, 512), (128, 256, 128)])
+@pytest.mark.parametrize("store", [0, 1])
+def test_t3_product(ctx, m, n, k, store):
+    import paper_1908_06936_gb300 as exa
+
+    A, B = operands(m, n, k, seed=m + n + k, spread=2)
+    C0 = np.random.default_rng(1).standard_normal((m, n))
+    got = run(ctx, exa.EXA_GEMM_T3, A, B, C0, store)
+    ref = A @ B.T if store else C0 - A @ B.T
+    bound = 2.0 ** -19 * (np.abs(A) @ np.abs(B).T) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 32, 64), (256, 96, 256), (128, 256, 128), (384, 32, 192)])
+@pytest.mark.parametrize("store", [0, 1])
+def test_oz_product(ctx, m, n, k, store):
+    import paper_1908_06936_gb300 as exa
+
+    A, B = operands(m, n, k, seed=7 * m + n + k, spread=3)
+    C0 = np.random.default_rng(2).standard_normal((m, n))
+    got = run(ctx, exa.EXA_GEMM_OZ, A, B, C0, store)
+    ref = A @ B.T if store else C0 - A @ B.T
+    bound = k * 2.0 ** -33 * np.outer(np.abs(A).max(1), np.abs(B).max(1)) + 4e-16 * np.abs(ref) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+
+
+def test_oz_exact_on_short_integers(ctx):
+    # values that are exactly representable in the digits: the product must be exact
+    import paper_1908_06936_gb300 as exa
+
+    rng = np.random.default_rng(5)
+    A = rng.integers(-127, 128, (128, 256)).astype(np.float64) / 128.0
+    B = rng.integers(-127, 128, (32, 256)).astype(np.float64) / 256.0
+    got = run(ctx, exa.EXA_GEMM_OZ, A, B, np.zeros((128, 32)), 1)
+    assert np.array_equal(got, A @ B.T)
+
+
+def test_bad_shapes(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    a = torch.zeros(100 * 64, dtype=torch.float64, device="cuda")
+    b = torch.zeros(128 * 64, dtype=torch.float64, device="cuda")
+    c = torch.zeros(128 * 128, dtype=torch.float64, device="cuda")
+    assert exa.exa_gemm_update(ctx.handle, exa.EXA_GEMM_T3, 100, 128, 64, a, b, c, 128, 0) == exa.EXA_ERR_ARG
