@@ -77,6 +77,8 @@ typedef struct {
   double ir_resid;    /* mixed: final ||z - Sigma x||_2 / ||z||_2; FP64: 0 */
   int32_t ir_iters;   /* mixed: refinement steps taken; FP64: 0 */
   int32_t tile_nb;    /* tile size used by the factorisation */
+  int32_t exact_band; /* mixed: tile rows next to the diagonal with exact products (all tiles when = T) */
+  int32_t n_tiles;    /* number of tile rows T of the factorisation */
   float ms_gen;       /* device time of the covariance generation (ms) */
   float ms_chol;      /* device time of the Cholesky factorisation (ms) */
   float ms_solve;     /* device time of log-det + solve (+ refinement) (ms) */
@@ -95,6 +97,16 @@ void exa_ctx_destroy(exa_ctx* ctx);
 
 /* Replace the stream work is issued on.                                    */
 exa_status exa_ctx_set_stream(exa_ctx* ctx, void* cuda_stream);
+
+/* Mixed precision: number of 256-wide tile rows next to the diagonal whose
+ * products use the exact digit-slice arithmetic (the rest use TF32x3).
+ * band >= 1 fixes it; a negative value makes every tile exact; 0 (the
+ * default) picks it per evaluation from Sigma itself: the widest tile-row
+ * offset d whose tiles hold some |Sigma_ij| >= 0.8 sigma^2 (where the Schur
+ * complement cancels most), and every tile when nu > 1.2 (smooth fields
+ * cancel everywhere).  If the reduced-precision factor loses positive
+ * definiteness the evaluation is repeated with every tile exact.           */
+exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
 
 /* Message describing the last error on this context ("" if none).  The
  * string is owned by the context and valid until its next call.           */

@@ -19,7 +19,7 @@ __all__ = [
     "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
-    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -43,7 +43,7 @@ class ExaError(RuntimeError):
 class ExaResult(ctypes.Structure):
     _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
                 ("ir_resid", ctypes.c_double), ("ir_iters", ctypes.c_int32), ("tile_nb", ctypes.c_int32),
-                ("ms_gen", ctypes.c_float), ("ms_chol", ctypes.c_float), ("ms_solve", ctypes.c_float),
+                ("exact_band", ctypes.c_int32), ("n_tiles", ctypes.c_int32), ("ms_gen", ctypes.c_float), ("ms_chol", ctypes.c_float), ("ms_solve", ctypes.c_float),
                 ("ms_total", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
                 "exa_loglik_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                                       ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P]),
                 "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
+                "exa_ctx_set_mixed_band": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
             }
@@ -194,6 +195,10 @@ def exa_ctx_destroy(ctx: int) -> None:
 
 def exa_ctx_set_stream(ctx: int, cuda_stream: int) -> int:
     return lib().exa_ctx_set_stream(_P(ctx), _P(cuda_stream or None))
+
+
+def exa_ctx_set_mixed_band(ctx: int, band: int) -> int:
+    return lib().exa_ctx_set_mixed_band(_P(ctx), int(band))
 
 
 def exa_last_error(ctx: int) -> str:

@@ -180,6 +180,12 @@ exa_status exa_ctx_set_stream(exa_ctx* c, void* cuda_stream) {
   return EXA_OK;
 }
 
+exa_status exa_ctx_set_mixed_band(exa_ctx* c, int band) {
+  if (!c) return EXA_ERR_ARG;
+  c->mixed_band = band;
+  return EXA_OK;
+}
+
 const char* exa_last_error(const exa_ctx* c) { return c ? c->err : "null context"; }
 
 int64_t exa_last_pivot(const exa_ctx* c) { return c ? c->last_pivot : -1; }
@@ -311,19 +317,24 @@ extern "C" exa_status exa_simulate(exa_ctx* c, const double* d_locs, const doubl
   c->err[0] = 0;
   c->last_pivot = -1;
   if (n < 1 || !d_locs || !d_eps || !d_z) return set_err(c, EXA_ERR_ARG, "bad n or NULL device pointer");
-  if (prec != EXA_FP64) return set_err(c, EXA_ERR_ARG, "exa_simulate supports EXA_FP64 only");
+  if (prec != EXA_FP64 && prec != EXA_MIXED_TF32X3) return set_err(c, EXA_ERR_ARG, "unsupported precision");
   exa_status st = check_theta(c, theta);
   if (st != EXA_OK) return st;
   const int nb = c->tile_nb;
-  const int64_t npad = round_up(n, nb);
+  const int64_t npad = round_up(n, prec == EXA_FP64 ? nb : 256);
   if ((st = ensure(c, c->mat, (size_t)npad * npad * sizeof(double), "matrix")) != EXA_OK) return st;
   if ((st = reset_status(c)) != EXA_OK) return st;
   double* A = (double*)c->mat.p;
-  MaternParams P;
-  matern_params(theta, &P);
-  cudaError_t e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
-  if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
-  if ((st = factor_fp64(c, A, npad, npad, nb)) != EXA_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (prec == EXA_FP64) {
+    MaternParams P;
+    matern_params(theta, &P);
+    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
+    if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
+    if ((st = factor_fp64(c, A, npad, npad, nb)) != EXA_OK) return st;
+  } else {
+    if ((st = mixed_generate_factor(c, d_locs, n, theta, npad, prec, nullptr, nullptr)) != EXA_OK) return st;
+  }
   e = launch_trmv_lower(c->stream, A, npad, n, d_eps, d_z, c->d_status);
   if (e != cudaSuccess) return cuda_err(c, e, "trmv launch");
   return read_status(c);

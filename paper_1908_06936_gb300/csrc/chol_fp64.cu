@@ -269,3 +269,92 @@ cudaError_t launch_syrk_update(cudaStream_t s, double* a, int64_t ld, int64_t r0
 }
 
 }  // namespace exa
+
+namespace exa {
+
+// ---------------------------------------------------------------------------
+// Small strided FP64 product on DMMA:  C = alpha A B^T + beta C, element
+// accessors A(i,k) = a[i*ar + k*ac], B(j,k) = b[j*br + k*bc], C(i,j) = c[i*cr + j*cc].
+// M, N multiples of 32, K a multiple of 32.  One CTA (4 warps, 2 x 2 warp tiles
+// of 16 x 16) per 32 x 32 output tile.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) dgemm_nt_small_kernel(int K, double alpha, const double* __restrict__ a,
+                                                             int64_t ar, int64_t ac, const double* __restrict__ b,
+                                                             int64_t br, int64_t bc, double beta, double* c,
+                                                             int64_t cr, int64_t cc, const DevStatus* st) {
+  __shared__ double As[32 * kSS];
+  __shared__ double Bs[32 * kSS];
+  if (failed(st)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  double acc[2][2][2];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+  for (int t0 = 0; t0 < K; t0 += kKC) {
+    for (int idx = tid; idx < 32 * kKC; idx += blockDim.x) {
+      const int r = idx & 31, t = idx >> 5;
+      As[r * kSS + t] = a[(i0 + r) * ar + (int64_t)(t0 + t) * ac];
+      Bs[r * kSS + t] = b[(j0 + r) * br + (int64_t)(t0 + t) * bc];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKC; kk += 4) {
+      double af[2], bf[2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) af[mi] = As[(wm * 16 + mi * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) bf[ni] = Bs[(wn * 16 + ni * 8 + g) * kSS + kk + q];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) dmma_884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t i = i0 + wm * 16 + mi * 8 + g;
+        const int64_t j = j0 + wn * 16 + ni * 8 + 2 * q + e;
+        double* p = c + i * cr + j * cc;
+        *p = alpha * acc[mi][ni][e] + (beta != 0.0 ? beta * *p : 0.0);
+      }
+}
+
+cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double alpha, const double* a, int64_t ar,
+                                  int64_t ac, const double* b, int64_t br, int64_t bc, double beta, double* c,
+                                  int64_t cr, int64_t cc, const DevStatus* st) {
+  dim3 grid(N / 32, M / 32);
+  dgemm_nt_small_kernel<<<grid, 128, 0, s>>>(K, alpha, a, ar, ac, b, br, bc, beta, c, cr, cc, st);
+  return cudaGetLastError();
+}
+
+// W (2nb x 2nb, row-major, lower) <- [W00 0; 0 W11] from two inverted nb x nb
+// diagonal tiles; the W10 block is filled by two small products afterwards.
+__global__ void assemble_w2_kernel(const double* __restrict__ w00, const double* __restrict__ w11, int nb,
+                                   double* __restrict__ w) {
+  const int n2 = 2 * nb;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2 * n2; idx += gridDim.x * blockDim.x) {
+    const int r = idx / n2, c = idx % n2;
+    double v = 0.0;
+    if (r < nb && c < nb)
+      v = w00[r * nb + c];
+    else if (r >= nb && c >= nb)
+      v = w11[(r - nb) * nb + (c - nb)];
+    w[idx] = v;
+  }
+}
+
+cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w) {
+  assemble_w2_kernel<<<64, 256, 0, s>>>(w00, w11, nb, w);
+  return cudaGetLastError();
+}
+
+}  // namespace exa

@@ -26,6 +26,7 @@ struct exa_ctx {
   size_t ws_limit = 0;   // 0: unbounded
   size_t held_bytes = 0;
   int tile_nb = 128;     // FP64 tile
+  int mixed_band = 0;    // exact-product band (256-wide tiles); 0: from Sigma; < 0: all tiles
   int64_t last_pivot = -1;
   char err[512];
   // workspace
@@ -41,6 +42,8 @@ struct exa_ctx {
   exa::DevBuf mx_split_b;   // split-precision operands (B role: inverse diagonal block / test B)
   exa::SplitOperand sp_a, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
+  exa::DevBuf mx_w2;        // inverses of the 256-wide diagonal blocks (for the solves)
+  exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
   // gradient
   exa::DevBuf gr_part;      // per-block gradient partials
   // batched
@@ -62,6 +65,10 @@ exa_status check_theta(exa_ctx* c, const double theta[3]);
 exa_status reset_status(exa_ctx* c);
 exa_status read_status(exa_ctx* c);
 exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb);
+exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band);
+// Generate Sigma into `sigma_keep` (or straight into the factor buffer) and factor it in mixed precision.
+exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, const double theta[3], int64_t npad,
+                                 exa_prec prec, double* sigma_keep, int* band_used);
 exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                        exa_result* out, double** keep_y);
 exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,

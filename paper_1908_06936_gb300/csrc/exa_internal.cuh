@@ -68,10 +68,13 @@ struct DevStatus {
 // Lower triangle (diagonal included) of Sigma for rows/cols < n into column-major
 // `a` (leading dim ld).  Rows/cols in [n, npad) are filled as the identity so
 // that a padded matrix factors as diag(L, I).
+// If offmax is non-null, offmax[d] receives (as the bits of a non-negative double)
+// the largest off-diagonal |Sigma_ij| over 256-wide tile pairs (I, J) with I - J = d.
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld);
+                              double* a, int64_t ld, unsigned long long* offmax = nullptr);
 
 // FP64 tiled Cholesky steps (tile nb <= 128, multiple of 64; n multiple of nb).
+// The triangular-solve steps accept nb <= 256.
 cudaError_t launch_potrf_diag(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, double* w_out,
                               double* logdet_part, DevStatus* st);
 cudaError_t launch_trsm_panel(cudaStream_t s, double* a, int64_t ld, int64_t k0, int nb, int64_t m,
@@ -90,6 +93,17 @@ cudaError_t launch_trsv_bwd_step(cudaStream_t s, const double* a, int64_t ld, in
 // Deterministic reductions: out[0] = sum(v[i]^2) ; out[0] = sum(v[i]) over n values.
 cudaError_t launch_sumsq(cudaStream_t s, const double* v, int64_t n, double* partial, double* out);
 cudaError_t launch_sum(cudaStream_t s, const double* v, int64_t n, double* partial, double* out);
+
+// Small strided FP64 DMMA product C = alpha A B^T + beta C (M, N, K multiples of 32).
+cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double alpha, const double* a, int64_t ar,
+                                  int64_t ac, const double* b, int64_t br, int64_t bc, double beta, double* c,
+                                  int64_t cr, int64_t cc, const DevStatus* st);
+cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w);
+// Refinement helpers.
+cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y);
+cudaError_t launch_residual(cudaStream_t s, const double* z, const double* y, double* r, int64_t n);
+cudaError_t launch_axpy(cudaStream_t s, double a, const double* x, double* y, int64_t n);
+cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t n, double* partial, double* out);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -193,11 +193,12 @@ __device__ __forceinline__ void tri_decode(long long b, int& ti, int& tj) {
 // the column-major stores coalesce).
 __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restrict__ locs, int64_t n, int64_t npad,
                                                          const __grid_constant__ MaternParams P, double* __restrict__ a,
-                                                         int64_t ld) {
+                                                         int64_t ld, unsigned long long* __restrict__ offmax) {
   int ti, tj;
   tri_decode(blockIdx.x, ti, tj);
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
-  if (i >= npad) return;
+  double vmax = 0.0;  // largest off-diagonal |Sigma_ij| of this thread (for the precision map)
+  if (i < npad) {
   double xi = 0.0, yi = 0.0;
   if (i < n) {
     xi = __ldg(locs + 2 * i);
@@ -215,17 +216,29 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
       const double dx = xi - __ldg(locs + 2 * j);
       const double dy = yi - __ldg(locs + 2 * j + 1);
       v = matern_value(P, sqrt(dx * dx + dy * dy));
+      vmax = fmax(vmax, fabs(v));
     }
     a[i + j * ld] = v;
+  }
+  }
+  if (offmax) {
+    // non-negative doubles order like their bit patterns: one atomicMax per warp
+    unsigned long long b = (unsigned long long)__double_as_longlong(vmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+      b = ob > b ? ob : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&offmax[(ti >> 2) - (tj >> 2)], b);
   }
 }
 
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld) {
+                              double* a, int64_t ld, unsigned long long* offmax) {
   const long long t = (npad + 63) / 64;
   const long long blocks = t * (t + 1) / 2;
   if (blocks <= 0) return cudaSuccess;
-  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld);
+  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,12 @@
 
 namespace exa {
 
+constexpr int kMixNB = 256;      // panel width = K of every tensor-core product
+constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
+constexpr double kIrFailTol = 1e-8;
+constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
+constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
+
 exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz) {
   const size_t t3_bytes = t3 ? (size_t)rows * K * 4 : 0;
   const size_t dig_bytes = oz ? (size_t)kOzSlices * rows * K * 2 : 0;
@@ -33,6 +39,266 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
     op.rows = 0;
     return cuda_err(c, e, "tensor map encode");
   }
+  return EXA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision tiled Cholesky (panel width 256).  For tile column k:
+//   1. FP64 factorisation of the 256 x 256 diagonal block as two 128 sub-tiles
+//      (POTRF, TRSM, SYRK, POTRF on DMMA), then its inverse
+//      W = [W00 0; -W11 L10 W00  W11] (two small DMMA products).
+//   2. Panel TRSM  L_ik = A_ik W^T on the tensor cores: the first `band` tile
+//      rows with the exact OZ products, the rest with T3.
+//   3. Trailing update A_ij -= L_ik L_jk^T: tiles with I - J <= band (the
+//      diagonal tile and its neighbours, where the Schur complement cancels
+//      most) with OZ, all others with T3.  Storage stays FP64 throughout.
+// ---------------------------------------------------------------------------
+exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band) {
+  const int NB = kMixNB, nb = kMixSub;
+  const int T = (int)(npad / NB);
+  if (band < 1) band = 1;
+  const int T128 = (int)(npad / nb);
+  exa_status st;
+  if (prec != EXA_MIXED_TF32X3) return set_err(c, EXA_ERR_ARG, "precision %d has no mixed kernel", (int)prec);
+  if ((st = ensure(c, c->w_all, (size_t)T128 * nb * nb * sizeof(double), "inverted diagonal tiles")) != EXA_OK)
+    return st;
+  if ((st = ensure(c, c->panel, (size_t)(nb * nb + NB * NB + nb * nb) * sizeof(double), "panel")) != EXA_OK)
+    return st;
+  if ((st = ensure(c, c->logdet_part, (size_t)T128 * sizeof(double), "log-det partials")) != EXA_OK) return st;
+  if ((st = ensure_split(c, c->sp_a, c->mx_split, npad, NB, true, true)) != EXA_OK) return st;
+  if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
+  if ((st = ensure(c, c->mx_w2, (size_t)T * NB * NB * sizeof(double), "diagonal block inverses")) != EXA_OK)
+    return st;
+  double* W = (double*)c->w_all.p;
+  double* P = (double*)c->panel.p;       // 128 x 128 FP64 panel of the in-block TRSM
+  double* tmp = P + nb * nb;             // 128 x 128 scratch
+  double* LD = (double*)c->logdet_part.p;
+  cudaStream_t s = c->stream;
+  for (int k = 0; k < T; ++k) {
+    const int64_t k0 = (int64_t)k * NB;
+    cudaError_t e = launch_potrf_diag(s, a, ld, k0, nb, W, LD, c->d_status);
+    if (e == cudaSuccess) e = launch_trsm_panel(s, a, ld, k0, nb, nb, W, P, c->d_status);
+    if (e == cudaSuccess) e = launch_syrk_update(s, a, ld, k0 + nb, nb, nb, P, c->d_status);
+    if (e == cudaSuccess) e = launch_potrf_diag(s, a, ld, k0 + nb, nb, W, LD, c->d_status);
+    if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
+    double* W2 = (double*)c->mx_w2.p + (int64_t)k * NB * NB;  // 256 x 256 inverse of the block (row-major)
+    const double* w00 = W + (k0 / nb) * (int64_t)nb * nb;
+    const double* w11 = w00 + (int64_t)nb * nb;
+    e = launch_assemble_w2(s, w00, w11, nb, W2);
+    // tmp = L10 W00 ;  W10 = -W11 tmp
+    if (e == cudaSuccess)
+      e = launch_dgemm_nt_small(s, nb, nb, nb, 1.0, a + (k0 + nb) + k0 * ld, 1, ld, w00, 1, nb, 0.0, tmp, nb, 1,
+                                c->d_status);
+    if (e == cudaSuccess)
+      e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, w11, nb, 1, tmp, 1, nb, 0.0, W2 + (int64_t)nb * NB, NB, 1,
+                                c->d_status);
+    if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
+    if (k == T - 1) break;
+    e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
+    const int64_t r0 = k0 + NB;
+    const int64_t m = npad - r0;
+    double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
+    if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    if (e != cudaSuccess) return cuda_err(c, e, "inverse / split launch");
+    // TRSM on the tensor cores: L_ik = A_ik W^T
+    const int64_t rb = m < (int64_t)band * NB ? m : (int64_t)band * NB;
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.C = a;
+    g.ldc = ld;
+    g.K = NB;
+    g.st = c->d_status;
+    g.store = 1;
+    g.enum_mode = kEnumFull;
+    g.c_col0 = k0;
+    g.c_row0 = r0;
+    g.a_row0 = 0;
+    g.b_row0 = 0;
+    g.nt = NB / 32;
+    g.ntiles = (rb / 128) * g.nt;
+    e = launch_gemm_oz(s, c->sp_a, c->sp_b, g);
+    if (e == cudaSuccess && m > rb) {
+      g.c_row0 = r0 + rb;
+      g.a_row0 = (int)rb;
+      g.nt = NB / 128;
+      g.ntiles = ((m - rb) / 128) * g.nt;
+      e = launch_gemm_t3(s, c->sp_a, c->sp_b, g);
+    }
+    if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
+    // trailing update
+    memset(&g, 0, sizeof(g));
+    g.C = a;
+    g.ldc = ld;
+    g.K = NB;
+    g.st = c->d_status;
+    g.store = 0;
+    g.lower_mask = 1;
+    g.band = band;
+    g.c_row0 = g.c_col0 = r0;
+    const long long t128 = m / 128;
+    g.enum_mode = kEnumLowerOffBand;
+    g.ntiles = t128 * (t128 + 1) / 2;
+    e = launch_gemm_t3(s, c->sp_a, c->sp_a, g);
+    if (e == cudaSuccess) {
+      const long long tr = m / NB;
+      long long pairs = 0;
+      for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
+      g.enum_mode = kEnumBand;
+      g.ntiles = pairs * (NB / 128) * (NB / 32);
+      e = launch_gemm_oz(s, c->sp_a, c->sp_a, g);
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "trailing update launch");
+  }
+  return EXA_OK;
+}
+
+// x = (L L^T)^-1 rhs with the FP64-stored factor, on 256-wide tiles with the
+// stored inverses of the diagonal blocks.
+static cudaError_t solve_llt(exa_ctx* c, const double* a, int64_t ld, int64_t npad, const double* rhs, double* x,
+                             double* work, double* part) {
+  const int nb = kMixNB;
+  const int T = (int)(npad / nb);
+  const double* W = (const double*)c->mx_w2.p;
+  cudaError_t e = cudaMemcpyAsync(work, rhs, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  for (int k = 0; k < T && e == cudaSuccess; ++k)
+    e = launch_trsv_fwd_step(c->stream, a, ld, npad, nb, k, W, x, work, c->d_status);
+  for (int k = T - 1; k >= 0 && e == cudaSuccess; --k)
+    e = launch_trsv_bwd_step(c->stream, a, ld, npad, nb, k, W, x, part, c->d_status);
+  return e;
+}
+
+// Generation (FP64, with the per-offset maxima for the precision map), the
+// band choice and the mixed factorisation, retried with every tile exact if
+// the reduced-precision factor is not positive definite.
+exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, const double theta[3], int64_t npad,
+                                 exa_prec prec, double* sigma_keep, int* band_used) {
+  const int T = (int)(npad / kMixNB);
+  exa_status st;
+  if ((st = ensure(c, c->mat, (size_t)npad * npad * sizeof(double), "matrix")) != EXA_OK) return st;
+  if ((st = ensure(c, c->mx_offmax, (size_t)(T + 1) * sizeof(unsigned long long), "precision map")) != EXA_OK)
+    return st;
+  double* A = (double*)c->mat.p;
+  double* G = sigma_keep ? sigma_keep : A;
+  unsigned long long* offmax = (unsigned long long*)c->mx_offmax.p;
+  MaternParams Pm;
+  matern_params(theta, &Pm);
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemsetAsync(offmax, 0, (size_t)(T + 1) * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax);
+  if (e == cudaSuccess && sigma_keep)
+    e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "generation");
+  cudaEventRecord(c->ev[1], s);
+  int band = c->mixed_band;
+  if (band == 0 && theta[2] > kSmoothNu) band = -1;  // smooth fields: exact products everywhere
+  if (band == 0) {
+    static thread_local unsigned long long h[1 << 14];
+    const int cnt = T < (1 << 14) ? T : (1 << 14);
+    e = cudaMemcpyAsync(h, offmax, (size_t)cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(c, e, "precision map read");
+    band = 1;
+    for (int d = cnt - 1; d >= 1; --d) {
+      double v;
+      memcpy(&v, &h[d], sizeof(v));
+      if (v >= kExactThreshold * theta[0]) {
+        band = d;
+        break;
+      }
+    }
+  } else if (band < 0) {
+    band = T;
+  }
+  st = factor_mixed(c, A, npad, npad, prec, band);
+  if (st != EXA_OK) return st;
+  st = read_status(c);
+  if (st == EXA_ERR_NOT_SPD && band < T && sigma_keep) {
+    // the reduced-precision updates broke positive definiteness: redo with exact products everywhere
+    if ((st = reset_status(c)) != EXA_OK) return st;
+    e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_err(c, e, "refactor copy");
+    band = T;
+    st = factor_mixed(c, A, npad, npad, prec, band);
+    if (st == EXA_OK) st = read_status(c);
+  }
+  if (band_used) *band_used = band;
+  return st;
+}
+
+exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                        exa_prec prec, exa_result* out) {
+  if (prec != EXA_MIXED_TF32X3)
+    return set_err(c, EXA_ERR_ARG,
+                   "EXA_MIXED_BF16X3 is not offered: three BF16 products (16 significant bits) leave "
+                   "|dl|/|l| near 3e-4 on smooth Matern fields; use EXA_MIXED_TF32X3");
+  const int64_t npad = round_up(n, kMixNB);
+  const int T128 = (int)(npad / kMixSub);
+  exa_status st;
+  if ((st = ensure(c, c->mx_sigma, (size_t)npad * npad * sizeof(double), "FP64 covariance copy")) != EXA_OK)
+    return st;
+  if ((st = ensure(c, c->mx_vec, (size_t)6 * npad * sizeof(double), "refinement vectors")) != EXA_OK) return st;
+  if ((st = ensure(c, c->partial, (size_t)(kPartialDoubles(npad, kMixNB)) * sizeof(double), "partials")) != EXA_OK)
+    return st;
+  if ((st = reset_status(c)) != EXA_OK) return st;
+  double* S = (double*)c->mx_sigma.p;
+  double* zp = (double*)c->mx_vec.p;
+  double* x = zp + npad;
+  double* r = x + npad;
+  double* d = r + npad;
+  double* y = d + npad;
+  double* work = y + npad;
+  double* part = (double*)c->partial.p;
+  double* red = part + 2 * kRedPartials;  // backward-solve partials live after the reduction partials
+  cudaStream_t s = c->stream;
+  cudaEventRecord(c->ev[0], s);
+  int band = 0;
+  if ((st = mixed_generate_factor(c, d_locs, n, theta, npad, prec, S, &band)) != EXA_OK) return st;
+  cudaEventRecord(c->ev[2], s);
+  cudaError_t e;
+  e = launch_sum(s, (const double*)c->logdet_part.p, T128, part, c->d_scalars + 1);
+  if (e == cudaSuccess) e = launch_pad_vector(s, d_z, n, npad, zp);
+  if (e == cudaSuccess) e = launch_sumsq(s, zp, npad, part, c->d_scalars + 2);
+  double* A = (double*)c->mat.p;
+  if (e == cudaSuccess) e = solve_llt(c, A, npad, npad, zp, x, work, red);
+  if (e != cudaSuccess) return cuda_err(c, e, "solve launch");
+  // iterative refinement of x = Sigma^-1 z with the FP64 residual
+  double rel = 0.0, prev = 1e300;
+  int it = 0;
+  const int kMaxIt = 10;
+  for (;; ++it) {
+    e = launch_symv_lower(s, S, npad, npad, x, y);
+    if (e == cudaSuccess) e = launch_residual(s, zp, y, r, npad);
+    if (e == cudaSuccess) e = launch_sumsq(s, r, npad, part, c->d_scalars + 3);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_err(c, e, "refinement launch");
+    if ((st = read_status(c)) != EXA_OK) return st;  // synchronises
+    rel = sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]);
+    if (!(rel > 1e-15) || it >= kMaxIt || rel > 0.5 * prev) break;
+    prev = rel;
+    e = solve_llt(c, A, npad, npad, r, d, work, red);
+    if (e == cudaSuccess) e = launch_axpy(s, 1.0, d, x, npad);
+    if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
+  }
+  e = launch_dot(s, zp, x, npad, part, c->d_scalars + 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "quadratic form");
+  cudaEventRecord(c->ev[3], s);
+  if ((st = read_status(c)) != EXA_OK) return st;
+  cudaEventElapsedTime(&out->ms_gen, c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&out->ms_chol, c->ev[1], c->ev[2]);
+  cudaEventElapsedTime(&out->ms_solve, c->ev[2], c->ev[3]);
+  cudaEventElapsedTime(&out->ms_total, c->ev[0], c->ev[3]);
+  out->tile_nb = kMixNB;
+  out->exact_band = band;
+  out->n_tiles = (int)(npad / kMixNB);
+  out->ir_iters = it;
+  out->ir_resid = rel;
+  out->quad = c->h_scalars[0];
+  out->logdet = 2.0 * c->h_scalars[1];
+  out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * out->logdet - 0.5 * out->quad;
+  if (!(rel <= kIrFailTol))
+    return set_err(c, EXA_ERR_IR_NOCONV, "refinement stalled at relative residual %.3e", rel);
   return EXA_OK;
 }
 

@@ -2,11 +2,8 @@
 #include "ctx.cuh"
 
 namespace exa {
-exa_status loglik_mixed(exa_ctx* c, const double*, const double*, const double*, int64_t, exa_prec, exa_result*) {
-  return set_err(c, EXA_ERR_ARG, "mixed precision is not available in this build");
-}
 void release_extra(exa_ctx* c) {
-  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split_b, &c->mx_vec, &c->gr_part,
+  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split_b, &c->mx_vec, &c->mx_w2, &c->mx_offmax, &c->gr_part,
                     &c->bt_mat, &c->bt_meta, &c->bt_vec, &c->bt_work};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);

@@ -16,8 +16,8 @@ __device__ __forceinline__ bool failed_s(const DevStatus* st) { return *(volatil
 __global__ void __launch_bounds__(256) trsv_fwd_kernel(const double* __restrict__ a, int64_t ld, int64_t npad, int nb,
                                                        int k, const double* __restrict__ w_all, double* __restrict__ z,
                                                        double* __restrict__ y, const DevStatus* st) {
-  __shared__ double zk[128];
-  __shared__ double yk[128];
+  __shared__ double zk[256];
+  __shared__ double yk[256];
   if (failed_s(st)) return;
   const int tid = threadIdx.x;
   const int64_t k0 = (int64_t)k * nb;
@@ -56,28 +56,32 @@ cudaError_t launch_trsv_fwd_step(cudaStream_t s, const double* a, int64_t ld, in
 // block that finishes the sum in order and applies W_k^T.
 constexpr int kBwdRows = 1024;  // rows per partial
 
-__global__ void __launch_bounds__(128) trsv_bwd_partial_kernel(const double* __restrict__ a, int64_t ld, int64_t npad,
+__global__ void __launch_bounds__(256) trsv_bwd_partial_kernel(const double* __restrict__ a, int64_t ld, int64_t npad,
                                                                int nb, int k, const double* __restrict__ y,
                                                                double* __restrict__ part, const DevStatus* st) {
-  // block b: rows [k0+nb + b*kBwdRows, ...), thread t: column t of the panel
+  // block b: rows [k0+nb + b*kBwdRows, ...); warp w: panel columns w, w+8, ...; lanes stride the
+  // rows so every load of a column is one coalesced 256-byte access
   if (failed_s(st)) return;
-  const int t = threadIdx.x;
-  if (t >= nb) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = (int64_t)k * nb;
   const int64_t rs = k0 + nb + (int64_t)blockIdx.x * kBwdRows;
   int64_t re = rs + kBwdRows;
   if (re > npad) re = npad;
-  const double* col = a + (k0 + t) * ld;
-  double s = 0.0;
-  for (int64_t r = rs; r < re; ++r) s = fma(col[r], y[r], s);
-  part[(int64_t)blockIdx.x * nb + t] = s;
+  for (int t = warp; t < nb; t += 8) {
+    const double* col = a + (k0 + t) * ld;
+    double s = 0.0;
+    for (int64_t r = rs + lane; r < re; r += 32) s = fma(col[r], y[r], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part[(int64_t)blockIdx.x * nb + t] = s;
+  }
 }
 
-__global__ void __launch_bounds__(128) trsv_bwd_finish_kernel(int64_t npad, int nb, int k, int nparts,
+__global__ void __launch_bounds__(256) trsv_bwd_finish_kernel(int64_t npad, int nb, int k, int nparts,
                                                               const double* __restrict__ w_all,
                                                               const double* __restrict__ part, double* __restrict__ y,
                                                               const DevStatus* st) {
-  __shared__ double v[128];
+  __shared__ double v[256];
   if (failed_s(st)) return;
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)k * nb;
@@ -102,9 +106,9 @@ cudaError_t launch_trsv_bwd_step(cudaStream_t s, const double* a, int64_t ld, in
   int nparts = 0;
   if (m > 0) {
     nparts = (int)((m + kBwdRows - 1) / kBwdRows);
-    trsv_bwd_partial_kernel<<<nparts, 128, 0, s>>>(a, ld, npad, nb, k, y, tmp, st);
+    trsv_bwd_partial_kernel<<<nparts, 256, 0, s>>>(a, ld, npad, nb, k, y, tmp, st);
   }
-  trsv_bwd_finish_kernel<<<1, 128, 0, s>>>(npad, nb, k, nparts, w_all, tmp, y, st);
+  trsv_bwd_finish_kernel<<<1, 256, 0, s>>>(npad, nb, k, nparts, w_all, tmp, y, st);
   return cudaGetLastError();
 }
 
@@ -169,6 +173,89 @@ cudaError_t launch_sumsq(cudaStream_t s, const double* v, int64_t n, double* par
 }
 cudaError_t launch_sum(cudaStream_t s, const double* v, int64_t n, double* partial, double* out) {
   return launch_reduce<false>(s, v, n, partial, out);
+}
+
+}  // namespace exa
+
+namespace exa {
+
+// y = S x for symmetric S stored as its lower triangle (column-major, ld), in
+// two deterministic passes that each stream the triangle once:
+//   pass 1 (thread per row i):  y_i  = sum_{j <= i} S_ij x_j
+//   pass 2 (warp per column i): y_i += sum_{j > i}  S_ji x_j
+__global__ void __launch_bounds__(256) symv_lower_rows_kernel(const double* __restrict__ s, int64_t ld, int64_t n,
+                                                              const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t j = 0; j <= i; ++j) acc = fma(s[i + j * ld], x[j], acc);
+  y[i] = acc;
+}
+
+__global__ void __launch_bounds__(256) symv_lower_cols_kernel(const double* __restrict__ s, int64_t ld, int64_t n,
+                                                              const double* __restrict__ x, double* __restrict__ y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + warp;
+  if (i >= n) return;
+  const double* col = s + i * ld;
+  double acc = 0.0;
+  for (int64_t j = i + 1 + lane; j < n; j += 32) acc = fma(col[j], x[j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[i] += acc;
+}
+
+// r = z - y ; elementwise helpers
+__global__ void residual_kernel(const double* __restrict__ z, const double* __restrict__ y, double* __restrict__ r,
+                                int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = z[i] - y[i];
+}
+
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], y[i]);
+}
+
+__global__ void __launch_bounds__(kRedThreads) dot_stage1(const double* __restrict__ a, const double* __restrict__ b,
+                                                          int64_t n, int64_t chunk, double* __restrict__ partial) {
+  __shared__ double sh[kRedThreads];
+  const int64_t start = (int64_t)blockIdx.x * chunk;
+  int64_t end = start + chunk;
+  if (end > n) end = n;
+  double s = 0.0;
+  for (int64_t i = start + threadIdx.x; i < end; i += kRedThreads) s = fma(a[i], b[i], s);
+  const double r = block_reduce(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y) {
+  symv_lower_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, ld, n, x, y);
+  symv_lower_cols_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(a, ld, n, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(cudaStream_t s, const double* z, const double* y, double* r, int64_t n) {
+  residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, y, r, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(cudaStream_t s, double a, const double* x, double* y, int64_t n) {
+  axpy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t n, double* partial, double* out) {
+  int64_t chunk = 4096;
+  int64_t blocks = (n + chunk - 1) / chunk;
+  if (blocks > kRedMaxBlocks) {
+    chunk = (n + kRedMaxBlocks - 1) / kRedMaxBlocks;
+    blocks = (n + chunk - 1) / chunk;
+  }
+  if (blocks < 1) blocks = 1;
+  dot_stage1<<<(unsigned)blocks, kRedThreads, 0, s>>>(a, b, n, chunk, partial);
+  reduce_stage2<<<1, kRedThreads, 0, s>>>(partial, (int)blocks, out);
+  return cudaGetLastError();
 }
 
 }  // namespace exa

@@ -1,0 +1,149 @@
+"""Mixed-precision path (MP variant of Section II-A, Fig. 1(d)) against the FP64 oracle.
+
+Stated bound: |dl|/|l| <= 1e-6 (the accuracy the mixed form must keep); the
+quadratic form is refined in FP64 to a relative residual below 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_06936_gb300 import synth
+from gpu_util import to_dev, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1908_06936_gb300 as exa
+
+    c = exa.Context()
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("m,theta", [(40, (1.0, 0.1, 0.5)), (50, (1.0, 0.18, 1.0)), (80, (1.0, 0.1125, 1.0)),
+                                     (37, (1.5, 0.2, 1.5)), (60, (1.0, 0.03, 1.0))])
+def test_mixed_vs_oracle(ctx, m, theta):
+    import paper_1908_06936_gb300 as exa
+
+    locs, Z = workload(m, seed=m, theta0=theta)
+    ref = oracle.loglik(locs, Z, theta)
+    got = ctx.loglik_ex(to_dev(locs), to_dev(Z), theta, exa.EXA_MIXED_TF32X3)
+    rel = abs(got["loglik"] - ref["l"]) / abs(ref["l"])
+    print("m=%d theta=%s |dl|/|l|=%.3e ir_iters=%d ir_resid=%.2e" % (m, theta, rel, got["ir_iters"], got["ir_resid"]))
+    assert rel <= 1e-6
+    assert got["ir_resid"] <= 1e-11
+    assert 1 <= got["exact_band"] <= got["n_tiles"]
+    # the refined quadratic form is accurate far beyond the factor's precision
+    assert abs(got["quad"] - ref["quad"]) <= 1e-9 * abs(ref["quad"])
+
+
+def test_mixed_matches_gpu_fp64(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    locs, Z = workload(64, seed=3, theta0=(1.0, 0.1, 0.5))
+    dl, dz = to_dev(locs), to_dev(Z)
+    for th in [(1.0, 0.1, 0.5), (0.8, 0.07, 0.9)]:
+        f = ctx.loglik_ex(dl, dz, th, exa.EXA_FP64)
+        mx = ctx.loglik_ex(dl, dz, th, exa.EXA_MIXED_TF32X3)
+        assert abs(mx["loglik"] - f["loglik"]) <= 1e-6 * abs(f["loglik"])
+
+
+def test_mixed_power_of_two_scaling_is_exact(ctx):
+    # sigma^2 = 4 scales every stored value by 4 and every factor entry by 2 exactly, so
+    # log|Sigma| shifts by n ln 4 and the quadratic form divides by 4, both to rounding
+    import paper_1908_06936_gb300 as exa
+
+    locs, Z = workload(48, seed=4, theta0=(1.0, 0.1, 1.0))
+    dl, dz = to_dev(locs), to_dev(Z)
+    n = locs.shape[0]
+    a = ctx.loglik_ex(dl, dz, (1.0, 0.1, 1.0), exa.EXA_MIXED_TF32X3)
+    b = ctx.loglik_ex(dl, dz, (4.0, 0.1, 1.0), exa.EXA_MIXED_TF32X3)
+    assert abs(b["logdet"] - (a["logdet"] + n * math.log(4.0))) <= 1e-12 * abs(a["logdet"]) + 1e-9
+    assert abs(b["quad"] - a["quad"] / 4.0) <= 1e-11 * a["quad"]
+
+
+def test_mixed_independence_limit(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    locs = synth.jittered_grid(40, seed=3)
+    Z = synth.normals(1600, 3)
+    s2 = 1.7
+    got = ctx.loglik(to_dev(locs), to_dev(Z), (s2, 1e-4, 1.0), exa.EXA_MIXED_TF32X3)
+    ref = -800 * math.log(2 * math.pi * s2) - float(Z @ Z) / (2 * s2)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+
+
+def test_mixed_tiny_and_ragged(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    for m, cut in [(1, 0), (5, 3), (16, 1), (17, 0)]:
+        locs = synth.jittered_grid(m, seed=m)[: m * m - cut]
+        Z = synth.normals(m * m, seed=m)[: m * m - cut]
+        ref = oracle.loglik(locs, Z, (1.0, 0.1, 0.5))["l"]
+        got = ctx.loglik(to_dev(locs), to_dev(Z), (1.0, 0.1, 0.5), exa.EXA_MIXED_TF32X3)
+        assert abs(got - ref) <= 1e-6 * abs(ref)
+
+
+def test_mixed_not_spd(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    locs = synth.jittered_grid(30, seed=1)
+    locs[611, 0] = float("nan")
+    with pytest.raises(exa.ExaError) as ei:
+        ctx.loglik(to_dev(locs), to_dev(synth.normals(900, 1)), (1.0, 0.1, 0.5), exa.EXA_MIXED_TF32X3)
+    assert ei.value.status == exa.EXA_ERR_NOT_SPD
+
+
+def test_bf16x3_is_refused_with_reason(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    locs, Z = workload(8, seed=1)
+    with pytest.raises(exa.ExaError) as ei:
+        ctx.loglik(to_dev(locs), to_dev(Z), (1.0, 0.1, 0.5), exa.EXA_MIXED_BF16X3)
+    assert ei.value.status == exa.EXA_ERR_ARG and "3e-4" in str(ei.value)
+
+
+def test_mixed_simulate_close_to_oracle(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    locs = synth.jittered_grid(20, seed=5)
+    eps = synth.normals(400, 5)
+    th = (1.0, 0.1, 0.5)
+    ref = oracle.simulate(locs, th, eps)
+    got = ctx.simulate(to_dev(locs), to_dev(eps), th, exa.EXA_MIXED_TF32X3).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_mixed_all_exact_is_fp64_grade(ctx):
+    # every tile through the exact digit-slice products: error far below the TF32x3 tiles
+    import paper_1908_06936_gb300 as exa
+
+    locs, Z = workload(37, seed=37, theta0=(1.5, 0.2, 1.5))
+    ref = oracle.loglik(locs, Z, (1.5, 0.2, 1.5))
+    exa.exa_ctx_set_mixed_band(ctx.handle, -1)
+    try:
+        got = ctx.loglik_ex(to_dev(locs), to_dev(Z), (1.5, 0.2, 1.5), exa.EXA_MIXED_TF32X3)
+    finally:
+        exa.exa_ctx_set_mixed_band(ctx.handle, 0)
+    assert got["exact_band"] == got["n_tiles"]
+    assert abs(got["loglik"] - ref["l"]) <= 1e-8 * abs(ref["l"])
+
+
+def test_mixed_ill_conditioned_reports_nonconvergence_or_is_accurate(ctx):
+    # a very smooth, long-range field: either the refinement converges (and l is accurate)
+    # or the library says it did not; it never returns a silently wrong value
+    import paper_1908_06936_gb300 as exa
+
+    m, th = 60, (1.5, 0.2, 1.5)
+    locs, Z = workload(m, seed=2, theta0=th)
+    ref = oracle.loglik(locs, Z, th)
+    try:
+        got = ctx.loglik_ex(to_dev(locs), to_dev(Z), th, exa.EXA_MIXED_TF32X3)
+    except exa.ExaError as e:
+        assert e.status == exa.EXA_ERR_IR_NOCONV
+        return
+    assert abs(got["loglik"] - ref["l"]) <= 1e-6 * abs(ref["l"])
