@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact Matérn Gaussian log-likelihood on GB300.
+
+Metric: log-likelihood evaluations per second and Cholesky TFLOP/s at n = 90,000
+(300 x 300 jittered grid on the unit square, theta0 = (sigma^2, beta, nu) =
+(1, 0.03, 1.0)), mixed precision (the headline `value`) next to FP64, with the
+mixed result's |dl|/|l| against the FP64 evaluation at the same theta.
+
+One step = one full evaluation of l(theta) (Matérn generation, Cholesky,
+log-determinant, solve and refinement) on inputs already resident in HBM.
+Multi-GPU runs are independent replicas (weak scaling): each rank evaluates its
+own field; `value` is the evaluations of all ranks over the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--m 300] [--fp64-steps 1] [--prec tf32x3]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "log-lik evals/s and Cholesky TFLOP/s at n=90K: FP64 vs mixed-precision at |dl|/|l|<=1e-6"
+THETA0 = (1.0, 0.03, 1.0)
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}  # dense TFLOP/s, for the dtype ratios
+
+
+def peaks() -> dict:
+    """Measured denominators (MEASURED_PEAKS.json), else the recipe's fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        src = "measured"
+    else:
+        d = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+        src = "fallback"
+    bf = d.get("bf16_tflops_sustained", d["bf16_tflops"])
+    return {"hbm_gbs": d["hbm_gbs"], "bf16": bf, "tf32": bf * NOMINAL["tf32"] / NOMINAL["bf16"],
+            "fp64": d["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], "source": src}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str | None):
+        self.proc = None
+        self.dev_id = dev_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.dev_id:
+            cmd += ["-i", self.dev_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gpu_id_for_smi() -> str | None:
+    import torch
+
+    if torch.cuda.device_count() == 1 and not os.environ.get("CUDA_VISIBLE_DEVICES"):
+        return None
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[0] if vis and vis.split(",")[0].isdigit() else None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(locs, Z, n_s: int) -> dict:
+    """Time the FP64 oracle on the first n_s locations of the workload."""
+    import oracle
+
+    t0 = time.perf_counter()
+    r = oracle.loglik(locs[:n_s], Z[:n_s], THETA0)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "l": r["l"], "threads": oracle.max_threads()}
+
+
+def cpu_baseline_entry(n: int, n_s: int, dt: float, threads: int) -> dict:
+    evals = 1.0 / (dt * (n / n_s) ** 3)
+    return {"value": evals, "unit": "evals/s", "cores": threads, "kind": "oracle",
+            "sample": "oracle log-likelihood of the first %d of the %d locations (%d grid rows of the same field), "
+                      "%.2f s on %d threads; scaled to n=%d by (n/n_s)^3 (Cholesky-dominated)"
+                      % (n_s, n, n_s // int(math.isqrt(n)), dt, threads, n)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_inputs(m: int, seed: int):
+    import numpy as np
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+
+    n = m * m
+    locs = synth.jittered_grid(m, seed)
+    eps = synth.normals(n, seed)
+    dl = torch.as_tensor(locs, device="cuda")
+    de = torch.as_tensor(eps, device="cuda")
+    with exa.Context() as c:  # exact realisation Z = L eps from the mixed factor (data, not the timed quantity)
+        dz = c.simulate(dl, de, THETA0, exa.EXA_MIXED_TF32X3)
+    torch.cuda.synchronize()
+    return locs, dl, dz, np.ascontiguousarray(dz.cpu().numpy())
+
+
+def roofline(stats: list, pk: dict) -> dict:
+    dom = max(stats, key=lambda s: s["ms"]) if stats else None
+    if not dom or dom["timed_launches"] == 0 or dom["ms"] <= 0:
+        return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
+    avg_ms = dom["ms"] / dom["timed_launches"]
+    name = dom["name"]
+    if name in ("gemm_tf32x3_tc",):
+        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+        peak = pk["tf32"]
+        bound, unit, note = "tensor", "TFLOP/s", "useful flops vs tf32 peak (3 tf32 MMAs per useful product)"
+    elif name in ("gemm_ozaki_tc",):
+        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+        peak = pk["bf16"]
+        bound, unit, note = "tensor", "TFLOP/s", "useful flops vs bf16 peak (15 bf16 MMAs per useful product)"
+    elif name in ("syrk_update_fp64", "trsm_panel_fp64", "potrf_diag_fp64", "dgemm_small_fp64"):
+        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+        peak = pk["fp64"]
+        bound, unit, note = "tensor", "TFLOP/s", "FP64 DMMA"
+    else:
+        ach = dom["bytes"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e9
+        peak = pk["hbm_gbs"]
+        bound, unit, note = "hbm", "GB/s", "algorithmic bytes vs measured copy bandwidth"
+    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "avg_launch_ms": avg_ms, "launches": dom["timed_launches"],
+            "peak_source": pk["source"], "note": note}
+
+
+def run_ours(args, rank: int, world: int) -> dict | None:
+    import numpy as np
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    prec = exa.PREC[args.prec]
+    m = args.m
+    n = m * m
+    locs, dl, dz, z_host = make_inputs(m, seed=rank)
+    ctx = exa.Context()
+    # warm-up
+    for _ in range(args.warmup):
+        ctx.loglik_ex(dl, dz, THETA0, prec)
+    torch.cuda.synchronize()
+    exa.exa_profile_read(ctx.handle, reset=1)
+    exa.exa_profile_enable(ctx.handle, 1)
+    clocks = ClockSampler(gpu_id_for_smi())
+    clocks.start()
+    time.sleep(0.5)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    res = None
+    for _ in range(args.steps):
+        res = ctx.loglik_ex(dl, dz, THETA0, prec)
+    e1.record(s)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    stats = exa.exa_profile_read(ctx.handle, reset=1)
+    exa.exa_profile_enable(ctx.handle, 0)
+    t = torch.tensor([ms_total], device="cuda")
+    if dist:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+    launches = int(sum(st["launches"] for st in stats))
+
+    # end to end through the C ABI: pinned host inputs copied in every step, result read back
+    h_locs = torch.as_tensor(locs).pin_memory()
+    h_z = torch.as_tensor(z_host).pin_memory()
+    d_locs2 = torch.empty_like(dl)
+    d_z2 = torch.empty_like(dz)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e2.record(s)
+    for _ in range(e2e_steps):
+        d_locs2.copy_(h_locs, non_blocking=True)
+        d_z2.copy_(h_z, non_blocking=True)
+        l_val = ctx.loglik(d_locs2, d_z2, THETA0, prec)  # the library returns l to the host
+    e3.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / e2e_steps
+    e2e = {"value": world / (e2e_ms / 1e3), "unit": "evals/s", "h2d_bytes_per_step": int(h_locs.numel() * 8 + h_z.numel() * 8),
+           "d2h_bytes_per_step": 8, "steps": e2e_steps}
+
+    out = None
+    if rank == 0:
+        chol_tflops = (n ** 3 / 3.0) / (res["ms_chol"] * 1e-3) / 1e12
+        fp64 = None
+        if args.fp64_steps > 0:
+            ms, rr = [], None
+            for _ in range(args.fp64_steps):
+                rr = ctx.loglik_ex(dl, dz, THETA0, exa.EXA_FP64)
+                ms.append(rr["ms_total"])
+            fp64 = {"evals_per_s": 1e3 / statistics.mean(ms), "ms_per_eval": statistics.mean(ms),
+                    "chol_ms": rr["ms_chol"], "chol_tflops": (n ** 3 / 3.0) / (rr["ms_chol"] * 1e-3) / 1e12,
+                    "chol_frac_of_fp64_peak": (n ** 3 / 3.0) / (rr["ms_chol"] * 1e-3) / 1e12 / peaks()["fp64"],
+                    "loglik": rr["loglik"], "steps": args.fp64_steps, "warmup": 0}
+        pk = peaks()
+        rl = roofline(stats, pk)
+        # CPU oracle baseline on a bounded sample of the same field
+        n_s = args.cpu_sample
+        cs = oracle_sample(locs, z_host, n_s)
+        out = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+tf32x3", "data": "synthetic",
+            "config": {"workload": "n=%d (%dx%d jittered grid on [0,1]^2), theta0=(1, 0.03, 1.0), %s Cholesky with exact "
+                                   "band + FP64 refinement; FP64 leg at the same n" % (n, m, m, args.prec),
+                       "n": n, "theta0": list(THETA0), "prec": args.prec,
+                       "l2": "working set %.0f GB >> 129 MB L2 (no flush needed)" % (2 * 8 * n * n / 1e9)},
+            "mixed": {"evals_per_s": value / world, "chol_tflops": chol_tflops, "ms_gen": res["ms_gen"],
+                      "ms_chol": res["ms_chol"], "ms_solve": res["ms_solve"], "ir_iters": res["ir_iters"],
+                      "ir_resid": res["ir_resid"], "exact_band": res["exact_band"], "n_tiles": res["n_tiles"],
+                      "loglik": res["loglik"]},
+            "fp64": fp64,
+            "rel_dl_vs_fp64": (abs(res["loglik"] - fp64["loglik"]) / abs(fp64["loglik"])) if fp64 else None,
+            "speedup_mixed_vs_fp64": (fp64["ms_per_eval"] / (ms_max / args.steps)) if fp64 else None,
+            "roofline": rl,
+            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()} for st in stats],
+            "cpu_baseline": cpu_baseline_entry(n, n_s, cs["seconds"], cs["threads"]),
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+    ctx.close()
+    return out
+
+
+def run_reference(args) -> dict:
+    """The FP64 CPU oracle on the host cores, on a bounded sample of the same workload."""
+    import oracle
+    from paper_1908_06936_gb300 import synth
+
+    m = args.m
+    n = m * m
+    n_s = args.ref_sample
+    locs = synth.jittered_grid(m, 0)
+    # observations of the sample: an exact realisation on the sample's own locations
+    z = oracle.simulate(locs[:n_s], THETA0, synth.normals(n, 0)[:n_s])
+    for _ in range(args.warmup):
+        oracle.loglik(locs[:n_s], z, THETA0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.loglik(locs[:n_s], z, THETA0)
+    dt = (time.perf_counter() - t0) / args.steps
+    cb = cpu_baseline_entry(n, n_s, dt, oracle.max_threads())
+    v = cb["value"]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * (n / n_s) ** 3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n=%d (%dx%d jittered grid), theta0=(1, 0.03, 1.0); FP64 CPU oracle on a "
+                                   "%d-location sample scaled by (n/n_s)^3" % (n, m, m, n_s), "n": n},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=300, help="grid side (n = m^2)")
+    ap.add_argument("--prec", choices=["tf32x3"], default="tf32x3")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 evaluations at the same n (0 to skip)")
+    ap.add_argument("--cpu-sample", type=int, default=3600, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=2500, help="oracle sample size per reference step")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1908_06936_gb300 import build as exa_build
+
+    if rank == 0:
+        exa_build.build()
+    if world > 1:
+        tdist.barrier()
+    out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

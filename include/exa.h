@@ -174,6 +174,22 @@ typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1 } exa_gemm_kind;
 exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
                            const double* d_b, double* d_c, int64_t ldc, int store);
 
+/* Kernel accounting.  Launch counts and the algorithmic flops / bytes of every
+ * kernel class are always accumulated; with profiling enabled each launch is
+ * also bracketed by CUDA events on the context stream (adds ~2 us per launch). */
+typedef struct {
+  char name[32];          /* kernel class */
+  int64_t launches;       /* kernels launched */
+  int64_t timed_launches; /* launch groups timed with events */
+  double ms;              /* summed device time of the timed launches */
+  double flops;           /* algorithmic flops (useful multiply-adds x 2) */
+  double bytes;           /* algorithmic DRAM bytes (compulsory reads + writes) */
+} exa_kernel_stat;
+exa_status exa_profile_enable(exa_ctx* ctx, int on);
+/* Copy up to max per-class records into out (host); returns how many.  Waits
+ * for pending timed launches.  reset != 0 zeroes the accumulators.         */
+int exa_profile_read(exa_ctx* ctx, exa_kernel_stat* out, int max, int reset);
+
 /* Exact synthetic realisation (Section III, Example 1, simulate_obs_exact):
  * d_z = L d_eps with L L^T = Sigma(theta), both n FP64 device vectors.       */
 exa_status exa_simulate(exa_ctx* ctx, const double* d_locs, const double* d_eps, const double theta[3], int64_t n,

@@ -19,7 +19,8 @@ __all__ = [
     "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
-    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_profile_enable",
+    "exa_profile_read", "KernelStat", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -38,6 +39,11 @@ class ExaError(RuntimeError):
         super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
         self.status = status
         self.pivot = pivot
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class ExaResult(ctypes.Structure):
@@ -82,6 +88,8 @@ def lib() -> ctypes.CDLL:
                                                       ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P]),
                 "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
                 "exa_ctx_set_mixed_band": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
             }
@@ -256,3 +264,14 @@ def exa_simulate(ctx: int, locs, eps, theta, n: int, prec: int, z) -> int:
 def exa_gemm_update(ctx: int, kind: int, m: int, n: int, k: int, a, b, c, ldc: int, store: int) -> int:
     return lib().exa_gemm_update(_P(ctx), int(kind), m, n, k, _P(_dev_ptr(a, "a", m * k)), _P(_dev_ptr(b, "b", n * k)),
                                  _P(_dev_ptr(c, "c")), ldc, int(store))
+
+
+def exa_profile_enable(ctx: int, on: int) -> int:
+    return lib().exa_profile_enable(_P(ctx), int(on))
+
+
+def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
+    buf = (KernelStat * 32)()
+    k = lib().exa_profile_read(_P(ctx), buf, 32, int(reset))
+    return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "timed_launches": buf[i].timed_launches,
+             "ms": buf[i].ms, "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(k)]

@@ -95,9 +95,20 @@ exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb) 
   for (int k = 0; k < T; ++k) {
     const int64_t k0 = (int64_t)k * nb;
     const int64_t m = npad - k0 - nb;
-    cudaError_t e = launch_potrf_diag(c->stream, a, ld, k0, nb, W, LD, c->d_status);
-    if (e == cudaSuccess) e = launch_trsm_panel(c->stream, a, ld, k0, nb, m, W, P, c->d_status);
-    if (e == cudaSuccess) e = launch_syrk_update(c->stream, a, ld, k0 + nb, m, nb, P, c->d_status);
+    const double dnb = nb, dm = (double)m;
+    cudaError_t e;
+    {
+      ProfScope ps(c, PK_POTRF, dnb * dnb * dnb, 24.0 * dnb * dnb);
+      e = launch_potrf_diag(c->stream, a, ld, k0, nb, W, LD, c->d_status);
+    }
+    if (e == cudaSuccess && m > 0) {
+      ProfScope ps(c, PK_TRSM64, 2.0 * dm * dnb * dnb, 24.0 * dm * dnb);
+      e = launch_trsm_panel(c->stream, a, ld, k0, nb, m, W, P, c->d_status);
+    }
+    if (e == cudaSuccess && m > 0) {
+      ProfScope ps(c, PK_SYRK64, dm * (dm + 64.0) * dnb, 8.0 * dm * (dm + 64.0) + 8.0 * dm * dnb);
+      e = launch_syrk_update(c->stream, a, ld, k0 + nb, m, nb, P, c->d_status);
+    }
     if (e != cudaSuccess) return cuda_err(c, e, "cholesky launch");
   }
   return EXA_OK;
@@ -165,6 +176,7 @@ void exa_ctx_destroy(exa_ctx* c) {
   free_buf(c, c->vec);
   free_buf(c, c->partial);
   release_extra(c);
+  prof_release(c);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalars) cudaFree(c->d_scalars);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -279,16 +291,29 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
   MaternParams P;
   matern_params(theta, &P);
   cudaEventRecord(c->ev[0], c->stream);
-  cudaError_t e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
+  cudaError_t e;
+  {
+    ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
+    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
+  }
   if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
   cudaEventRecord(c->ev[1], c->stream);
   if ((st = factor_fp64(c, A, npad, npad, nb)) != EXA_OK) return st;
   cudaEventRecord(c->ev[2], c->stream);
-  e = launch_pad_vector(c->stream, d_z, n, npad, zw);
-  for (int k = 0; k < T && e == cudaSuccess; ++k)
+  {
+    ProfScope ps(c, PK_OTHER, 0.0, 16.0 * (double)npad);
+    e = launch_pad_vector(c->stream, d_z, n, npad, zw);
+  }
+  for (int k = 0; k < T && e == cudaSuccess; ++k) {
+    ProfScope ps(c, PK_TRSV, 2.0 * (double)(npad - (int64_t)k * nb) * nb, 8.0 * (double)(npad - (int64_t)k * nb) * nb);
     e = launch_trsv_fwd_step(c->stream, A, npad, npad, nb, k, (const double*)c->w_all.p, y, zw, c->d_status);
-  if (e == cudaSuccess) e = launch_sumsq(c->stream, y, npad, part, c->d_scalars + 0);
-  if (e == cudaSuccess) e = launch_sum(c->stream, (const double*)c->logdet_part.p, T, part + kRedPartials, c->d_scalars + 1);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_OTHER, 0.0, 8.0 * (double)npad, 4);
+    e = launch_sumsq(c->stream, y, npad, part, c->d_scalars + 0);
+    if (e == cudaSuccess)
+      e = launch_sum(c->stream, (const double*)c->logdet_part.p, T, part + kRedPartials, c->d_scalars + 1);
+  }
   if (e != cudaSuccess) return cuda_err(c, e, "solve launch");
   cudaEventRecord(c->ev[3], c->stream);
   e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -62,10 +62,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
     for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i * sd + j] *= inv;
     __syncthreads();
     if (tid == 0) S[j * sd + j] = lj;
-    const int m = nb - j - 1;
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {
-      const int i = j + 1 + idx % m, l = j + 1 + idx / m;
-      if (l <= i) S[i * sd + l] = fma(-S[i * sd + j], S[l * sd + j], S[i * sd + l]);
+    // rank-1 update of the trailing lower triangle: thread -> column l, rows i >= l
+    // split between the blockDim / nb threads sharing that column
+    {
+      const int per = blockDim.x / nb;          // threads per column (2 for nb = 128)
+      const int l = tid % nb, i0 = tid / nb;
+      if (l > j) {
+        const double slj = S[l * sd + j];
+        for (int i = l + i0; i < nb; i += per) S[i * sd + l] = fma(-S[i * sd + j], slj, S[i * sd + l]);
+      }
     }
     __syncthreads();
   }

@@ -5,6 +5,7 @@
 
 #include "exa_internal.cuh"
 #include "gemm_tc.cuh"
+#include "prof.cuh"
 
 namespace exa {
 
@@ -54,6 +55,7 @@ struct exa_ctx {
   double* d_scalars = nullptr;
   double* h_scalars = nullptr;          // pinned
   cudaEvent_t ev[exa::kNumEvents] = {};
+  exa::Prof prof;
 };
 
 namespace exa {

@@ -79,6 +79,9 @@ __device__ __forceinline__ void record_timeout(DevStatus* st, int site) {
 // ===========================================================================
 // T3 kernel: tile 128 x 128, K chunks of 32 FP32 (TF32) values, 3 stages.
 // ===========================================================================
+constexpr int kEpiThreads = 256;                 // 8 epilogue warps
+constexpr int kGemmThreads = 64 + kEpiThreads;   // + TMA producer warp + MMA warp
+
 namespace t3 {
 constexpr int TM = 128, TN = 128, KC = 32, STAGES = 3;
 constexpr int OP_BYTES = TM * KC * 4;           // 16 KB per operand tile
@@ -88,7 +91,7 @@ constexpr uint32_t IDESC = idesc(kFmtTF32, TM, TN);
 constexpr int TMEM_COLS = 256;                  // 2 accumulator buffers x 128 columns
 }  // namespace t3
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kGemmThreads)
     gemm_t3_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                    const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
                    const __grid_constant__ GemmArgs g) {
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
-      mbar_init(&accempty[b], 128);
+      mbar_init(&accempty[b], kEpiThreads);
     }
     *abort = 0;
     fence_barrier_init();
@@ -210,7 +213,9 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> FP64 C ----------------
-    const int quad = warp & 3;  // TMEM lanes 32*quad .. 32*quad+31
+    // 8 warps: warp w drains TMEM lanes 32*(w%4).. (its row quarter) and column half (w-2)/4
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = quad * 32 + lane;
     int it = 0;
     for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
@@ -228,24 +233,29 @@ __global__ void __launch_bounds__(192, 1)
       const int64_t col0 = g.c_col0 + (int64_t)bj * TN;
       const bool diag = g.lower_mask && (bi == bj);
       double* cp = g.C + row + col0 * g.ldc;
+      // two rounds of 32 C loads in flight per thread (64 KB per SM), then drain TMEM
 #pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
-        uint32_t acc[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + b * TN + c * 32, acc);
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int cb = half * 64 + h2 * 32;
         double cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(c * 32 + j) * g.ldc];
-        tmem_ld_wait();
-        if (c == 3) {
-          fence_before();
-          mbar_arrive(&accempty[b]);
-        }
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(cb + j) * g.ldc];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int cc = c * 32 + j;
-          if (diag && cc > r) continue;
-          const double v = (double)__uint_as_float(acc[j]);
-          cp[(int64_t)cc * g.ldc] = g.store ? v : cv[j] - v;
+        for (int c = 0; c < 2; ++c) {
+          uint32_t acc[16];
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * TN + cb + c * 16, acc);
+          tmem_ld_wait();
+          if (h2 == 1 && c == 1) {
+            fence_before();
+            mbar_arrive(&accempty[b]);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int cc = cb + c * 16 + j;
+            if (diag && cc > r) continue;
+            const double v = (double)__uint_as_float(acc[j]);
+            cp[(int64_t)cc * g.ldc] = g.store ? v : cv[c * 16 + j] - v;
+          }
         }
       }
       ++it;
@@ -274,7 +284,7 @@ constexpr int BUF_COLS = S * GROUP_COLS;
 constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a power of two
 }  // namespace oz
 
-__global__ void __launch_bounds__(192, 1) gemm_oz_kernel(const __grid_constant__ OzMaps ta,
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_constant__ OzMaps ta,
                                                          const __grid_constant__ OzMaps tb,
                                                          const __grid_constant__ GemmArgs g) {
   using namespace oz;
@@ -295,7 +305,7 @@ __global__ void __launch_bounds__(192, 1) gemm_oz_kernel(const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
-      mbar_init(&accempty[b], 128);
+      mbar_init(&accempty[b], kEpiThreads);
     }
     *abort = 0;
     fence_barrier_init();
@@ -399,6 +409,7 @@ __global__ void __launch_bounds__(192, 1) gemm_oz_kernel(const __grid_constant__
     }
   } else if (warp >= 2) {
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;  // columns [16*half, 16*half + 16)
     const int r = quad * 32 + lane;
     int it = 0;
     for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
@@ -412,32 +423,32 @@ __global__ void __launch_bounds__(192, 1) gemm_oz_kernel(const __grid_constant__
         break;
       }
       fence_after();
-      double v[32];
+      const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
+      const int64_t col0 = g.c_col0 + (int64_t)bj * TN + 16 * half;
+      double* cp = g.C + row + col0 * g.ldc;
+      double cv[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = 0.0;
+      for (int j = 0; j < 16; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)j * g.ldc];
+      double v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.0;
 #pragma unroll
       for (int gs = S - 1; gs >= 0; --gs) {  // smallest group first
-        uint32_t acc[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS, acc);
+        uint32_t acc[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS + 16 * half, acc);
         tmem_ld_wait();
         const double sc = ldexp(1.0, -7 * (gs + 2));
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fma((double)__uint_as_float(acc[j]), sc, v[j]);
+        for (int j = 0; j < 16; ++j) v[j] = fma((double)__uint_as_float(acc[j]), sc, v[j]);
       }
       fence_before();
       mbar_arrive(&accempty[b]);
-      const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
-      const int64_t col0 = g.c_col0 + (int64_t)bj * TN;
       const int er = g.ea[g.a_row0 + bi * TM + r];
       const bool lower = g.lower_mask != 0;
-      double* cp = g.C + row + col0 * g.ldc;
-      double cv[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)j * g.ldc];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < 16; ++j) {
         if (lower && col0 + j > row) continue;
-        const int ec = g.eb[g.b_row0 + bj * TN + j];
+        const int ec = g.eb[g.b_row0 + bj * TN + 16 * half + j];
         const double x = ldexp(v[j], er + ec);
         cp[(int64_t)j * g.ldc] = g.store ? x : cv[j] - x;
       }
@@ -497,6 +508,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
       frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |a| 2^-e <= 1
     }
     if (lane == 0 && ex) ex[orow] = e;
+    const double sc = ldexp(1.0, 35 - e);
     for (int k = lane; k < K; k += 32) {
       const double a = tile[rr * ld + k];
       if (hi) {
@@ -506,16 +518,23 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
         lo[orow * K + k] = l;
       }
       if (dig) {
-        double x = ldexp(a, -e);
+        // N = round(a 2^(35-e)), |N| <= 2^35; balanced base-128 digits from the least
+        // significant end: d = ((N + 64) mod 128) - 64, N = (N - d) / 128.  The leading
+        // digit keeps the rest (|d_0| <= 128, |d_s| <= 64 otherwise); all exact in BF16.
+        long long N = llrint(a * sc);
+        short d[kOzSlices];
 #pragma unroll
-        for (int s = 0; s < kOzSlices; ++s) {
-          const double d = rint(ldexp(x, 7 * (s + 1)));
-          x -= ldexp(d, -7 * (s + 1));
-          // |d| <= 128: exactly representable in BF16 (8-bit significand)
-          const float df = (float)d;
+        for (int s2 = kOzSlices - 1; s2 >= 1; --s2) {
+          const long long q = ((N + 64) & 127) - 64;
+          d[s2] = (short)q;
+          N = (N - q) >> 7;
+        }
+        d[0] = (short)N;
+#pragma unroll
+        for (int s2 = 0; s2 < kOzSlices; ++s2) {
           __nv_bfloat16_raw raw;
-          raw.x = (unsigned short)(__float_as_uint(df) >> 16);
-          dig[(int64_t)s * dig_stride + orow * K + k] = raw;
+          raw.x = (unsigned short)(__float_as_uint((float)d[s2]) >> 16);
+          dig[(int64_t)s2 * dig_stride + orow * K + k] = raw;
         }
       }
     }
@@ -610,7 +629,7 @@ cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOpe
     attr = true;
   }
   const int grid = (int)(g.ntiles < num_sms() ? g.ntiles : num_sms());
-  gemm_t3_kernel<<<grid, 192, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
+  gemm_t3_kernel<<<grid, kGemmThreads, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
   return cudaGetLastError();
 }
 
@@ -627,7 +646,7 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
   GemmArgs g2 = g;
   g2.ea = A.ex;
   g2.eb = B.ex;
-  gemm_oz_kernel<<<grid, 192, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
+  gemm_oz_kernel<<<grid, kGemmThreads, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
   return cudaGetLastError();
 }
 

@@ -76,29 +76,46 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   cudaStream_t s = c->stream;
   for (int k = 0; k < T; ++k) {
     const int64_t k0 = (int64_t)k * NB;
-    cudaError_t e = launch_potrf_diag(s, a, ld, k0, nb, W, LD, c->d_status);
-    if (e == cudaSuccess) e = launch_trsm_panel(s, a, ld, k0, nb, nb, W, P, c->d_status);
-    if (e == cudaSuccess) e = launch_syrk_update(s, a, ld, k0 + nb, nb, nb, P, c->d_status);
-    if (e == cudaSuccess) e = launch_potrf_diag(s, a, ld, k0 + nb, nb, W, LD, c->d_status);
+    const double dnb = nb;
+    cudaError_t e;
+    {
+      ProfScope ps(c, PK_POTRF, 2.0 * dnb * dnb * dnb, 48.0 * dnb * dnb, 2);
+      e = launch_potrf_diag(s, a, ld, k0, nb, W, LD, c->d_status);
+      if (e == cudaSuccess) {
+        ProfScope p2(c, PK_TRSM64, 2.0 * dnb * dnb * dnb, 24.0 * dnb * dnb);
+        e = launch_trsm_panel(s, a, ld, k0, nb, nb, W, P, c->d_status);
+      }
+      if (e == cudaSuccess) {
+        ProfScope p3(c, PK_SYRK64, dnb * (dnb + 64.0) * dnb, 16.0 * dnb * dnb);
+        e = launch_syrk_update(s, a, ld, k0 + nb, nb, nb, P, c->d_status);
+      }
+      if (e == cudaSuccess) e = launch_potrf_diag(s, a, ld, k0 + nb, nb, W, LD, c->d_status);
+    }
     if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
     double* W2 = (double*)c->mx_w2.p + (int64_t)k * NB * NB;  // 256 x 256 inverse of the block (row-major)
     const double* w00 = W + (k0 / nb) * (int64_t)nb * nb;
     const double* w11 = w00 + (int64_t)nb * nb;
-    e = launch_assemble_w2(s, w00, w11, nb, W2);
-    // tmp = L10 W00 ;  W10 = -W11 tmp
-    if (e == cudaSuccess)
-      e = launch_dgemm_nt_small(s, nb, nb, nb, 1.0, a + (k0 + nb) + k0 * ld, 1, ld, w00, 1, nb, 0.0, tmp, nb, 1,
-                                c->d_status);
-    if (e == cudaSuccess)
-      e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, w11, nb, 1, tmp, 1, nb, 0.0, W2 + (int64_t)nb * NB, NB, 1,
-                                c->d_status);
+    {
+      ProfScope ps(c, PK_DGEMM_SMALL, 4.0 * dnb * dnb * dnb, 8.0 * 8.0 * dnb * dnb, 3);
+      e = launch_assemble_w2(s, w00, w11, nb, W2);
+      // tmp = L10 W00 ;  W10 = -W11 tmp
+      if (e == cudaSuccess)
+        e = launch_dgemm_nt_small(s, nb, nb, nb, 1.0, a + (k0 + nb) + k0 * ld, 1, ld, w00, 1, nb, 0.0, tmp, nb, 1,
+                                  c->d_status);
+      if (e == cudaSuccess)
+        e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, w11, nb, 1, tmp, 1, nb, 0.0, W2 + (int64_t)nb * NB, NB, 1,
+                                  c->d_status);
+    }
     if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
     if (k == T - 1) break;
-    e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
     const int64_t r0 = k0 + NB;
     const int64_t m = npad - r0;
     double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
-    if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    {
+      ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)(m + NB) * NB, 2);
+      e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
+      if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    }
     if (e != cudaSuccess) return cuda_err(c, e, "inverse / split launch");
     // TRSM on the tensor cores: L_ik = A_ik W^T
     const int64_t rb = m < (int64_t)band * NB ? m : (int64_t)band * NB;
@@ -116,15 +133,22 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
     g.b_row0 = 0;
     g.nt = NB / 32;
     g.ntiles = (rb / 128) * g.nt;
-    e = launch_gemm_oz(s, c->sp_a, c->sp_b, g);
+    {
+      ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 8.0 * (double)rb * NB);
+      e = launch_gemm_oz(s, c->sp_a, c->sp_b, g);
+    }
     if (e == cudaSuccess && m > rb) {
       g.c_row0 = r0 + rb;
       g.a_row0 = (int)rb;
       g.nt = NB / 128;
       g.ntiles = ((m - rb) / 128) * g.nt;
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 8.0 * (double)(m - rb) * NB);
       e = launch_gemm_t3(s, c->sp_a, c->sp_b, g);
     }
-    if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    if (e == cudaSuccess) {
+      ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)m * NB);
+      e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
+    }
     if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
     // trailing update
     memset(&g, 0, sizeof(g));
@@ -139,13 +163,24 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
     const long long t128 = m / 128;
     g.enum_mode = kEnumLowerOffBand;
     g.ntiles = t128 * (t128 + 1) / 2;
-    e = launch_gemm_t3(s, c->sp_a, c->sp_a, g);
+    long long t3_tiles = 0;  // tiles this launch computes (off the band)
+    for (long long bi = 0; bi < t128; ++bi) {
+      const long long lim = 2 * (bi / 2 - band);
+      if (lim > 0) t3_tiles += lim;
+    }
+    if (t3_tiles > 0) {
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
+                   16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m * NB);
+      e = launch_gemm_t3(s, c->sp_a, c->sp_a, g);
+    }
     if (e == cudaSuccess) {
       const long long tr = m / NB;
       long long pairs = 0;
       for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
       g.enum_mode = kEnumBand;
       g.ntiles = pairs * (NB / 128) * (NB / 32);
+      const double oz_tiles = (double)pairs * 16.0 - 4.0 * (double)tr;  // diagonal pairs skip 4 sub-tiles
+      ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles);
       e = launch_gemm_oz(s, c->sp_a, c->sp_a, g);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "trailing update launch");
@@ -161,10 +196,16 @@ static cudaError_t solve_llt(exa_ctx* c, const double* a, int64_t ld, int64_t np
   const int T = (int)(npad / nb);
   const double* W = (const double*)c->mx_w2.p;
   cudaError_t e = cudaMemcpyAsync(work, rhs, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-  for (int k = 0; k < T && e == cudaSuccess; ++k)
+  for (int k = 0; k < T && e == cudaSuccess; ++k) {
+    const double rows = (double)(npad - (int64_t)k * nb);
+    ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb);
     e = launch_trsv_fwd_step(c->stream, a, ld, npad, nb, k, W, x, work, c->d_status);
-  for (int k = T - 1; k >= 0 && e == cudaSuccess; --k)
+  }
+  for (int k = T - 1; k >= 0 && e == cudaSuccess; --k) {
+    const double rows = (double)(npad - (int64_t)k * nb);
+    ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb, 2);
     e = launch_trsv_bwd_step(c->stream, a, ld, npad, nb, k, W, x, part, c->d_status);
+  }
   return e;
 }
 
@@ -185,7 +226,10 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   matern_params(theta, &Pm);
   cudaStream_t s = c->stream;
   cudaError_t e = cudaMemsetAsync(offmax, 0, (size_t)(T + 1) * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax);
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
+    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax);
+  }
   if (e == cudaSuccess && sigma_keep)
     e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_err(c, e, "generation");
@@ -267,7 +311,10 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   int it = 0;
   const int kMaxIt = 10;
   for (;; ++it) {
-    e = launch_symv_lower(s, S, npad, npad, x, y);
+    {
+      ProfScope ps(c, PK_SYMV, 2.0 * (double)npad * (double)npad, 8.0 * (double)npad * (double)(npad + 1), 2);
+      e = launch_symv_lower(s, S, npad, npad, x, y);
+    }
     if (e == cudaSuccess) e = launch_residual(s, zp, y, r, npad);
     if (e == cudaSuccess) e = launch_sumsq(s, r, npad, part, c->d_scalars + 3);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);

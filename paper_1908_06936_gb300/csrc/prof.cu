@@ -1,0 +1,105 @@
+// Launch accounting and event timing per kernel class (see prof.cuh).
+#include <string.h>
+
+#include "ctx.cuh"
+#include "prof.cuh"
+
+namespace exa {
+
+static const char* kNames[PK_COUNT] = {"matern_gen", "potrf_diag_fp64", "trsm_panel_fp64", "syrk_update_fp64",
+                                       "dgemm_small_fp64", "split_rows", "gemm_tf32x3_tc", "gemm_ozaki_tc",
+                                       "trsv", "symv_residual", "gradient", "batched_chol", "other"};
+
+const char* prof_name(int kind) { return (kind >= 0 && kind < PK_COUNT) ? kNames[kind] : "?"; }
+
+static int take_event(Prof& p) {
+  if (p.used == p.pool.size()) {
+    if (p.pool.size() >= (1u << 17)) return -1;  // bounded: stop timing, keep counting
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    p.pool.push_back(e);
+  }
+  return (int)p.used++;
+}
+
+ProfScope::ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels)
+    : c_(c), kind_(kind), flops_(flops), bytes_(bytes) {
+  Prof& p = c->prof;
+  p.launches[kind] += nkernels;
+  p.flops[kind] += flops;
+  p.bytes[kind] += bytes;
+  if (p.on) {
+    ev0_ = take_event(p);
+    if (ev0_ >= 0) cudaEventRecord(p.pool[ev0_], c->stream);
+  }
+}
+
+ProfScope::~ProfScope() {
+  Prof& p = c_->prof;
+  if (!p.on || ev0_ < 0) return;
+  const int ev1 = take_event(p);
+  if (ev1 < 0) return;
+  cudaEventRecord(p.pool[ev1], c_->stream);
+  p.recs.push_back({kind_, ev0_, ev1, flops_, bytes_});
+}
+
+void prof_collect(exa_ctx* c) {
+  Prof& p = c->prof;
+  if (p.recs.empty()) {
+    p.used = 0;
+    return;
+  }
+  cudaStreamSynchronize(c->stream);
+  for (const ProfRec& r : p.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.pool[r.ev0], p.pool[r.ev1]) == cudaSuccess) {
+      p.ms[r.kind] += ms;
+      p.timed[r.kind] += 1;
+    }
+  }
+  p.recs.clear();
+  p.used = 0;
+}
+
+void prof_release(exa_ctx* c) {
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  c->prof.pool.clear();
+  c->prof.recs.clear();
+  c->prof.used = 0;
+}
+
+}  // namespace exa
+
+using namespace exa;
+
+extern "C" exa_status exa_profile_enable(exa_ctx* c, int on) {
+  if (!c) return EXA_ERR_ARG;
+  prof_collect(c);
+  c->prof.on = on != 0;
+  return EXA_OK;
+}
+
+extern "C" int exa_profile_read(exa_ctx* c, exa_kernel_stat* out, int max, int reset) {
+  if (!c || !out || max <= 0) return 0;
+  prof_collect(c);
+  Prof& p = c->prof;
+  int k = 0;
+  for (int i = 0; i < PK_COUNT && k < max; ++i) {
+    if (p.launches[i] == 0) continue;
+    memset(&out[k], 0, sizeof(out[k]));
+    strncpy(out[k].name, kNames[i], sizeof(out[k].name) - 1);
+    out[k].launches = p.launches[i];
+    out[k].timed_launches = p.timed[i];
+    out[k].ms = p.ms[i];
+    out[k].flops = p.flops[i];
+    out[k].bytes = p.bytes[i];
+    ++k;
+  }
+  if (reset) {
+    for (int i = 0; i < PK_COUNT; ++i) {
+      p.launches[i] = p.timed[i] = 0;
+      p.flops[i] = p.bytes[i] = p.ms[i] = 0.0;
+    }
+  }
+  return k;
+}

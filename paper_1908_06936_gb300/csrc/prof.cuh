@@ -1,0 +1,66 @@
+// Per-kernel-class launch counters (always on) and optional CUDA-event timing
+// with the algorithmic flop / byte counts of each launch.
+#pragma once
+
+#include <vector>
+
+#include "exa_internal.cuh"
+
+struct exa_ctx;
+
+namespace exa {
+
+enum ProfKind : int {
+  PK_GEN = 0,       // Matérn generation (a1)
+  PK_POTRF,         // FP64 diagonal tile factorisation + inversion
+  PK_TRSM64,        // FP64 DMMA panel solve
+  PK_SYRK64,        // FP64 DMMA trailing update
+  PK_DGEMM_SMALL,   // FP64 DMMA block-inverse products
+  PK_SPLIT,         // split of FP64 rows into TF32 halves / BF16 digits
+  PK_GEMM_T3,       // tcgen05 TF32x3 products
+  PK_GEMM_OZ,       // tcgen05 exact digit-slice products
+  PK_TRSV,          // triangular solves
+  PK_SYMV,          // refinement residual
+  PK_GRAD,          // gradient kernels
+  PK_BATCH,         // batched persistent factorisation
+  PK_OTHER,         // reductions, copies, padding
+  PK_COUNT
+};
+
+const char* prof_name(int kind);
+
+struct ProfRec {
+  int kind;
+  int ev0, ev1;
+  double flops, bytes;
+};
+
+struct Prof {
+  bool on = false;
+  int64_t launches[PK_COUNT] = {};
+  double flops[PK_COUNT] = {};
+  double bytes[PK_COUNT] = {};
+  double ms[PK_COUNT] = {};
+  int64_t timed[PK_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfRec> recs;
+  size_t used = 0;
+};
+
+// Scope around the launch(es) of one kernel class on the context's stream.
+class ProfScope {
+ public:
+  ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels = 1);
+  ~ProfScope();
+
+ private:
+  exa_ctx* c_;
+  int kind_;
+  int ev0_ = -1;
+  double flops_, bytes_;
+};
+
+void prof_collect(exa_ctx* c);  // synchronises and folds pending event pairs into the totals
+void prof_release(exa_ctx* c);
+
+}  // namespace exa
