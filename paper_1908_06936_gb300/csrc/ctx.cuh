@@ -46,7 +46,8 @@ struct exa_ctx {
   exa::DevBuf mx_w2;        // inverses of the 256-wide diagonal blocks (for the solves)
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
   // gradient
-  exa::DevBuf gr_part;      // per-block gradient partials
+  exa::DevBuf gr_part;      // second n x n buffer: Sigma^-1 for the gradient trace term
+  exa::DevBuf gr_blocks;    // per-block gradient partial sums
   // batched
   exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work;
   // status and small results

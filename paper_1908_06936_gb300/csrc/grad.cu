@@ -1,0 +1,394 @@
+// Gradient of the log-likelihood (Eq. 2) with respect to theta = (sigma^2, beta, nu):
+//
+//   dl/dtheta_k = 1/2 a^T D_k a - 1/2 tr(Sigma^-1 D_k),   a = Sigma^-1 z,  D_k = dSigma/dtheta_k,
+//
+// with D_k regenerated entry by entry from Eq. 3 (never stored):
+//   D_sigma2 = Sigma / sigma^2
+//   D_beta   = sigma^2 c x^nu K_{nu-1}(x) x / beta            (d[x^nu K_nu]/dx = -x^nu K_{nu-1}, DLMF 10.29.4)
+//   D_nu     = Sigma (-ln 2 - psi(nu) + ln x) + sigma^2 c x^nu dK_nu/dnu,   c = 2^(1-nu) / Gamma(nu)
+// and all three vanishing on the diagonal except D_sigma2 = 1.
+//
+// Steps after the FP64 factorisation Sigma = L L^T (DMMA):
+//   a  = L^-T (L^-1 z)                     backward block solve
+//   X  = L^-1 in place                      block columns right to left:
+//                                           T = X22 L_panel, X_panel = -T W_j, X_jj = W_j
+//   S  = X^T X = Sigma^-1 (lower tiles)     into a second n x n buffer
+//   g  = 1/2 sum_ij w_ij (a_i a_j - S_ij) D_k,ij   (w = 1 on the diagonal, 2 below), fused
+//                                           with the regeneration of D_k, fixed-order reduction.
+#include <math.h>
+#include <string.h>
+
+#include "bessel.cuh"
+#include "ctx.cuh"
+#include "util.cuh"
+
+namespace exa {
+
+__device__ __forceinline__ void dmma884(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+constexpr int gKC = 32, gSS = 36;
+
+// T(i, c) = sum_{l = l0}^{min(i, tile end)} X(i, l) L(l, j0 + c) for rows i in [l0, npad),
+// X lower triangular (entries above its diagonal read as 0).  Output T row-major, nb wide.
+// CTA: 64 x 64 output tile, 4 warps of 32 x 32.
+__global__ void __launch_bounds__(128) trmm_lower_panel_kernel(const double* __restrict__ a, int64_t ld, int64_t l0,
+                                                               int64_t j0, int nb, double* __restrict__ tout,
+                                                               const DevStatus* st) {
+  __shared__ double As[64 * gSS];
+  __shared__ double Bs[64 * gSS];
+  if (*(volatile const int32_t*)&st->info) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3, wm = warp >> 1, wn = warp & 1;
+  const int64_t i0 = l0 + (int64_t)blockIdx.y * 64;  // output rows [i0, i0 + 64)
+  const int c0 = blockIdx.x * 64;                      // output cols [c0, c0 + 64)
+  double acc[4][4][2];
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+  for (int64_t k0 = l0; k0 < i0 + 64; k0 += gKC) {
+    for (int idx = tid; idx < 64 * gKC; idx += blockDim.x) {
+      const int r = idx & 63, t = idx >> 6;
+      const int64_t i = i0 + r, l = k0 + t;
+      As[r * gSS + t] = (l <= i) ? a[i + l * ld] : 0.0;
+      const int tb = idx & 31, cb = idx >> 5;  // k fastest: the panel column is contiguous in l
+      Bs[cb * gSS + tb] = a[(k0 + tb) + (j0 + c0 + cb) * ld];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < gKC; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) af[mi] = As[(wm * 32 + mi * 8 + g) * gSS + kk + q];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) bf[ni] = Bs[(wn * 32 + ni * 8 + g) * gSS + kk + q];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t row = i0 + wm * 32 + mi * 8 + g - l0;
+        const int col = c0 + wn * 32 + ni * 8 + 2 * q + e;
+        tout[row * nb + col] = acc[mi][ni][e];
+      }
+}
+
+// Diagonal tile of X: lower triangle <- W_j (row-major), strict upper left untouched.
+__global__ void put_diag_inverse_kernel(double* __restrict__ a, int64_t ld, int64_t j0, int nb,
+                                        const double* __restrict__ w) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb * nb; idx += gridDim.x * blockDim.x) {
+    const int r = idx % nb, c = idx / nb;
+    if (r >= c) a[(j0 + r) + (j0 + c) * ld] = w[r * nb + c];
+  }
+}
+
+// S = X^T X on 64 x 64 lower tiles (I >= J):  S(i, j) = sum_{k >= I*64} X(k, i) X(k, j),
+// X lower triangular (X(k, i) = 0 for k < i).  Output column-major into s (ld_s).
+__device__ __forceinline__ void tri_dec(long long b, int& ti, int& tj) {
+  long long t = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while (t * (t + 1) / 2 > b) --t;
+  while ((t + 1) * (t + 2) / 2 <= b) ++t;
+  ti = (int)t;
+  tj = (int)(b - t * (t + 1) / 2);
+}
+
+__global__ void __launch_bounds__(128) lauum_tiles_kernel(const double* __restrict__ a, int64_t ld, int64_t npad,
+                                                          double* __restrict__ s, int64_t lds, const DevStatus* st) {
+  __shared__ double As[64 * gSS];
+  __shared__ double Bs[64 * gSS];
+  if (*(volatile const int32_t*)&st->info) return;
+  int ti, tj;
+  tri_dec(blockIdx.x, ti, tj);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3, wm = warp >> 1, wn = warp & 1;
+  const int64_t i0 = (int64_t)ti * 64, j0 = (int64_t)tj * 64;
+  double acc[4][4][2];
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+  for (int64_t k0 = i0; k0 < npad; k0 += gKC) {
+    for (int idx = tid; idx < 64 * gKC; idx += blockDim.x) {
+      const int t = idx & 31, r = idx >> 5;  // k fastest: X(k, col) contiguous in k
+      const int64_t k = k0 + t;
+      const int64_t ci = i0 + r, cj = j0 + r;
+      As[r * gSS + t] = (k >= ci) ? a[k + ci * ld] : 0.0;
+      Bs[r * gSS + t] = (k >= cj) ? a[k + cj * ld] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < gKC; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) af[mi] = As[(wm * 32 + mi * 8 + g) * gSS + kk + q];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) bf[ni] = Bs[(wn * 32 + ni * 8 + g) * gSS + kk + q];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) dmma884(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t i = i0 + wm * 32 + mi * 8 + g;
+        const int64_t j = j0 + wn * 32 + ni * 8 + 2 * q + e;
+        if (ti == tj && j > i) continue;
+        s[i + j * lds] = acc[mi][ni][e];
+      }
+}
+
+// sinh and cosh of x (series below 0.1 so that small steps keep full relative accuracy)
+__device__ __forceinline__ void sincosh_pair(double x, double& sh, double& ch) {
+  if (fabs(x) < 0.1) {
+    const double x2 = x * x;
+    sh = x * (1.0 + x2 * (1.0 / 6.0 + x2 * (1.0 / 120.0 + x2 * (1.0 / 5040.0 + x2 / 362880.0))));
+    ch = 1.0 + x2 * (0.5 + x2 * (1.0 / 24.0 + x2 * (1.0 / 720.0 + x2 * (1.0 / 40320.0 + x2 / 3628800.0))));
+  } else {
+    const double e = exp(x), ie = 1.0 / e;
+    sh = 0.5 * (e - ie);
+    ch = 0.5 * (e + ie);
+  }
+}
+
+// e^x dK_nu(x)/dnu = int_0^inf t sinh(nu t) exp(-x (cosh t - 1)) dt  (DLMF 10.32.9
+// differentiated in nu) by the trapezoid rule with step h = min(0.2, 0.6/sqrt(x)):
+// the integrand is entire, so the error falls like exp(-2 pi d / h) with d the
+// usable half-width of the strip around the real axis (~pi/2 for small x,
+// ~1/sqrt(x) for large x).  sinh(t/2) and sinh/cosh(nu t) advance by exact
+// hyperbolic rotations, so cosh t - 1 = 2 sinh^2(t/2) carries no cancellation.
+__device__ __forceinline__ double dknu_dnu_scaled(double nu, double x) {
+  if (nu == 0.0) return 0.0;
+  const double h = fmin(0.2, 0.6 / sqrt(x));
+  double sh_h, ch_h, snu_h, cnu_h;
+  sincosh_pair(0.5 * h, sh_h, ch_h);
+  sincosh_pair(nu * h, snu_h, cnu_h);
+  double s = 0.0, c = 1.0;    // sinh(t/2), cosh(t/2) at t = 0
+  double sn = 0.0, cn = 1.0;  // sinh(nu t), cosh(nu t)
+  double sum = 0.0;
+  const double anu = fabs(nu);
+  for (int k = 1; k < 4000; ++k) {
+    const double s2 = s * ch_h + c * sh_h;
+    const double c2 = c * ch_h + s * sh_h;
+    s = s2;
+    c = c2;
+    const double sn2 = sn * cnu_h + cn * snu_h;
+    const double cn2 = cn * cnu_h + sn * snu_h;
+    sn = sn2;
+    cn = cn2;
+    const double t = k * h;
+    const double f = t * sn * exp(-2.0 * x * s * s);
+    sum += f;
+    // past the peak (log-derivative 1/t + nu coth(nu t) - x sinh t < 0) and negligible
+    const double sinh_t = 2.0 * s * c;
+    if (x * sinh_t > 1.0 / t + anu * cn / fabs(sn) && fabs(f) <= 1e-18 * fabs(sum)) break;
+  }
+  return h * sum;
+}
+
+struct GradParams {
+  MaternParams m;
+  double psi_nu;  // digamma(nu)
+};
+
+// One 64 x 64 lower tile per block (as the generator), 256 threads; per-block partial
+// sums of w (a_i a_j - S_ij) D_k for k = sigma^2, beta, nu in a fixed order.
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const double* __restrict__ locs, int64_t n,
+                                                          const __grid_constant__ GradParams G,
+                                                          const double* __restrict__ alpha,
+                                                          const double* __restrict__ sinv, int64_t lds,
+                                                          double* __restrict__ partial) {
+  __shared__ double red[3][256];
+  int ti, tj;
+  tri_dec(blockIdx.x, ti, tj);
+  const MaternParams& P = G.m;
+  const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+  if (i < n) {
+    const double xi = locs[2 * i], yi = locs[2 * i + 1], ai = alpha[i];
+    for (int s = 0; s < 16; ++s) {
+      const int64_t j = (int64_t)tj * 64 + (threadIdx.x >> 6) + 4 * s;
+      if (j > i) continue;
+      const double w = (i == j) ? 1.0 : 2.0;
+      const double cij = w * (ai * alpha[j] - sinv[i + j * lds]);
+      double d0, d1, d2;
+      const double dx = xi - locs[2 * j], dy = yi - locs[2 * j + 1];
+      const double r = sqrt(dx * dx + dy * dy);
+      if (r == 0.0) {
+        d0 = 1.0;
+        d1 = d2 = 0.0;
+      } else {
+        const double x = r / P.beta;
+        if (x > 800.0) {
+          d0 = d1 = d2 = 0.0;
+        } else {
+          const double lnx = log(x);
+          double knu, knum1;
+          const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
+          const double base = P.logc + P.nu * lnx;
+          const double pre = P.sigma2 * exp(base - (scaled ? x : 0.0));  // sigma^2 c x^nu (e^-x if scaled)
+          const double sig = pre * knu;
+          d0 = sig / P.sigma2;
+          d1 = pre * knum1 * x / P.beta;
+          d2 = sig * (lnx - 0.69314718055994530942 - G.psi_nu) +
+               P.sigma2 * exp(base - x) * dknu_dnu_scaled(P.nu, x);
+        }
+      }
+      acc0 = fma(cij, d0, acc0);
+      acc1 = fma(cij, d1, acc1);
+      acc2 = fma(cij, d2, acc2);
+    }
+  }
+  const int tid = threadIdx.x;
+  red[0][tid] = acc0;
+  red[1][tid] = acc1;
+  red[2][tid] = acc2;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[0][tid] += red[0][tid + w];
+      red[1][tid] += red[1][tid + w];
+      red[2][tid] += red[2][tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid < 3) partial[(int64_t)blockIdx.x * 3 + tid] = red[tid][0];
+}
+
+// out[k] = 1/2 sum_b partial[b][k]  (one block per component, fixed order)
+__global__ void __launch_bounds__(256) grad_finish_kernel(const double* __restrict__ partial, int64_t nblocks,
+                                                          double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int k = blockIdx.x, tid = threadIdx.x;
+  double s = 0.0;
+  for (int64_t b = tid; b < nblocks; b += 256) s += partial[b * 3 + k];
+  sh[tid] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) out[k] = 0.5 * sh[0];
+}
+
+// digamma for the host-side constant psi(nu): shift to x >= 12 with psi(x) = psi(x+1) - 1/x,
+// then psi(x) = ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Bernoulli numbers B_2..B_10).
+static double host_digamma(double x) {
+  double shift = 0.0;
+  for (; x < 12.0; x += 1.0) shift += 1.0 / x;
+  const double r = 1.0 / (x * x);
+  const double tail = r * (1.0 / 12 - r * (1.0 / 120 - r * (1.0 / 252 - r * (1.0 / 240 - r * (1.0 / 132)))));
+  return log(x) - 0.5 / x - tail - shift;
+}
+
+static cudaError_t launch_gradient(exa_ctx* c, const double* locs, int64_t n, int64_t npad, const double theta[3],
+                                   const double* alpha, const double* sinv, double* partial, double* out) {
+  GradParams G;
+  matern_params(theta, &G.m);
+  G.psi_nu = host_digamma(theta[2]);
+  const long long t = (n + 63) / 64;
+  const long long blocks = t * (t + 1) / 2;
+  grad_reduce_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(locs, n, G, alpha, sinv, npad, partial);
+  grad_finish_kernel<<<3, 256, 0, c->stream>>>(partial, blocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace exa
+
+using namespace exa;
+
+extern "C" exa_status exa_loglik_grad(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3],
+                                      int64_t n, exa_prec prec, double* loglik, double grad[3]) {
+  if (!c) return EXA_ERR_ARG;
+  c->err[0] = 0;
+  c->last_pivot = -1;
+  if (!loglik || !grad) return set_err(c, EXA_ERR_ARG, "loglik / grad is NULL");
+  *loglik = NAN;
+  grad[0] = grad[1] = grad[2] = NAN;
+  if (n < 1 || !d_locs || !d_z) return set_err(c, EXA_ERR_ARG, "bad n or NULL device pointer");
+  if (prec != EXA_FP64) return set_err(c, EXA_ERR_ARG, "the gradient is computed in EXA_FP64 only");
+  exa_status st = check_theta(c, theta);
+  if (st != EXA_OK) return st;
+  const int nb = c->tile_nb;
+  const int64_t npad = round_up(n, nb);
+  const int T = (int)(npad / nb);
+  // the second n x n buffer (Sigma^-1) is requested first so that a bound that cannot
+  // hold both fails before any work
+  if ((st = ensure(c, c->gr_part, (size_t)npad * npad * sizeof(double), "inverse covariance")) != EXA_OK) return st;
+  exa_result res;
+  memset(&res, 0, sizeof(res));
+  double* y = nullptr;
+  if ((st = loglik_fp64(c, d_locs, d_z, theta, n, &res, &y)) != EXA_OK) return st;
+  *loglik = res.loglik;
+  double* A = (double*)c->mat.p;
+  double* W = (double*)c->w_all.p;
+  double* S = (double*)c->gr_part.p;
+  double* part = (double*)c->partial.p;
+  double* Tbuf = (double*)c->panel.p;  // npad x nb
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  // a = L^-T y (in place in y)
+  for (int k = T - 1; k >= 0 && e == cudaSuccess; --k) {
+    const double rows = (double)(npad - (int64_t)k * nb);
+    ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb, 2);
+    e = launch_trsv_bwd_step(s, A, npad, npad, nb, k, W, y, part + 2 * kRedPartials, c->d_status);
+  }
+  // X = L^-1 in place, block columns right to left
+  for (int j = T - 1; j >= 0 && e == cudaSuccess; --j) {
+    const int64_t j0 = (int64_t)j * nb, l0 = j0 + nb, m = npad - l0;
+    if (m > 0) {
+      ProfScope ps(c, PK_GRAD, (double)m * m * nb + 2.0 * m * nb * nb, 8.0 * ((double)m * m / 2 + 3.0 * m * nb), 2);
+      dim3 grid(nb / 64, (unsigned)(m / 64));
+      trmm_lower_panel_kernel<<<grid, 128, 0, s>>>(A, npad, l0, j0, nb, Tbuf, c->d_status);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = launch_dgemm_nt_small(s, (int)m, nb, nb, -1.0, Tbuf, nb, 1, W + (int64_t)j * nb * nb, 1, nb, 0.0,
+                                  A + l0 + j0 * npad, 1, npad, c->d_status);
+    }
+    if (e == cudaSuccess) {
+      put_diag_inverse_kernel<<<32, 256, 0, s>>>(A, npad, j0, nb, W + (int64_t)j * nb * nb);
+      e = cudaGetLastError();
+    }
+  }
+  // Sigma^-1 = X^T X (lower tiles) into S
+  if (e == cudaSuccess) {
+    const long long t64 = npad / 64;
+    ProfScope ps(c, PK_GRAD, (double)npad * npad * npad / 3.0, 8.0 * (double)npad * npad);
+    lauum_tiles_kernel<<<(unsigned)(t64 * (t64 + 1) / 2), 128, 0, s>>>(A, npad, npad, S, npad, c->d_status);
+    e = cudaGetLastError();
+  }
+  // fused regeneration of dSigma/dtheta and reduction
+  if ((st = ensure(c, c->vec, (size_t)3 * npad * sizeof(double), "vectors")) != EXA_OK) return st;
+  const long long t64n = (n + 63) / 64;
+  const size_t nblocks = (size_t)(t64n * (t64n + 1) / 2);
+  if ((st = ensure(c, c->gr_blocks, nblocks * 3 * sizeof(double), "gradient partials")) != EXA_OK) return st;
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_GRAD, 0.0, 4.0 * (double)n * (double)(n + 1));
+    e = launch_gradient(c, d_locs, n, npad, theta, y, S, (double*)c->gr_blocks.p, c->d_scalars + 8);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_scalars + 8, c->d_scalars + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "gradient launch");
+  if ((st = read_status(c)) != EXA_OK) return st;
+  grad[0] = c->h_scalars[8];
+  grad[1] = c->h_scalars[9];
+  grad[2] = c->h_scalars[10];
+  return EXA_OK;
+}

@@ -6,6 +6,7 @@
 // work is one log, one exp (+ one sqrt for x > 2) and division-free loops.
 #include <math.h>
 
+#include "bessel.cuh"
 #include "exa_internal.cuh"
 
 namespace exa {
@@ -69,115 +70,8 @@ void matern_params(const double theta[3], MaternParams* p) {
 }
 
 // ---------------------------------------------------------------------------
-// Device side
+// Device side (K_nu itself lives in bessel.cuh)
 // ---------------------------------------------------------------------------
-
-// K_mu(x), K_{mu+1}(x) for 0 < x <= 2 by Temme's series:
-//   K_mu = sum_k c_k f_k,  K_{mu+1} = (2/x) sum_k c_k h_k,  c_k = (x^2/4)^k / k!,
-//   f_0 = (mu pi / sin mu pi) [cosh(s) Gamma_1 + sinh(s)/s ln(2/x) Gamma_2],  s = mu ln(2/x),
-//   p_0 = (x/2)^-mu Gamma(1+mu) / 2,  q_0 = (x/2)^mu Gamma(1-mu) / 2,
-//   f_k = (k f_{k-1} + p_{k-1} + q_{k-1}) / (k^2 - mu^2),  p_k = p_{k-1}/(k - mu),
-//   q_k = q_{k-1}/(k + mu),  h_k = p_k - k f_k.
-__device__ __forceinline__ void bessel_temme(const MaternParams& P, double x, double lnx, double& k0, double& k1) {
-  const double mu = P.mu;
-  const double l2x = 0.69314718055994530942 - lnx;  // ln(2/x)
-  const double s = mu * l2x;
-  const double es = exp(s);                          // (x/2)^-mu
-  const double ies = 1.0 / es;
-  const double ch = 0.5 * (es + ies);
-  double shs;                                        // sinh(s) / s
-  if (fabs(s) < 1e-3) {
-    const double s2 = s * s;
-    shs = 1.0 + s2 * (1.0 / 6.0 + s2 * (1.0 / 120.0 + s2 * (1.0 / 5040.0)));
-  } else {
-    shs = 0.5 * (es - ies) / s;
-  }
-  double f = P.mupi_sin * (ch * P.gam1 + shs * l2x * P.gam2);
-  double p = 0.5 * es * P.gp;
-  double q = 0.5 * ies * P.gm;
-  const double x2 = 0.25 * x * x;
-  double c = 1.0;
-  double s0 = f, s1 = p;
-  for (int k = 1; k <= kTemmeTerms; ++k) {
-    const double dk = (double)k;
-    f = fma(dk, f, p + q) * P.t_k2[k];
-    p *= P.t_km[k];
-    q *= P.t_kp[k];
-    c *= x2 / dk;
-    const double h = fma(-dk, f, p);
-    const double tf = c * f, th = c * h;
-    s0 += tf;
-    s1 += th;
-    if (fabs(tf) <= 1e-17 * fabs(s0) && fabs(th) <= 1e-17 * fabs(s1)) break;
-  }
-  k0 = s0;
-  k1 = 2.0 * s1 / x;
-}
-
-// e^x K_mu(x), e^x K_{mu+1}(x) for x > 2: z_k = U(mu + 1/2 + k, 2mu + 1, 2x) obey
-//   z_{k-1} = 2(k + x) z_k - ((k + 1/2)^2 - mu^2) z_{k+1}      (DLMF 13.3.7),
-// whose decaying solution is reached by running it backward from depth D
-// (Miller), and sum_k C_k z_k = (2x)^(-mu-1/2) fixes its scale, so
-//   e^x K_mu = sqrt(pi/(2x)) z_0 / sum_k C_k z_k,
-//   K_{mu+1} / K_mu = (mu + 1/2 + x + (mu^2 - 1/4) z_1/z_0) / x.
-// D = ceil(12 + 160/x) keeps the truncation error below 1e-16 for |mu| <= 1/2.
-__device__ __forceinline__ void bessel_miller(const MaternParams& P, double x, double& k0s, double& k1s) {
-  const double mu = P.mu;
-  int D = (int)(12.0 + 160.0 / x) + 1;
-  if (D > kMillerMax) D = kMillerMax;
-  double zp1 = 0.0, z = 1.0;
-  double S = P.m_c[D];
-  for (int k = D; k >= 1; --k) {
-    const double zm1 = fma(2.0 * ((double)k + x), z, -P.m_a[k] * zp1);
-    zp1 = z;
-    z = zm1;
-    S = fma(P.m_c[k - 1], z, S);
-  }
-  const double r01 = zp1 / z;  // z_1 / z_0
-  k0s = sqrt(1.5707963267948966192 / x) * (z / S);
-  k1s = k0s / x * (mu + 0.5 + x + (mu * mu - 0.25) * r01);
-}
-
-// K_nu(x) and K_{nu-1}(x) with a common scale: returns scaled = true when the
-// values are e^x K (x > 2).  x must be finite and > 0.
-__device__ __forceinline__ bool bessel_k_nu(const MaternParams& P, double x, double lnx, double& knu, double& knum1) {
-  double a, b;  // K_mu, K_{mu+1}
-  bool scaled;
-  if (x <= 2.0) {
-    bessel_temme(P, x, lnx, a, b);
-    scaled = false;
-  } else {
-    bessel_miller(P, x, a, b);
-    scaled = true;
-  }
-  if (P.N == 0) {
-    knu = a;
-    knum1 = b - 2.0 * P.mu / x * a;  // K_{mu-1} = K_{mu+1} - (2 mu / x) K_mu
-  } else {
-    const double ix = 1.0 / x;
-    for (int j = 1; j < P.N; ++j) {  // (a, b) = (K_{mu+j-1}, K_{mu+j}) -> (K_{mu+j}, K_{mu+j+1})
-      const double c = fma(2.0 * (P.mu + j) * ix, b, a);
-      a = b;
-      b = c;
-    }
-    knu = b;
-    knum1 = a;
-  }
-  return scaled;
-}
-
-// Eq. 3 at distance r.
-__device__ __forceinline__ double matern_value(const MaternParams& P, double r) {
-  if (r == 0.0) return P.sigma2;
-  const double x = r / P.beta;
-  if (!(x > 0.0)) return x;      // NaN propagates
-  if (x > 800.0) return 0.0;     // sigma^2 c x^nu K_nu(x) < 1e-340: underflows to 0
-  const double lnx = log(x);
-  double knu, knum1;
-  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
-  const double e = P.logc + P.nu * lnx - (scaled ? x : 0.0);
-  return P.sigma2 * exp(e) * knu;
-}
 
 __device__ __forceinline__ void tri_decode(long long b, int& ti, int& tj) {
   // b = ti (ti + 1) / 2 + tj,  0 <= tj <= ti

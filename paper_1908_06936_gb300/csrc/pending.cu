@@ -3,7 +3,7 @@
 
 namespace exa {
 void release_extra(exa_ctx* c) {
-  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split_b, &c->mx_vec, &c->mx_w2, &c->mx_offmax, &c->gr_part,
+  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split_b, &c->mx_vec, &c->mx_w2, &c->mx_offmax, &c->gr_part, &c->gr_blocks,
                     &c->bt_mat, &c->bt_meta, &c->bt_vec, &c->bt_work};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
@@ -15,10 +15,6 @@ void release_extra(exa_ctx* c) {
 }  // namespace exa
 
 extern "C" {
-exa_status exa_loglik_grad(exa_ctx* c, const double*, const double*, const double*, int64_t, exa_prec, double*,
-                           double*) {
-  return exa::set_err(c, EXA_ERR_ARG, "gradient is not available in this build");
-}
 exa_status exa_loglik_batched(exa_ctx* c, int32_t, const int64_t*, const double* const*, const double* const*,
                               const double*, exa_prec, double*, int32_t*) {
   return exa::set_err(c, EXA_ERR_ARG, "batched form is not available in this build");
