@@ -148,7 +148,8 @@ exa_status exa_loglik_ex(exa_ctx* ctx, const double* d_locs, const double* d_z, 
 exa_status exa_loglik_grad(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                            exa_prec prec, double* loglik, double grad[3]);
 
-/* Batched evaluation of nrep independent replicate fields of uneven sizes.
+/* Batched evaluation of nrep independent replicate fields of uneven sizes
+ * (FP64; one persistent launch walks the tile tasks of every replicate).
  *   h_n       host array of nrep sizes (each >= 1).
  *   d_locs    host array of nrep DEVICE pointers, replicate r has h_n[r] x 2 locations.
  *   d_z       host array of nrep DEVICE pointers, h_n[r] observations each.
@@ -156,7 +157,11 @@ exa_status exa_loglik_grad(exa_ctx* ctx, const double* d_locs, const double* d_z
  *             so a captured graph can be replayed with new parameters.
  *   d_loglik  DEVICE output, nrep values (NaN where the replicate is not SPD).
  *   d_status  DEVICE output, nrep exa_status codes.
- * Stream-asynchronous: returns once the work is enqueued.                   */
+ * Stream-asynchronous: returns once the work is enqueued; device memory is
+ * allocated on the first call for a shape set, so make that call before any
+ * CUDA-graph capture, after which the sequence can be captured and replayed
+ * with new d_theta.  Calls that overlap on the GPU share the context's
+ * buffers and must not run concurrently.                                     */
 exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, const double* const* d_locs,
                               const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
                               int32_t* d_status);
@@ -189,6 +194,15 @@ exa_status exa_profile_enable(exa_ctx* ctx, int on);
 /* Copy up to max per-class records into out (host); returns how many.  Waits
  * for pending timed launches.  reset != 0 zeroes the accumulators.         */
 int exa_profile_read(exa_ctx* ctx, exa_kernel_stat* out, int max, int reset);
+
+/* Options of the batched form:
+ *   tile_nb      tile of the persistent factorisation, 32 or 64 (0: 64);
+ *   ctas_per_sm  persistent CTAs per SM, capped at what fits resident (0: all that fit);
+ *   spin_cycles  bound of one dependency wait in SM clock cycles (0: 2e9, about 1 s);
+ *   inject_stall test hook: non-zero adds to the work list a task whose dependency is
+ *                never met, so its wait runs out and the affected replicates report
+ *                EXA_ERR_TIMEOUT (the path a real stall would take).                 */
+exa_status exa_ctx_set_batched(exa_ctx* ctx, int tile_nb, int ctas_per_sm, long long spin_cycles, int inject_stall);
 
 /* Exact synthetic realisation (Section III, Example 1, simulate_obs_exact):
  * d_z = L d_eps with L L^T = Sigma(theta), both n FP64 device vectors.       */

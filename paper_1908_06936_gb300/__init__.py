@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
                 "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
                 "exa_ctx_set_mixed_band": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
                 "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
@@ -275,3 +276,8 @@ def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
     k = lib().exa_profile_read(_P(ctx), buf, 32, int(reset))
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "timed_launches": buf[i].timed_launches,
              "ms": buf[i].ms, "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(k)]
+
+
+def exa_ctx_set_batched(ctx: int, tile_nb: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,
+                        inject_stall: int = 0) -> int:
+    return lib().exa_ctx_set_batched(_P(ctx), int(tile_nb), int(ctas_per_sm), int(spin_cycles), int(inject_stall))

@@ -176,6 +176,7 @@ void exa_ctx_destroy(exa_ctx* c) {
   free_buf(c, c->vec);
   free_buf(c, c->partial);
   release_extra(c);
+  release_batched(c);
   prof_release(c);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_scalars) cudaFree(c->d_scalars);

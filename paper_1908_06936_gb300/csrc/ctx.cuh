@@ -9,6 +9,8 @@
 
 namespace exa {
 
+struct BatchPlan;
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -50,6 +52,13 @@ struct exa_ctx {
   exa::DevBuf gr_blocks;    // per-block gradient partial sums
   // batched
   exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work;
+  exa::BatchPlan* bplan = nullptr;  // cached work list of the last shape set
+  void* bt_stage = nullptr;         // pinned host staging for the work list / metadata
+  size_t bt_stage_bytes = 0;
+  int batched_nb = 64;              // tile of the batched factorisation (32 or 64)
+  int batched_ctas_per_sm = 0;      // 0: as many as fit
+  long long batched_spin = 2000000000LL;  // bound of one dependency wait (SM cycles)
+  int batched_stall = 0;            // test hook: add a task whose dependency is never met
   // status and small results
   exa::DevStatus* d_status = nullptr;
   exa::DevStatus* h_status = nullptr;  // pinned
@@ -77,6 +86,7 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
 exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                         exa_prec prec, exa_result* out);
 void release_extra(exa_ctx* c);
+void release_batched(exa_ctx* c);
 // Lay out a split operand of `rows` x K in `buf` (T3 planes and/or OZ digits) and build its TMA maps.
 exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz);
 

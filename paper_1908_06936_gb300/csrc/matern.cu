@@ -15,59 +15,7 @@ namespace exa {
 // Host side
 // ---------------------------------------------------------------------------
 
-// D(mu) = (Gamma(1+mu) - Gamma(1-mu)) / (2 mu) = int_0^inf e^-t sinh(mu ln t) / mu dt.
-// With t = e^u the integrand exp(u - e^u) sinh(mu u)/mu is analytic in the strip
-// |Im u| < pi/2 and decays like e^{(1-|mu|) u} (u -> -inf) and doubly
-// exponentially (u -> +inf), so the trapezoid rule with h = 1/16 on [-110, 5]
-// is exact to rounding.  D(0) = Gamma'(1).  Written this way Gamma_1(mu) has no
-// cancellation as mu -> 0 (integer nu).
-static double temme_D(double mu) {
-  const double h = 1.0 / 16.0;
-  double s = 0.0;
-  for (int k = -110 * 16; k <= 5 * 16; ++k) {
-    const double u = h * k;
-    const double w = mu * u;
-    double sh;  // sinh(mu u) / mu
-    if (fabs(w) < 1e-4)
-      sh = u * (1.0 + w * w / 6.0);
-    else
-      sh = sinh(w) / mu;
-    s += exp(u - exp(u)) * sh;
-  }
-  return s * h;
-}
-
-void matern_params(const double theta[3], MaternParams* p) {
-  const double nu = theta[2];
-  p->sigma2 = theta[0];
-  p->beta = theta[1];
-  p->nu = nu;
-  p->logc = (1.0 - nu) * 0.69314718055994530942 - lgamma(nu);
-  const int N = (int)floor(nu + 0.5);
-  const double mu = nu - N;
-  p->N = N;
-  p->mu = mu;
-  p->pad_ = 0;
-  const double pi = 3.14159265358979323846;
-  const double sinc = (mu == 0.0) ? 1.0 : sin(pi * mu) / (pi * mu);
-  p->mupi_sin = 1.0 / sinc;
-  p->gp = tgamma(1.0 + mu);
-  p->gm = tgamma(1.0 - mu);
-  // Gamma_1 = D(mu) / (Gamma(1+mu) Gamma(1-mu)) and Gamma(1+mu) Gamma(1-mu) = 1 / sinc
-  p->gam1 = temme_D(mu) * sinc;
-  p->gam2 = 0.5 * (1.0 / p->gm + 1.0 / p->gp);
-  p->t_k2[0] = p->t_km[0] = p->t_kp[0] = 0.0;
-  for (int k = 1; k <= kTemmeTerms; ++k) {
-    p->t_k2[k] = 1.0 / ((double)k * k - mu * mu);
-    p->t_km[k] = 1.0 / (k - mu);
-    p->t_kp[k] = 1.0 / (k + mu);
-  }
-  p->m_c[0] = 1.0;
-  for (int k = 0; k <= kMillerMax + 1; ++k) {
-    p->m_a[k] = (k + 0.5) * (k + 0.5) - mu * mu;
-    if (k + 1 <= kMillerMax + 1) p->m_c[k + 1] = p->m_c[k] * p->m_a[k] / (k + 1);
-  }
-}
+void matern_params(const double theta[3], MaternParams* p) { matern_params_hd(theta, p); }
 
 // ---------------------------------------------------------------------------
 // Device side (K_nu itself lives in bessel.cuh)

@@ -14,9 +14,4 @@ void release_extra(exa_ctx* c) {
 }
 }  // namespace exa
 
-extern "C" {
-exa_status exa_loglik_batched(exa_ctx* c, int32_t, const int64_t*, const double* const*, const double* const*,
-                              const double*, exa_prec, double*, int32_t*) {
-  return exa::set_err(c, EXA_ERR_ARG, "batched form is not available in this build");
-}
-}
+

@@ -1,0 +1,147 @@
+"""Batched replicate fields (one persistent launch) against the FP64 oracle, plus failure paths."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_06936_gb300 import synth
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(sides, seed, theta0=(1.0, 0.1, 0.5), with_z=True):
+    locs, zs = [], []
+    for r, m in enumerate(sides):
+        l = synth.jittered_grid(int(m), seed + r)
+        locs.append(l)
+        zs.append(oracle.simulate(l, theta0, synth.normals(int(m) ** 2, seed + r)) if with_z
+                  else synth.normals(int(m) ** 2, seed + r))
+    return locs, zs
+
+
+def run(ctx, locs, zs, thetas, prec=0):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.asarray(thetas, dtype=np.float64).ravel())
+    out = torch.empty(len(ns), dtype=torch.float64, device="cuda")
+    st = torch.empty(len(ns), dtype=torch.int32, device="cuda")
+    ctx.check(exa.exa_loglik_batched(ctx.handle, len(ns), ns, dl, dz, th, prec, out, st))
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), st.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1908_06936_gb300 as exa
+
+    c = exa.Context()
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_batched_vs_oracle(ctx, tile):
+    import paper_1908_06936_gb300 as exa
+
+    sides = [5, 9, 12, 17, 20, 1, 3, 25, 8, 14]
+    locs, zs = make_batch(sides, seed=10)
+    thetas = synth.theta_perturbations((1.0, 0.1, 0.5), len(sides), seed=3)
+    exa.exa_ctx_set_batched(ctx.handle, tile, 0, 0, 0)
+    got, st = run(ctx, locs, zs, thetas)
+    assert np.all(st == 0)
+    for r in range(len(sides)):
+        ref = oracle.loglik(locs[r], zs[r], thetas[r])["l"]
+        assert abs(got[r] - ref) <= 1e-10 * abs(ref), (r, got[r], ref)
+    exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
+
+
+def test_batched_failures_are_per_replicate(ctx):
+    sides = [6, 10, 7, 11]
+    locs, zs = make_batch(sides, seed=20)
+    locs[1][17, 0] = float("nan")
+    thetas = np.tile([1.0, 0.1, 0.5], (4, 1))
+    thetas[3, 1] = -0.2
+    got, st = run(ctx, locs, zs, thetas)
+    assert list(st) == [0, 2, 0, 1]
+    assert math.isnan(got[1]) and math.isnan(got[3])
+    for r in (0, 2):
+        assert abs(got[r] - oracle.loglik(locs[r], zs[r], thetas[r])["l"]) <= 1e-10 * abs(got[r])
+
+
+def test_batched_wait_times_out_and_context_survives(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    sides = [8, 12, 16]
+    locs, zs = make_batch(sides, seed=30)
+    thetas = np.tile([1.0, 0.1, 0.5], (3, 1))
+    exa.exa_ctx_set_batched(ctx.handle, 64, 0, 2_000_000, 1)  # ~1 ms waits, one task that never becomes ready
+    try:
+        got, st = run(ctx, locs, zs, thetas)
+    finally:
+        exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
+    assert np.any(st == exa.EXA_ERR_TIMEOUT)
+    assert all(math.isnan(got[r]) for r in range(3) if st[r] != 0)
+    got2, st2 = run(ctx, locs, zs, thetas)
+    assert np.all(st2 == 0)
+    for r in range(3):
+        assert abs(got2[r] - oracle.loglik(locs[r], zs[r], thetas[r])["l"]) <= 1e-10 * abs(got2[r])
+
+
+def test_batched_graph_capture_replay_with_new_theta(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    sides = [7, 13, 10]
+    locs, zs = make_batch(sides, seed=40)
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.tile([1.0, 0.1, 0.5], 3))
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    st = torch.empty(3, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        exa.exa_ctx_set_stream(ctx.handle, s.cuda_stream)
+        ctx.check(exa.exa_loglik_batched(ctx.handle, 3, ns, dl, dz, th, 0, out, st))  # allocates, outside capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctx.check(exa.exa_loglik_batched(ctx.handle, 3, ns, dl, dz, th, 0, out, st))
+    exa.exa_ctx_set_stream(ctx.handle, torch.cuda.current_stream().cuda_stream)
+    for new in ([1.3, 0.08, 0.7], [0.6, 0.15, 1.2]):
+        th.copy_(torch.tensor(new * 3, dtype=torch.float64))
+        g.replay()
+        torch.cuda.synchronize()
+        res = out.cpu().numpy()
+        for r in range(3):
+            ref = oracle.loglik(locs[r], zs[r], new)["l"]
+            assert abs(res[r] - ref) <= 1e-10 * abs(ref)
+
+
+def test_batched_full_config_sigma2_scaling(ctx):
+    # 256 replicates with n_i = m_i^2, m_i ~ U{20..80}: l(s) = a - (n/2) ln s - q/(2 s) holds
+    # exactly for every replicate, so three sigma^2 values over-determine (a, q)
+    sides = synth.replicate_sides(256, seed=5)
+    locs = [synth.jittered_grid(int(m), 1000 + r) for r, m in enumerate(sides)]
+    zs = [synth.normals(int(m) ** 2, 1000 + r) for r, m in enumerate(sides)]
+    res = {}
+    for s2 in (1.0, 2.0, 4.0):
+        got, st = run(ctx, locs, zs, np.tile([s2, 0.1, 0.5], (256, 1)))
+        assert np.all(st == 0)
+        res[s2] = got
+    n = np.array([l.shape[0] for l in locs], dtype=np.float64)
+    # from s = 1 and s = 4: q = (8/3)(l4 - l1 + n ln 2); predict s = 2
+    q = (8.0 / 3.0) * (res[4.0] - res[1.0] + n * math.log(2.0))
+    a = res[1.0] + 0.5 * q
+    pred2 = a - 0.5 * n * math.log(2.0) - q / 4.0
+    assert np.all(np.abs(pred2 - res[2.0]) <= 1e-10 * np.abs(res[2.0]))
+    # spot-check the smallest replicates against the oracle
+    for r in np.argsort(n)[:3]:
+        ref = oracle.loglik(locs[r], zs[r], (1.0, 0.1, 0.5))["l"]
+        assert abs(res[1.0][r] - ref) <= 1e-10 * abs(ref)
