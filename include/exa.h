@@ -209,6 +209,30 @@ exa_status exa_ctx_set_batched(exa_ctx* ctx, int tile_nb, int ctas_per_sm, long 
 exa_status exa_simulate(exa_ctx* ctx, const double* d_locs, const double* d_eps, const double theta[3], int64_t n,
                         exa_prec prec, double* d_z);
 
+/* Allocation-free FP64 log-likelihood (no counterpart in the paper; an
+ * interface for callers that cannot allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: a host application whose memory pool
+ * owns all device memory, or a latency-critical path that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree imply.  This entry point
+ * computes the same l(theta) as exa_loglik with EXA_FP64 but allocates
+ * nothing: it needs no context, and its workspace is one fixed array in the
+ * library's device memory, about 36 MiB, held by every GPU that loads the
+ * library until the process exits.
+ *   cuda_stream  stream to run on (NULL: the legacy default stream).
+ *   d_locs, d_z  device inputs as for exa_loglik; theta on the host.
+ *   n            1 <= n <= 2048; larger n returns EXA_ERR_ARG.
+ *   loglik       host output (NaN on any error).
+ * The call synchronises the stream.  On the first call on a device it looks
+ * up the device address of the array (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls on a device share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Returns EXA_ERR_NOT_SPD for a
+ * non-positive pivot (no pivot index is kept) and EXA_ERR_CUDA if a CUDA call
+ * fails.                                                                     */
+exa_status exa_loglik_noalloc(void* cuda_stream, const double* d_locs, const double* d_z, const double theta[3],
+                              int64_t n, double* loglik);
+
 #ifdef __cplusplus
 }
 #endif

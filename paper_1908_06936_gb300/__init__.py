@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
                 "exa_simulate": (ctypes.c_int, [_P, _P, _P, _PD, _I64, ctypes.c_int, _P]),
                 "exa_ctx_set_mixed_band": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_loglik_noalloc": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
                 "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
@@ -281,3 +282,9 @@ def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
 def exa_ctx_set_batched(ctx: int, tile_nb: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,
                         inject_stall: int = 0) -> int:
     return lib().exa_ctx_set_batched(_P(ctx), int(tile_nb), int(ctas_per_sm), int(spin_cycles), int(inject_stall))
+
+
+def exa_loglik_noalloc(cuda_stream: int, locs, z, theta, n: int, loglik: ctypes.c_double) -> int:
+    """Allocation-free FP64 log-likelihood (n <= 2048); see include/exa.h."""
+    return lib().exa_loglik_noalloc(_P(cuda_stream or None), _P(_dev_ptr(locs, "locs", 2 * n)),
+                                    _P(_dev_ptr(z, "z", n)), _theta(theta), n, ctypes.byref(loglik))
