@@ -170,4 +170,29 @@ __device__ __forceinline__ double matern_value(const MaternParams& P, double r) 
   return P.sigma2 * exp(e) * knu;
 }
 
+// Segment of x for the table (x finite, 2^kTabE0 <= x < 2^(kTabE0 + kTabOct)):
+// integer work on the bit pattern only.
+__device__ __forceinline__ int table_segment(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const int sub = (int)((b >> (52 - 3)) & (kTabSub - 1));
+  return (e - kTabE0) * kTabSub + sub;
+}
+
+// Sigma at distance r from the table (exact routine below 2^kTabE0).
+__device__ __forceinline__ double matern_value_tab(const MaternParams& P, const MaternTable* __restrict__ T, double r) {
+  if (r == 0.0) return P.sigma2;
+  const double x = r / P.beta;
+  if (!(x > 0.0)) return x;
+  if (x > 800.0) return 0.0;
+  if (x < 0.0625) return matern_value(P, r);
+  const int sgi = table_segment(x);
+  const double t = fma(x, __ldg(&T->ih[sgi]), __ldg(&T->mc[sgi]));
+  const double* c = T->a[sgi];
+  double q = __ldg(&c[kTabDeg]);
+#pragma unroll
+  for (int k = kTabDeg - 1; k >= 0; --k) q = fma(q, t, __ldg(&c[k]));
+  return P.sigma2 * exp(q - x);
+}
+
 }  // namespace exa

@@ -114,6 +114,22 @@ exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb) 
   return EXA_OK;
 }
 
+exa_status matern_table(exa_ctx* c, const MaternParams& P, const MaternTable** tab) {
+  const size_t bytes = sizeof(MaternTable) + (size_t)kTabSeg * (kTabDeg + 1) * sizeof(double) + 256;
+  exa_status st = ensure(c, c->table, bytes, "interpolation table");
+  if (st != EXA_OK) return st;
+  MaternTable* t = (MaternTable*)c->table.p;
+  double* nodes = (double*)((char*)c->table.p + ((sizeof(MaternTable) + 255) / 256) * 256);
+  cudaError_t e;
+  {
+    ProfScope ps(c, PK_GEN, 0.0, 0.0, 2);
+    e = launch_matern_table(c->stream, P, t, nodes);
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "table build");
+  *tab = t;
+  return EXA_OK;
+}
+
 // Read the device status after a synchronise; map a failed pivot to NOT_SPD.
 exa_status read_status(exa_ctx* c) {
   cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream);
@@ -175,6 +191,7 @@ void exa_ctx_destroy(exa_ctx* c) {
   free_buf(c, c->logdet_part);
   free_buf(c, c->vec);
   free_buf(c, c->partial);
+  free_buf(c, c->table);
   release_extra(c);
   release_batched(c);
   prof_release(c);
@@ -214,7 +231,9 @@ exa_status exa_covariance(exa_ctx* c, const double* d_locs, int64_t n, const dou
   if (st != EXA_OK) return st;
   MaternParams P;
   matern_params(theta, &P);
-  cudaError_t e = launch_matern_gen(c->stream, d_locs, n, n, P, d_sigma, ld);
+  const MaternTable* tab = nullptr;
+  if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
+  cudaError_t e = launch_matern_gen(c->stream, d_locs, n, n, P, d_sigma, ld, nullptr, tab);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "covariance generation");
   return EXA_OK;
@@ -292,10 +311,12 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
   MaternParams P;
   matern_params(theta, &P);
   cudaEventRecord(c->ev[0], c->stream);
+  const MaternTable* tab = nullptr;
+  if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
   cudaError_t e;
   {
     ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
-    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
+    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad, nullptr, tab);
   }
   if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
   cudaEventRecord(c->ev[1], c->stream);
@@ -355,7 +376,9 @@ extern "C" exa_status exa_simulate(exa_ctx* c, const double* d_locs, const doubl
   if (prec == EXA_FP64) {
     MaternParams P;
     matern_params(theta, &P);
-    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad);
+    const MaternTable* tab = nullptr;
+    if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
+    e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad, nullptr, tab);
     if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
     if ((st = factor_fp64(c, A, npad, npad, nb)) != EXA_OK) return st;
   } else {

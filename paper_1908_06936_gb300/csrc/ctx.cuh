@@ -39,6 +39,7 @@ struct exa_ctx {
   exa::DevBuf logdet_part;  // per-tile log-det sums
   exa::DevBuf vec;          // n-vectors
   exa::DevBuf partial;      // reduction partials
+  exa::DevBuf table;        // per-theta Matérn interpolation table + its node values
   // mixed precision
   exa::DevBuf mx_sigma;     // FP64 copy of Sigma for the refinement residual
   exa::DevBuf mx_split;     // split-precision panel operands (A role)
@@ -86,6 +87,8 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
 exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                         exa_prec prec, exa_result* out);
 void release_extra(exa_ctx* c);
+// Build the interpolation table for theta on the context stream; returns its device address.
+exa_status matern_table(exa_ctx* c, const MaternParams& P, const MaternTable** tab);
 void release_batched(exa_ctx* c);
 // Lay out a split operand of `rows` x K in `buf` (T3 planes and/or OZ digits) and build its TMA maps.
 exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz);

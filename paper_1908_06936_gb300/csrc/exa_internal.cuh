@@ -52,6 +52,24 @@ struct MaternParams {
 // Host: fill the parameter block for theta (defined in matern.cu).
 void matern_params(const double theta[3], MaternParams* p);
 
+// Per-theta interpolation table of q(x) = ln(2^(1-nu)/Gamma(nu) x^nu e^x K_nu(x)), so that
+// Sigma = sigma^2 exp(q(x) - x).  Segments follow the binary exponent of x: octave
+// [2^e, 2^(e+1)), e in [kTabE0, kTabE0 + kTabOct), split into kTabSub equal pieces; on
+// each, q is a degree-kTabDeg polynomial in t = (x - centre) / half-width.  Below
+// 2^kTabE0 and above 800 the exact routine / zero apply.
+constexpr int kTabE0 = -4;
+constexpr int kTabOct = 14;
+constexpr int kTabSub = 8;
+constexpr int kTabSeg = kTabOct * kTabSub;
+constexpr int kTabDeg = 10;
+struct MaternTable {
+  double mc[kTabSeg];                  // -centre / half-width
+  double ih[kTabSeg];                  // 1 / half-width
+  double a[kTabSeg][kTabDeg + 1];      // monomial coefficients in t
+};
+// Build the table for one theta (two small kernels) into device memory.
+cudaError_t launch_matern_table(cudaStream_t s, const MaternParams& p, MaternTable* tab, double* nodes);
+
 // Device status block (lives in device memory, one per context).
 struct DevStatus {
   int32_t info;        // 0 ok; 1 not SPD
@@ -70,8 +88,10 @@ struct DevStatus {
 // that a padded matrix factors as diag(L, I).
 // If offmax is non-null, offmax[d] receives (as the bits of a non-negative double)
 // the largest off-diagonal |Sigma_ij| over 256-wide tile pairs (I, J) with I - J = d.
+// With tab != nullptr the entries with x >= 2^kTabE0 come from the table.
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld, unsigned long long* offmax = nullptr);
+                              double* a, int64_t ld, unsigned long long* offmax = nullptr,
+                              const MaternTable* tab = nullptr);
 
 // FP64 tiled Cholesky steps (tile nb <= 128, multiple of 64; n multiple of nb).
 // The triangular-solve steps accept nb <= 256.

@@ -35,7 +35,8 @@ __device__ __forceinline__ void tri_decode(long long b, int& ti, int& tj) {
 // the column-major stores coalesce).
 __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restrict__ locs, int64_t n, int64_t npad,
                                                          const __grid_constant__ MaternParams P, double* __restrict__ a,
-                                                         int64_t ld, unsigned long long* __restrict__ offmax) {
+                                                         int64_t ld, unsigned long long* __restrict__ offmax,
+                                                         const MaternTable* __restrict__ tab) {
   int ti, tj;
   tri_decode(blockIdx.x, ti, tj);
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
@@ -57,7 +58,8 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
     } else {
       const double dx = xi - __ldg(locs + 2 * j);
       const double dy = yi - __ldg(locs + 2 * j + 1);
-      v = matern_value(P, sqrt(dx * dx + dy * dy));
+      const double r = sqrt(dx * dx + dy * dy);
+      v = tab ? matern_value_tab(P, tab, r) : matern_value(P, r);
       vmax = fmax(vmax, fabs(v));
     }
     a[i + j * ld] = v;
@@ -76,11 +78,77 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
 }
 
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld, unsigned long long* offmax) {
+                              double* a, int64_t ld, unsigned long long* offmax, const MaternTable* tab) {
   const long long t = (npad + 63) / 64;
   const long long blocks = t * (t + 1) / 2;
   if (blocks <= 0) return cudaSuccess;
-  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax);
+  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax, tab);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Table construction: q at the kTabDeg + 1 Chebyshev points of every segment by
+// the exact routine, then Chebyshev coefficients and their monomial form.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void segment_geometry(int sgi, double& centre, double& half) {
+  const int e = kTabE0 + sgi / kTabSub, sub = sgi % kTabSub;
+  const double lo = ldexp(1.0 + (double)sub / kTabSub, e);
+  const double w = ldexp(1.0 / kTabSub, e);
+  centre = lo + 0.5 * w;
+  half = 0.5 * w;
+}
+
+__global__ void matern_table_nodes_kernel(const __grid_constant__ MaternParams P, double* __restrict__ nodes) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= kTabSeg * (kTabDeg + 1)) return;
+  const int sgi = id / (kTabDeg + 1), k = id % (kTabDeg + 1);
+  double centre, half;
+  segment_geometry(sgi, centre, half);
+  const double tk = cos(3.14159265358979323846 * (k + 0.5) / (kTabDeg + 1));
+  const double x = centre + half * tk;
+  const double lnx = log(x);
+  double knu, knum1;
+  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
+  nodes[id] = P.logc + P.nu * lnx + log(knu) + (scaled ? 0.0 : x);
+}
+
+__global__ void matern_table_coef_kernel(const double* __restrict__ nodes, MaternTable* __restrict__ T) {
+  const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sgi >= kTabSeg) return;
+  constexpr int N = kTabDeg + 1;
+  const double* q = nodes + sgi * N;
+  double cheb[N];
+  for (int j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += q[k] * cos(3.14159265358979323846 * j * (k + 0.5) / N);
+    cheb[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+  }
+  // monomial coefficients: T_0 = 1, T_1 = t, T_{j+1} = 2 t T_j - T_{j-1}
+  double a[N], tm1[N], t0[N], t1[N];
+  for (int i = 0; i < N; ++i) a[i] = tm1[i] = t0[i] = 0.0;
+  tm1[0] = 1.0;  // T_0
+  t0[1] = 1.0;   // T_1
+  a[0] = cheb[0];
+  for (int i = 0; i < N; ++i) a[i] += cheb[1] * t0[i];
+  for (int j = 2; j < N; ++j) {
+    for (int i = 0; i < N; ++i) t1[i] = (i > 0 ? 2.0 * t0[i - 1] : 0.0) - tm1[i];
+    for (int i = 0; i < N; ++i) a[i] += cheb[j] * t1[i];
+    for (int i = 0; i < N; ++i) {
+      tm1[i] = t0[i];
+      t0[i] = t1[i];
+    }
+  }
+  double centre, half;
+  segment_geometry(sgi, centre, half);
+  T->ih[sgi] = 1.0 / half;
+  T->mc[sgi] = -centre / half;
+  for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
+}
+
+cudaError_t launch_matern_table(cudaStream_t s, const MaternParams& p, MaternTable* tab, double* nodes) {
+  const int total = kTabSeg * (kTabDeg + 1);
+  matern_table_nodes_kernel<<<(total + 127) / 128, 128, 0, s>>>(p, nodes);
+  matern_table_coef_kernel<<<1, 128, 0, s>>>(nodes, tab);
   return cudaGetLastError();
 }
 

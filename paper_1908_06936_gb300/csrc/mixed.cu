@@ -225,10 +225,12 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   MaternParams Pm;
   matern_params(theta, &Pm);
   cudaStream_t s = c->stream;
+  const MaternTable* tab = nullptr;
+  if ((st = matern_table(c, Pm, &tab)) != EXA_OK) return st;
   cudaError_t e = cudaMemsetAsync(offmax, 0, (size_t)(T + 1) * sizeof(unsigned long long), s);
   if (e == cudaSuccess) {
     ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
-    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax);
+    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax, tab);
   }
   if (e == cudaSuccess && sigma_keep)
     e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);

@@ -171,3 +171,16 @@ def test_workspace_limit_reports_nomem():
         with pytest.raises(exa.ExaError) as ei:
             c.loglik(to_dev(locs), to_dev(Z), (1.0, 0.1, 0.5))
         assert ei.value.status == exa.EXA_ERR_NOMEM
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.03, 1.0), (1.0, 0.1, 0.5), (2.0, 0.2, 1.5), (0.7, 0.05, 0.27),
+                                   (1.0, 0.1, 1.999999), (1.0, 1.0, 0.1)])
+def test_covariance_dense_distances(ctx, theta):
+    # points on a line at geometric offsets: x = r / beta sweeps 1e-3 .. 900 across every
+    # table segment boundary (octaves and eighths) and the exact-routine cut-off
+    xs = np.concatenate([[0.0], np.geomspace(1e-3, 900.0, 700) * theta[1]])
+    locs = np.stack([xs, np.zeros_like(xs)], axis=1)
+    ref = np.tril(oracle.covariance(locs, theta))
+    got = lower_colmajor(ctx.covariance(to_dev(locs), theta), locs.shape[0])
+    err = np.abs(got - ref)
+    assert np.all(err <= matern_tol(locs, theta, ref)), float(np.max(err / (np.abs(ref) + 1e-300)))
