@@ -174,7 +174,8 @@ exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, co
  * the arithmetic: EXA_GEMM_T3 (three TF32 products, FP32 accumulation) or
  * EXA_GEMM_OZ (five exact 7-bit BF16 digit slices per row, exact FP32
  * accumulation, FP64 combination).  Shapes: m % 128 == 0, k % 64 == 0,
- * n % 128 == 0 (T3) or n % 32 == 0 (OZ), k <= 512, and k <= 256 for OZ.  */
+ * n % 128 == 0 (T3) or n % 32 == 0 (OZ), and k <= 512 (the digit sums of OZ  *
+ * stay below 2^24 up to k = 512, so its accumulation is exact).             */
 typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1 } exa_gemm_kind;
 exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
                            const double* d_b, double* d_c, int64_t ldc, int store);

@@ -368,7 +368,7 @@ extern "C" exa_status exa_simulate(exa_ctx* c, const double* d_locs, const doubl
   exa_status st = check_theta(c, theta);
   if (st != EXA_OK) return st;
   const int nb = c->tile_nb;
-  const int64_t npad = round_up(n, prec == EXA_FP64 ? nb : 256);
+  const int64_t npad = round_up(n, prec == EXA_FP64 ? nb : kMixPanel);
   if ((st = ensure(c, c->mat, (size_t)npad * npad * sizeof(double), "matrix")) != EXA_OK) return st;
   if ((st = reset_status(c)) != EXA_OK) return st;
   double* A = (double*)c->mat.p;

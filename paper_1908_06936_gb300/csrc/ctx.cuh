@@ -17,6 +17,7 @@ struct DevBuf {
 };
 
 constexpr int kNumEvents = 8;
+constexpr int kMixPanel = 512;     // panel width of the mixed-precision factorisation
 constexpr int kRedPartials = 512;  // partial sums of one two-stage reduction
 
 inline int64_t kPartialDoubles(int64_t npad, int nb) { return 2 * kRedPartials + (npad / 1024 + 2) * (int64_t)nb; }

@@ -87,11 +87,13 @@ struct DevStatus {
 // `a` (leading dim ld).  Rows/cols in [n, npad) are filled as the identity so
 // that a padded matrix factors as diag(L, I).
 // If offmax is non-null, offmax[d] receives (as the bits of a non-negative double)
-// the largest off-diagonal |Sigma_ij| over 256-wide tile pairs (I, J) with I - J = d.
+// the largest off-diagonal |Sigma_ij| over `panel`-wide tile pairs (I, J) with I - J = d.
 // With tab != nullptr the entries with x >= 2^kTabE0 come from the table.
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
                               double* a, int64_t ld, unsigned long long* offmax = nullptr,
-                              const MaternTable* tab = nullptr);
+                              const MaternTable* tab = nullptr, int panel = 256);
+// W (sub*nb square, row-major) <- block diagonal of `sub` inverted nb x nb tiles, zero elsewhere.
+cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w);
 
 // FP64 tiled Cholesky steps (tile nb <= 128, multiple of 64; n multiple of nb).
 // The triangular-solve steps accept nb <= 256.

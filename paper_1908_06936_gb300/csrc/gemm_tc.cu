@@ -48,13 +48,14 @@ __device__ __forceinline__ bool decode_tile(const GemmArgs& g, long long t, int&
     bj = (int)(t % g.nt);
     return true;
   }
-  if (g.enum_mode == kEnumLowerOffBand) {  // TM == TN == 128, band measured in 256-wide tiles
+  if (g.enum_mode == kEnumLowerOffBand) {  // TM == TN == 128, band measured in panel-wide tiles
     tile_tri_decode(t, bi, bj);
-    return (bi / 2 - bj / 2) > g.band;
+    const int per = g.panel / 128;
+    return (bi / per - bj / per) > g.band;
   }
-  // kEnumBand: pairs (I, J) of 256-wide tiles with 0 <= I - J <= band, each split in
-  // (256/TM) x (256/TN) sub-tiles
-  constexpr int SI = 256 / TM, SJ = 256 / TN;
+  // kEnumBand: pairs (I, J) of panel-wide tiles with 0 <= I - J <= band, each split in
+  // (panel/TM) x (panel/TN) sub-tiles
+  const int SI = g.panel / TM, SJ = g.panel / TN;
   const long long pair = t / (SI * SJ);
   const int sub = (int)(t % (SI * SJ));
   const int b = g.band;

@@ -28,7 +28,8 @@ struct GemmArgs {
   int K;                      // reduction length (T3: % 32, OZ: % 64, <= 256 for OZ)
   int enum_mode;              // kEnum*
   int nt;                     // tiles along N (kEnumFull)
-  int band;                   // band width in 256-wide tiles (kEnumLowerOffBand / kEnumBand)
+  int band;                   // band width in panel tiles (kEnumLowerOffBand / kEnumBand)
+  int panel;                  // panel width (256 or 512) that `band` is measured in
   long long ntiles;           // number of enumerated tiles
   int store;                  // 1: C = A B^T ; 0: C -= A B^T
   int lower_mask;             // skip entries above the diagonal

@@ -36,7 +36,7 @@ __device__ __forceinline__ void tri_decode(long long b, int& ti, int& tj) {
 __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restrict__ locs, int64_t n, int64_t npad,
                                                          const __grid_constant__ MaternParams P, double* __restrict__ a,
                                                          int64_t ld, unsigned long long* __restrict__ offmax,
-                                                         const MaternTable* __restrict__ tab) {
+                                                         const MaternTable* __restrict__ tab, int oshift) {
   int ti, tj;
   tri_decode(blockIdx.x, ti, tj);
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
@@ -73,16 +73,17 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
       const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
       b = ob > b ? ob : b;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(&offmax[(ti >> 2) - (tj >> 2)], b);
+    if ((threadIdx.x & 31) == 0) atomicMax(&offmax[(ti >> oshift) - (tj >> oshift)], b);
   }
 }
 
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld, unsigned long long* offmax, const MaternTable* tab) {
+                              double* a, int64_t ld, unsigned long long* offmax, const MaternTable* tab, int panel) {
+  const int oshift = panel == 512 ? 3 : 2;  // 64-row generator tiles per panel tile: 2^oshift
   const long long t = (npad + 63) / 64;
   const long long blocks = t * (t + 1) / 2;
   if (blocks <= 0) return cudaSuccess;
-  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax, tab);
+  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax, tab, oshift);
   return cudaGetLastError();
 }
 

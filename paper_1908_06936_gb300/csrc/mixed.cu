@@ -10,7 +10,7 @@
 
 namespace exa {
 
-constexpr int kMixNB = 256;      // panel width = K of every tensor-core product
+constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
@@ -54,60 +54,66 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
 //      most) with OZ, all others with T3.  Storage stays FP64 throughout.
 // ---------------------------------------------------------------------------
 exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band) {
-  const int NB = kMixNB, nb = kMixSub;
+  const int NB = kMixNB, nb = kMixSub, SUB = kMixNB / kMixSub;
   const int T = (int)(npad / NB);
-  if (band < 1) band = 1;
   const int T128 = (int)(npad / nb);
+  if (band < 1) band = 1;
   exa_status st;
   if (prec != EXA_MIXED_TF32X3) return set_err(c, EXA_ERR_ARG, "precision %d has no mixed kernel", (int)prec);
   if ((st = ensure(c, c->w_all, (size_t)T128 * nb * nb * sizeof(double), "inverted diagonal tiles")) != EXA_OK)
     return st;
-  if ((st = ensure(c, c->panel, (size_t)(nb * nb + NB * NB + nb * nb) * sizeof(double), "panel")) != EXA_OK)
-    return st;
+  if ((st = ensure(c, c->panel, (size_t)(NB * nb + nb * nb) * sizeof(double), "panel")) != EXA_OK) return st;
   if ((st = ensure(c, c->logdet_part, (size_t)T128 * sizeof(double), "log-det partials")) != EXA_OK) return st;
   if ((st = ensure_split(c, c->sp_a, c->mx_split, npad, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
-  if ((st = ensure(c, c->mx_w2, (size_t)T * NB * NB * sizeof(double), "diagonal block inverses")) != EXA_OK)
-    return st;
+  if ((st = ensure(c, c->mx_w2, (size_t)NB * NB * sizeof(double), "diagonal block inverse")) != EXA_OK) return st;
   double* W = (double*)c->w_all.p;
-  double* P = (double*)c->panel.p;       // 128 x 128 FP64 panel of the in-block TRSM
-  double* tmp = P + nb * nb;             // 128 x 128 scratch
+  double* P = (double*)c->panel.p;       // (NB - 128) x 128 FP64 panel of the in-block TRSM
+  double* tmp = P + (size_t)NB * nb;     // 128 x 128 scratch
   double* LD = (double*)c->logdet_part.p;
+  double* W2 = (double*)c->mx_w2.p;      // NB x NB inverse of the diagonal block (row-major)
   cudaStream_t s = c->stream;
+  const double dnb = nb;
   for (int k = 0; k < T; ++k) {
     const int64_t k0 = (int64_t)k * NB;
-    const double dnb = nb;
-    cudaError_t e;
-    {
-      ProfScope ps(c, PK_POTRF, 2.0 * dnb * dnb * dnb, 48.0 * dnb * dnb, 2);
-      e = launch_potrf_diag(s, a, ld, k0, nb, W, LD, c->d_status);
-      if (e == cudaSuccess) {
-        ProfScope p2(c, PK_TRSM64, 2.0 * dnb * dnb * dnb, 24.0 * dnb * dnb);
-        e = launch_trsm_panel(s, a, ld, k0, nb, nb, W, P, c->d_status);
+    cudaError_t e = cudaSuccess;
+    // 1. FP64 factorisation of the diagonal block as SUB sub-tiles of 128
+    for (int kk = 0; kk < SUB && e == cudaSuccess; ++kk) {
+      const int64_t s0 = k0 + (int64_t)kk * nb;
+      const int64_t mm = (int64_t)(SUB - 1 - kk) * nb;  // rows below within the block
+      {
+        ProfScope ps(c, PK_POTRF, dnb * dnb * dnb, 24.0 * dnb * dnb);
+        e = launch_potrf_diag(s, a, ld, s0, nb, W, LD, c->d_status);
       }
-      if (e == cudaSuccess) {
-        ProfScope p3(c, PK_SYRK64, dnb * (dnb + 64.0) * dnb, 16.0 * dnb * dnb);
-        e = launch_syrk_update(s, a, ld, k0 + nb, nb, nb, P, c->d_status);
+      if (e == cudaSuccess && mm > 0) {
+        ProfScope p2(c, PK_TRSM64, 2.0 * (double)mm * dnb * dnb, 24.0 * (double)mm * dnb);
+        e = launch_trsm_panel(s, a, ld, s0, nb, mm, W, P, c->d_status);
       }
-      if (e == cudaSuccess) e = launch_potrf_diag(s, a, ld, k0 + nb, nb, W, LD, c->d_status);
+      if (e == cudaSuccess && mm > 0) {
+        ProfScope p3(c, PK_SYRK64, (double)mm * ((double)mm + 64.0) * dnb, 16.0 * (double)mm * (double)mm);
+        e = launch_syrk_update(s, a, ld, s0 + nb, mm, nb, P, c->d_status);
+      }
     }
     if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
-    double* W2 = (double*)c->mx_w2.p + (int64_t)k * NB * NB;  // 256 x 256 inverse of the block (row-major)
-    const double* w00 = W + (k0 / nb) * (int64_t)nb * nb;
-    const double* w11 = w00 + (int64_t)nb * nb;
+    if (k == T - 1) break;
+    // 2. W = L_kk^-1 by block rows: W_ii from the tiles, W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj
     {
-      ProfScope ps(c, PK_DGEMM_SMALL, 4.0 * dnb * dnb * dnb, 8.0 * 8.0 * dnb * dnb, 3);
-      e = launch_assemble_w2(s, w00, w11, nb, W2);
-      // tmp = L10 W00 ;  W10 = -W11 tmp
-      if (e == cudaSuccess)
-        e = launch_dgemm_nt_small(s, nb, nb, nb, 1.0, a + (k0 + nb) + k0 * ld, 1, ld, w00, 1, nb, 0.0, tmp, nb, 1,
-                                  c->d_status);
-      if (e == cudaSuccess)
-        e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, w11, nb, 1, tmp, 1, nb, 0.0, W2 + (int64_t)nb * NB, NB, 1,
-                                  c->d_status);
+      ProfScope ps(c, PK_DGEMM_SMALL, (double)NB * NB * NB / 3.0, 8.0 * 4.0 * NB * NB, 1 + SUB * (SUB - 1));
+      const double* wk = W + (k0 / nb) * (int64_t)nb * nb;
+      e = launch_assemble_wblocks(s, wk, nb, SUB, W2);
+      for (int i = 1; i < SUB && e == cudaSuccess; ++i) {
+        for (int j = 0; j < i && e == cudaSuccess; ++j) {
+          const int K = (i - j) * nb;
+          const double* Lrow = a + (k0 + (int64_t)i * nb) + (k0 + (int64_t)j * nb) * ld;
+          e = launch_dgemm_nt_small(s, nb, nb, K, 1.0, Lrow, 1, ld, W2 + (int64_t)(j * nb) * NB + j * nb, 1, NB, 0.0,
+                                    tmp, nb, 1, c->d_status);
+          if (e == cudaSuccess)
+            e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, wk + (int64_t)i * nb * nb, nb, 1, tmp, 1, nb, 0.0,
+                                      W2 + (int64_t)(i * nb) * NB + j * nb, NB, 1, c->d_status);
+        }
+      }
     }
     if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
-    if (k == T - 1) break;
     const int64_t r0 = k0 + NB;
     const int64_t m = npad - r0;
     double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
@@ -116,14 +122,15 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
       e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
       if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
     }
-    if (e != cudaSuccess) return cuda_err(c, e, "inverse / split launch");
-    // TRSM on the tensor cores: L_ik = A_ik W^T
+    if (e != cudaSuccess) return cuda_err(c, e, "split launch");
+    // 3. panel TRSM on the tensor cores: L_ik = A_ik W^T
     const int64_t rb = m < (int64_t)band * NB ? m : (int64_t)band * NB;
     GemmArgs g;
     memset(&g, 0, sizeof(g));
     g.C = a;
     g.ldc = ld;
     g.K = NB;
+    g.panel = NB;
     g.st = c->d_status;
     g.store = 1;
     g.enum_mode = kEnumFull;
@@ -150,11 +157,12 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
       e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
-    // trailing update
+    // 4. trailing update: band tiles exact (OZ), the rest TF32x3
     memset(&g, 0, sizeof(g));
     g.C = a;
     g.ldc = ld;
     g.K = NB;
+    g.panel = NB;
     g.st = c->d_status;
     g.store = 0;
     g.lower_mask = 1;
@@ -165,7 +173,7 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
     g.ntiles = t128 * (t128 + 1) / 2;
     long long t3_tiles = 0;  // tiles this launch computes (off the band)
     for (long long bi = 0; bi < t128; ++bi) {
-      const long long lim = 2 * (bi / 2 - band);
+      const long long lim = (long long)SUB * (bi / SUB - band);
       if (lim > 0) t3_tiles += lim;
     }
     if (t3_tiles > 0) {
@@ -177,9 +185,15 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
       const long long tr = m / NB;
       long long pairs = 0;
       for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
+      const long long per_pair = (long long)(NB / 128) * (NB / 32);
       g.enum_mode = kEnumBand;
-      g.ntiles = pairs * (NB / 128) * (NB / 32);
-      const double oz_tiles = (double)pairs * 16.0 - 4.0 * (double)tr;  // diagonal pairs skip 4 sub-tiles
+      g.ntiles = pairs * per_pair;
+      // diagonal pairs skip their sub-tiles strictly above the diagonal
+      long long skipped = 0;
+      for (int h = 0; h < NB / 128; ++h)
+        for (int q = 0; q < NB / 32; ++q)
+          if ((long long)q * 32 > (long long)h * 128 + 127) ++skipped;
+      const double oz_tiles = (double)pairs * per_pair - (double)skipped * (double)tr;
       ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles);
       e = launch_gemm_oz(s, c->sp_a, c->sp_a, g);
     }
@@ -188,13 +202,13 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   return EXA_OK;
 }
 
-// x = (L L^T)^-1 rhs with the FP64-stored factor, on 256-wide tiles with the
-// stored inverses of the diagonal blocks.
+// x = (L L^T)^-1 rhs with the FP64-stored factor, on 128-wide tiles with the
+// stored inverses of the diagonal sub-tiles.
 static cudaError_t solve_llt(exa_ctx* c, const double* a, int64_t ld, int64_t npad, const double* rhs, double* x,
                              double* work, double* part) {
-  const int nb = kMixNB;
+  const int nb = kMixSub;
   const int T = (int)(npad / nb);
-  const double* W = (const double*)c->mx_w2.p;
+  const double* W = (const double*)c->w_all.p;
   cudaError_t e = cudaMemcpyAsync(work, rhs, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   for (int k = 0; k < T && e == cudaSuccess; ++k) {
     const double rows = (double)(npad - (int64_t)k * nb);
@@ -230,7 +244,7 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   cudaError_t e = cudaMemsetAsync(offmax, 0, (size_t)(T + 1) * sizeof(unsigned long long), s);
   if (e == cudaSuccess) {
     ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
-    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax, tab);
+    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax, tab, kMixNB);
   }
   if (e == cudaSuccess && sigma_keep)
     e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -363,7 +377,7 @@ extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m,
     return set_err(c, EXA_ERR_ARG, "bad gemm arguments");
   const bool oz = (kind == EXA_GEMM_OZ);
   if (kind != EXA_GEMM_T3 && kind != EXA_GEMM_OZ) return set_err(c, EXA_ERR_ARG, "unknown gemm kind");
-  if (m % 128 || k % 64 || k > kSplitMaxK || (oz ? (n % 32 || k > 256) : (n % 128)))
+  if (m % 128 || k % 64 || k > kSplitMaxK || (oz ? (n % 32) : (n % 128)))
     return set_err(c, EXA_ERR_ARG, "gemm shape m=%lld n=%lld k=%lld not supported", (long long)m, (long long)n,
                    (long long)k);
   exa_status st;
