@@ -121,6 +121,10 @@ cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double al
                                   int64_t ac, const double* b, int64_t br, int64_t bc, double beta, double* c,
                                   int64_t cr, int64_t cc, const DevStatus* st);
 cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w);
+// Persistent forward + backward solve with 128-wide tiles: x = (L L^T)^-1 rhs.
+// rhs_work (npad, overwritten), sbuf (npad), flags (2 npad/128 + 1 ints) are scratch.
+cudaError_t launch_llt_solve_persistent(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* w,
+                                        double* rhs_work, double* x, double* sbuf, int* flags, DevStatus* st);
 // Refinement helpers.
 cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y);
 cudaError_t launch_residual(cudaStream_t s, const double* z, const double* y, double* r, int64_t n);

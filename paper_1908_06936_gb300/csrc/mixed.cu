@@ -206,21 +206,12 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
 // stored inverses of the diagonal sub-tiles.
 static cudaError_t solve_llt(exa_ctx* c, const double* a, int64_t ld, int64_t npad, const double* rhs, double* x,
                              double* work, double* part) {
-  const int nb = kMixSub;
-  const int T = (int)(npad / nb);
-  const double* W = (const double*)c->w_all.p;
+  // part holds the backward partial sums (npad doubles) followed by the flags
   cudaError_t e = cudaMemcpyAsync(work, rhs, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-  for (int k = 0; k < T && e == cudaSuccess; ++k) {
-    const double rows = (double)(npad - (int64_t)k * nb);
-    ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb);
-    e = launch_trsv_fwd_step(c->stream, a, ld, npad, nb, k, W, x, work, c->d_status);
-  }
-  for (int k = T - 1; k >= 0 && e == cudaSuccess; --k) {
-    const double rows = (double)(npad - (int64_t)k * nb);
-    ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb, 2);
-    e = launch_trsv_bwd_step(c->stream, a, ld, npad, nb, k, W, x, part, c->d_status);
-  }
-  return e;
+  if (e != cudaSuccess) return e;
+  ProfScope ps(c, PK_TRSV, 2.0 * (double)npad * (double)npad, 8.0 * (double)npad * (double)npad, 2);
+  return launch_llt_solve_persistent(c->stream, a, ld, npad, (const double*)c->w_all.p, work, x, part,
+                                     (int*)(part + npad), c->d_status);
 }
 
 // Generation (FP64, with the per-offset maxima for the precision map), the
@@ -298,7 +289,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   if ((st = ensure(c, c->mx_sigma, (size_t)npad * npad * sizeof(double), "FP64 covariance copy")) != EXA_OK)
     return st;
   if ((st = ensure(c, c->mx_vec, (size_t)6 * npad * sizeof(double), "refinement vectors")) != EXA_OK) return st;
-  if ((st = ensure(c, c->partial, (size_t)(kPartialDoubles(npad, kMixNB)) * sizeof(double), "partials")) != EXA_OK)
+  if ((st = ensure(c, c->partial, (size_t)(2 * kRedPartials + 2 * npad + 64) * sizeof(double), "partials")) != EXA_OK)
     return st;
   if ((st = reset_status(c)) != EXA_OK) return st;
   double* S = (double*)c->mx_sigma.p;

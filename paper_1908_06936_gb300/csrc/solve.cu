@@ -259,3 +259,184 @@ cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t
 }
 
 }  // namespace exa
+
+namespace exa {
+
+// ---------------------------------------------------------------------------
+// Persistent block triangular solves (one cooperative launch per solve).
+// 128-row blocks with stored row-major inverses W_k of the diagonal tiles.
+// CTA c owns the blocks b with b % gridDim.x == c and is the only writer of
+// their right-hand side / partial sums, so every sum runs in a fixed order.
+// Block k's result is published with a flag (release); readers wait on it with
+// a bounded spin (acquire) and read it from L2.
+// ---------------------------------------------------------------------------
+constexpr int kPNB = 128;
+
+struct PTrsvArgs {
+  const double* a;
+  int64_t ld, npad;
+  int T;
+  const double* w;
+  double* z;     // forward: working right-hand side (in: rhs);  backward: partial sums s (zeroed)
+  double* y;     // forward: output L^-1 rhs;  backward: in y, out L^-T y (in place)
+  int* flags;    // T flags, zeroed
+  int* abort;
+  DevStatus* st;
+  long long spin;
+};
+
+__device__ __forceinline__ bool ptrsv_wait(const int* f, volatile int* abort, long long spin) {
+  if (*(volatile const int*)f) return true;
+  const long long t0 = clock64();
+  while (!*(volatile const int*)f) {
+    if (*abort) return false;
+    if (clock64() - t0 > spin) return false;
+    __nanosleep(100);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void ptrsv_fail(const PTrsvArgs& g, int site) {
+  if (atomicExch(g.abort, 1) == 0 && atomicExch(&g.st->timeout, 1) == 0) g.st->timeout_where = site;
+}
+
+__global__ void __launch_bounds__(256) trsv_fwd_persistent_kernel(PTrsvArgs g) {
+  __shared__ double yk[kPNB];
+  __shared__ double red[2][kPNB];
+  __shared__ int ok;
+  const int tid = threadIdx.x, row = tid & (kPNB - 1), half = tid >> 7;
+  const int G = gridDim.x, me = blockIdx.x;
+  if (*(volatile const int*)&g.st->info) return;
+  for (int k = 0; k < g.T; ++k) {
+    const int64_t k0 = (int64_t)k * kPNB;
+    if (k % G == me) {
+      // z_k is final: every update to it was applied by this CTA, in order
+      const double* W = g.w + (int64_t)k * kPNB * kPNB;
+      double s = 0.0;
+      for (int t = half * 64; t < half * 64 + 64 && t <= row; ++t) s = fma(W[row * kPNB + t], __ldcg(&g.z[k0 + t]), s);
+      red[half][row] = s;
+      __syncthreads();
+      if (tid < kPNB) {
+        const double v = red[0][tid] + red[1][tid];
+        yk[tid] = v;
+        g.y[k0 + tid] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicExch(&g.flags[k], 1);
+      }
+    } else {
+      if (tid == 0) {
+        ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
+        if (!ok) ptrsv_fail(g, 41);
+        __threadfence();
+      }
+      __syncthreads();
+      if (!ok) return;
+      if (tid < kPNB) yk[tid] = __ldcg(&g.y[k0 + tid]);
+      __syncthreads();
+    }
+    // z_b -= L_bk y_k for this CTA's blocks b > k, nearest first
+    int b = k + 1 + ((me - (k + 1)) % G + G) % G;
+    for (; b < g.T; b += G) {
+      const int64_t r = (int64_t)b * kPNB + row;
+      const double* col = g.a + r + k0 * g.ld;
+      double s = 0.0;
+#pragma unroll 8
+      for (int t = half * 64; t < half * 64 + 64; ++t) s = fma(__ldcg(col + (int64_t)t * g.ld), yk[t], s);
+      red[half][row] = s;
+      __syncthreads();
+      if (tid < kPNB) g.z[r] = g.z[r] - (red[0][tid] + red[1][tid]);
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) trsv_bwd_persistent_kernel(PTrsvArgs g) {
+  __shared__ double ak[kPNB];
+  __shared__ double v[kPNB];
+  __shared__ int ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x, me = blockIdx.x;
+  if (*(volatile const int*)&g.st->info) return;
+  for (int k = g.T - 1; k >= 0; --k) {
+    const int64_t k0 = (int64_t)k * kPNB;
+    if (k % G == me) {
+      // a_k = W_k^T (y_k - s_k); s_k was accumulated by this CTA, in order
+      if (tid < kPNB) v[tid] = g.y[k0 + tid] - g.z[k0 + tid];
+      __syncthreads();
+      const double* W = g.w + (int64_t)k * kPNB * kPNB;
+      if (tid < kPNB) {
+        double s = 0.0;
+        for (int t = tid; t < kPNB; ++t) s = fma(W[t * kPNB + tid], v[t], s);
+        ak[tid] = s;
+        g.y[k0 + tid] = s;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicExch(&g.flags[k], 1);
+      }
+    } else {
+      if (tid == 0) {
+        ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
+        if (!ok) ptrsv_fail(g, 42);
+        __threadfence();
+      }
+      __syncthreads();
+      if (!ok) return;
+      if (tid < kPNB) ak[tid] = __ldcg(&g.y[k0 + tid]);
+      __syncthreads();
+    }
+    // s_j += L_kj^T a_k for this CTA's blocks j < k, nearest first: warp per column
+    int j = k - 1 - ((k - 1 - me) % G + G) % G;
+    for (; j >= 0; j -= G) {
+      for (int c = warp; c < kPNB; c += 8) {
+        const double* col = g.a + k0 + ((int64_t)j * kPNB + c) * g.ld;
+        double s = 0.0;
+#pragma unroll
+        for (int r = lane; r < kPNB; r += 32) s = fma(__ldcg(col + r), ak[r], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) g.z[(int64_t)j * kPNB + c] += s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static int ptrsv_grid() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0, per2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trsv_fwd_persistent_kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, trsv_bwd_persistent_kernel, 256, 0);
+    if (per2 < per) per = per2;
+    if (per > 2) per = 2;
+    grid = (per < 1 ? 1 : per) * sms;
+  }
+  return grid;
+}
+
+// Forward (x = L^-1 rhs, rhs overwritten) then backward (x = L^-T x) solve.
+// work: npad doubles; flags: 2 T + 1 ints (zeroed here).
+cudaError_t launch_llt_solve_persistent(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* w,
+                                        double* rhs_work, double* x, double* sbuf, int* flags, DevStatus* st) {
+  const int T = (int)(npad / kPNB);
+  cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)(2 * T + 1) * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf, 0, (size_t)npad * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const int grid = ptrsv_grid() < T ? ptrsv_grid() : T;
+  PTrsvArgs g{a, ld, npad, T, w, rhs_work, x, flags, flags + 2 * T, st, 2000000000LL};
+  void* args[] = {&g};
+  e = cudaLaunchCooperativeKernel((const void*)trsv_fwd_persistent_kernel, grid, 256, args, 0, s);
+  if (e != cudaSuccess) return e;
+  PTrsvArgs g2{a, ld, npad, T, w, sbuf, x, flags + T, flags + 2 * T, st, 2000000000LL};
+  void* args2[] = {&g2};
+  return cudaLaunchCooperativeKernel((const void*)trsv_bwd_persistent_kernel, grid, 256, args2, 0, s);
+}
+
+}  // namespace exa
