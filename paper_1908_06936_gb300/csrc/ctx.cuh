@@ -43,9 +43,10 @@ struct exa_ctx {
   exa::DevBuf table;        // per-theta Matérn interpolation table + its node values
   // mixed precision
   exa::DevBuf mx_sigma;     // FP64 copy of Sigma for the refinement residual
-  exa::DevBuf mx_split;     // split-precision panel operands (A role)
+  exa::DevBuf mx_split;     // split-precision panel operands (A role), two buffers by step parity
+  exa::DevBuf mx_split2;
   exa::DevBuf mx_split_b;   // split-precision operands (B role: inverse diagonal block / test B)
-  exa::SplitOperand sp_a, sp_b;
+  exa::SplitOperand sp_a, sp_a2, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
   exa::DevBuf mx_w2;        // inverses of the 256-wide diagonal blocks (for the solves)
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
@@ -67,6 +68,8 @@ struct exa_ctx {
   double* d_scalars = nullptr;
   double* h_scalars = nullptr;          // pinned
   cudaEvent_t ev[exa::kNumEvents] = {};
+  cudaStream_t side = nullptr;          // look-ahead stream of the mixed factorisation
+  cudaEvent_t la_ev[2] = {};            // look-ahead hand-off events
   exa::Prof prof;
 };
 

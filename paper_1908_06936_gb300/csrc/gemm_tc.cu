@@ -620,7 +620,10 @@ static int num_sms() {
   return n;
 }
 
-cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g) {
+int tc_num_sms() { return num_sms(); }
+
+cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                           int max_ctas) {
   if (g.ntiles <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -629,12 +632,15 @@ cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOpe
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int grid = (int)(g.ntiles < num_sms() ? g.ntiles : num_sms());
+  int cap = num_sms();
+  if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
+  const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
   gemm_t3_kernel<<<grid, kGemmThreads, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g) {
+cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                           int max_ctas) {
   if (g.ntiles <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -643,7 +649,9 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int grid = (int)(g.ntiles < num_sms() ? g.ntiles : num_sms());
+  int cap = num_sms();
+  if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
+  const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
   GemmArgs g2 = g;
   g2.ea = A.ex;
   g2.eb = B.ex;

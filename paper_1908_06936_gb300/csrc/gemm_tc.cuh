@@ -56,7 +56,11 @@ cudaError_t make_split_maps(SplitOperand& op);
 // rows [0, rows) of src (element (r, k) at src[r*rs + k*cs]) -> operand rows [out_row0, ...)
 cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int64_t cs, int rows, int K,
                               SplitOperand& op, int out_row0);
-cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g);
-cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g);
+// max_ctas > 0 caps the persistent grid (to leave SMs to concurrent work).
+cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                           int max_ctas = 0);
+cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                           int max_ctas = 0);
+int tc_num_sms();
 
 }  // namespace exa

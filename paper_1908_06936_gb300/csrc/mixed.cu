@@ -13,6 +13,7 @@ namespace exa {
 constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
+constexpr int kLookaheadSMs = 12;         // SMs left to the look-ahead stream during a trailing update
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 
@@ -53,8 +54,199 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
 //      diagonal tile and its neighbours, where the Schur complement cancels
 //      most) with OZ, all others with T3.  Storage stays FP64 throughout.
 // ---------------------------------------------------------------------------
-exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band) {
+struct MixStep {
+  exa_ctx* c;
+  double* a;
+  int64_t ld, npad;
+  int band, T;
+};
+
+// FP64 diagonal block k, its inverse, the panel splits and the tensor-core TRSM
+// L_ik = A_ik W^T, all on stream s; the split of panel k lands in `sp`.
+// `ctas` caps the persistent grids of the TRSM (0: all SMs).
+static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOperand& sp, int ctas) {
+  exa_ctx* c = M.c;
+  double* a = M.a;
+  const int64_t ld = M.ld, npad = M.npad;
   const int NB = kMixNB, nb = kMixSub, SUB = kMixNB / kMixSub;
+  double* W = (double*)c->w_all.p;
+  double* P = (double*)c->panel.p;       // (NB - 128) x 128 FP64 panel of the in-block TRSM
+  double* tmp = P + (size_t)NB * nb;     // 128 x 128 scratch
+  double* LD = (double*)c->logdet_part.p;
+  double* W2 = (double*)c->mx_w2.p;      // NB x NB inverse of the diagonal block (row-major)
+  const double dnb = nb;
+  const int64_t k0 = (int64_t)k * NB;
+  cudaError_t e = cudaSuccess;
+  // 1. FP64 factorisation of the diagonal block as SUB sub-tiles of 128
+  for (int kk = 0; kk < SUB && e == cudaSuccess; ++kk) {
+    const int64_t s0 = k0 + (int64_t)kk * nb;
+    const int64_t mm = (int64_t)(SUB - 1 - kk) * nb;  // rows below within the block
+    {
+      ProfScope ps(c, PK_POTRF, dnb * dnb * dnb, 24.0 * dnb * dnb, 1, s, true);
+      e = launch_potrf_diag(s, a, ld, s0, nb, W, LD, c->d_status);
+    }
+    if (e == cudaSuccess && mm > 0) {
+      ProfScope p2(c, PK_TRSM64, 2.0 * (double)mm * dnb * dnb, 24.0 * (double)mm * dnb, 1, s, true);
+      e = launch_trsm_panel(s, a, ld, s0, nb, mm, W, P, c->d_status);
+    }
+    if (e == cudaSuccess && mm > 0) {
+      ProfScope p3(c, PK_SYRK64, (double)mm * ((double)mm + 64.0) * dnb, 16.0 * (double)mm * (double)mm, 1, s, true);
+      e = launch_syrk_update(s, a, ld, s0 + nb, mm, nb, P, c->d_status);
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
+  if (k == M.T - 1) return EXA_OK;
+  // 2. W = L_kk^-1 by block rows: W_ii from the tiles, W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj
+  {
+    ProfScope ps(c, PK_DGEMM_SMALL, (double)NB * NB * NB / 3.0, 8.0 * 4.0 * NB * NB, 1 + SUB * (SUB - 1), s, true);
+    const double* wk = W + (k0 / nb) * (int64_t)nb * nb;
+    e = launch_assemble_wblocks(s, wk, nb, SUB, W2);
+    for (int i = 1; i < SUB && e == cudaSuccess; ++i) {
+      for (int j = 0; j < i && e == cudaSuccess; ++j) {
+        const int K = (i - j) * nb;
+        const double* Lrow = a + (k0 + (int64_t)i * nb) + (k0 + (int64_t)j * nb) * ld;
+        e = launch_dgemm_nt_small(s, nb, nb, K, 1.0, Lrow, 1, ld, W2 + (int64_t)(j * nb) * NB + j * nb, 1, NB, 0.0,
+                                  tmp, nb, 1, c->d_status);
+        if (e == cudaSuccess)
+          e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, wk + (int64_t)i * nb * nb, nb, 1, tmp, 1, nb, 0.0,
+                                    W2 + (int64_t)(i * nb) * NB + j * nb, NB, 1, c->d_status);
+      }
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
+  const int64_t r0 = k0 + NB;
+  const int64_t m = npad - r0;
+  double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
+  {
+    ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)(m + NB) * NB, 2, s, true);
+    e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
+    if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, sp, 0);
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "split launch");
+  // 3. panel TRSM on the tensor cores: the first `band` tile rows exact, the rest TF32x3
+  const int64_t rb = m < (int64_t)M.band * NB ? m : (int64_t)M.band * NB;
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.C = a;
+  g.ldc = ld;
+  g.K = NB;
+  g.panel = NB;
+  g.st = c->d_status;
+  g.store = 1;
+  g.enum_mode = kEnumFull;
+  g.c_col0 = k0;
+  g.c_row0 = r0;
+  g.nt = NB / 32;
+  g.ntiles = (rb / 128) * g.nt;
+  {
+    ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 8.0 * (double)rb * NB, 1, s, true);
+    e = launch_gemm_oz(s, sp, c->sp_b, g, ctas);
+  }
+  if (e == cudaSuccess && m > rb) {
+    g.c_row0 = r0 + rb;
+    g.a_row0 = (int)rb;
+    g.nt = NB / 128;
+    g.ntiles = ((m - rb) / 128) * g.nt;
+    ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 8.0 * (double)(m - rb) * NB, 1, s, true);
+    e = launch_gemm_t3(s, sp, c->sp_b, g, ctas);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)m * NB, 1, s, true);
+    e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, sp, 0);
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
+  return EXA_OK;
+}
+
+// Trailing update by panel k restricted to block columns [j_lo, j_hi) (in panel
+// units relative to the trailing region r0 = (k+1) NB): band tiles exact, the
+// rest TF32x3.  `ctas` caps the persistent grids.
+static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const SplitOperand& sp, bool next_column,
+                                  int ctas) {
+  exa_ctx* c = M.c;
+  const int NB = kMixNB, SUB = kMixNB / kMixSub;
+  const int64_t r0 = (int64_t)(k + 1) * NB;
+  const int64_t m = M.npad - r0;
+  const int band = M.band;
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.C = M.a;
+  g.ldc = M.ld;
+  g.K = NB;
+  g.panel = NB;
+  g.st = c->d_status;
+  g.store = 0;
+  g.band = band;
+  cudaError_t e = cudaSuccess;
+  if (next_column) {
+    // block column k+1: rows of its first band+1 tile rows exact, the rest TF32x3
+    const int64_t rb = m < (int64_t)(band + 1) * NB ? m : (int64_t)(band + 1) * NB;
+    g.enum_mode = kEnumFull;
+    g.lower_mask = 1;
+    g.c_row0 = r0;
+    g.c_col0 = r0;
+    g.nt = NB / 32;
+    g.ntiles = (rb / 128) * g.nt;
+    {
+      ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 16.0 * (double)rb * NB, 1, s, true);
+      e = launch_gemm_oz(s, sp, sp, g, ctas);
+    }
+    if (e == cudaSuccess && m > rb) {
+      g.lower_mask = 0;
+      g.c_row0 = r0 + rb;
+      g.a_row0 = (int)rb;
+      g.nt = NB / 128;
+      g.ntiles = ((m - rb) / 128) * g.nt;
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 16.0 * (double)(m - rb) * NB, 1, s, true);
+      e = launch_gemm_t3(s, sp, sp, g, ctas);
+    }
+  } else {
+    // block columns >= k+2: the trailing matrix from r0 + NB, operand rows offset by NB
+    const int64_t m2 = m - NB;
+    if (m2 <= 0) return EXA_OK;
+    g.lower_mask = 1;
+    g.c_row0 = g.c_col0 = r0 + NB;
+    g.a_row0 = g.b_row0 = NB;
+    const long long t128 = m2 / 128;
+    g.enum_mode = kEnumLowerOffBand;
+    g.ntiles = t128 * (t128 + 1) / 2;
+    long long t3_tiles = 0;
+    for (long long bi = 0; bi < t128; ++bi) {
+      const long long lim = (long long)SUB * (bi / SUB - band);
+      if (lim > 0) t3_tiles += lim;
+    }
+    if (t3_tiles > 0) {
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
+                   16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m2 * NB, 1, s, true);
+      e = launch_gemm_t3(s, sp, sp, g, ctas);
+    }
+    if (e == cudaSuccess) {
+      const long long tr = m2 / NB;
+      long long pairs = 0;
+      for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
+      const long long per_pair = (long long)(NB / 128) * (NB / 32);
+      g.enum_mode = kEnumBand;
+      g.ntiles = pairs * per_pair;
+      long long skipped = 0;
+      for (int h = 0; h < NB / 128; ++h)
+        for (int q = 0; q < NB / 32; ++q)
+          if ((long long)q * 32 > (long long)h * 128 + 127) ++skipped;
+      const double oz_tiles = (double)pairs * per_pair - (double)skipped * (double)tr;
+      ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles, 1, s, true);
+      e = launch_gemm_oz(s, sp, sp, g, ctas);
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "trailing update launch");
+  return EXA_OK;
+}
+
+// Mixed-precision tiled Cholesky with one step of look-ahead: while the main
+// stream applies panel k to block columns >= k+2 (on all but kLookaheadSMs
+// SMs), the side stream factors diagonal block k+1, inverts it and runs the
+// TRSM of panel k+1 on the reserved SMs.  Panel splits alternate between two
+// buffers so the side stream never overwrites operands still in use.
+exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band) {
+  const int NB = kMixNB, nb = kMixSub;
   const int T = (int)(npad / NB);
   const int T128 = (int)(npad / nb);
   if (band < 1) band = 1;
@@ -65,140 +257,38 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   if ((st = ensure(c, c->panel, (size_t)(NB * nb + nb * nb) * sizeof(double), "panel")) != EXA_OK) return st;
   if ((st = ensure(c, c->logdet_part, (size_t)T128 * sizeof(double), "log-det partials")) != EXA_OK) return st;
   if ((st = ensure_split(c, c->sp_a, c->mx_split, npad, NB, true, true)) != EXA_OK) return st;
+  if ((st = ensure_split(c, c->sp_a2, c->mx_split2, npad, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure(c, c->mx_w2, (size_t)NB * NB * sizeof(double), "diagonal block inverse")) != EXA_OK) return st;
-  double* W = (double*)c->w_all.p;
-  double* P = (double*)c->panel.p;       // (NB - 128) x 128 FP64 panel of the in-block TRSM
-  double* tmp = P + (size_t)NB * nb;     // 128 x 128 scratch
-  double* LD = (double*)c->logdet_part.p;
-  double* W2 = (double*)c->mx_w2.p;      // NB x NB inverse of the diagonal block (row-major)
-  cudaStream_t s = c->stream;
-  const double dnb = nb;
-  for (int k = 0; k < T; ++k) {
-    const int64_t k0 = (int64_t)k * NB;
-    cudaError_t e = cudaSuccess;
-    // 1. FP64 factorisation of the diagonal block as SUB sub-tiles of 128
-    for (int kk = 0; kk < SUB && e == cudaSuccess; ++kk) {
-      const int64_t s0 = k0 + (int64_t)kk * nb;
-      const int64_t mm = (int64_t)(SUB - 1 - kk) * nb;  // rows below within the block
-      {
-        ProfScope ps(c, PK_POTRF, dnb * dnb * dnb, 24.0 * dnb * dnb);
-        e = launch_potrf_diag(s, a, ld, s0, nb, W, LD, c->d_status);
-      }
-      if (e == cudaSuccess && mm > 0) {
-        ProfScope p2(c, PK_TRSM64, 2.0 * (double)mm * dnb * dnb, 24.0 * (double)mm * dnb);
-        e = launch_trsm_panel(s, a, ld, s0, nb, mm, W, P, c->d_status);
-      }
-      if (e == cudaSuccess && mm > 0) {
-        ProfScope p3(c, PK_SYRK64, (double)mm * ((double)mm + 64.0) * dnb, 16.0 * (double)mm * (double)mm);
-        e = launch_syrk_update(s, a, ld, s0 + nb, mm, nb, P, c->d_status);
-      }
+  if (!c->side) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->la_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->la_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, EXA_ERR_CUDA, "look-ahead stream creation failed");
     }
-    if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
-    if (k == T - 1) break;
-    // 2. W = L_kk^-1 by block rows: W_ii from the tiles, W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj
-    {
-      ProfScope ps(c, PK_DGEMM_SMALL, (double)NB * NB * NB / 3.0, 8.0 * 4.0 * NB * NB, 1 + SUB * (SUB - 1));
-      const double* wk = W + (k0 / nb) * (int64_t)nb * nb;
-      e = launch_assemble_wblocks(s, wk, nb, SUB, W2);
-      for (int i = 1; i < SUB && e == cudaSuccess; ++i) {
-        for (int j = 0; j < i && e == cudaSuccess; ++j) {
-          const int K = (i - j) * nb;
-          const double* Lrow = a + (k0 + (int64_t)i * nb) + (k0 + (int64_t)j * nb) * ld;
-          e = launch_dgemm_nt_small(s, nb, nb, K, 1.0, Lrow, 1, ld, W2 + (int64_t)(j * nb) * NB + j * nb, 1, NB, 0.0,
-                                    tmp, nb, 1, c->d_status);
-          if (e == cudaSuccess)
-            e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, wk + (int64_t)i * nb * nb, nb, 1, tmp, 1, nb, 0.0,
-                                      W2 + (int64_t)(i * nb) * NB + j * nb, NB, 1, c->d_status);
-        }
-      }
-    }
-    if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
-    const int64_t r0 = k0 + NB;
-    const int64_t m = npad - r0;
-    double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
-    {
-      ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)(m + NB) * NB, 2);
-      e = launch_split_rows(s, W2, NB, 1, NB, NB, c->sp_b, 0);
-      if (e == cudaSuccess) e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
-    }
-    if (e != cudaSuccess) return cuda_err(c, e, "split launch");
-    // 3. panel TRSM on the tensor cores: L_ik = A_ik W^T
-    const int64_t rb = m < (int64_t)band * NB ? m : (int64_t)band * NB;
-    GemmArgs g;
-    memset(&g, 0, sizeof(g));
-    g.C = a;
-    g.ldc = ld;
-    g.K = NB;
-    g.panel = NB;
-    g.st = c->d_status;
-    g.store = 1;
-    g.enum_mode = kEnumFull;
-    g.c_col0 = k0;
-    g.c_row0 = r0;
-    g.a_row0 = 0;
-    g.b_row0 = 0;
-    g.nt = NB / 32;
-    g.ntiles = (rb / 128) * g.nt;
-    {
-      ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 8.0 * (double)rb * NB);
-      e = launch_gemm_oz(s, c->sp_a, c->sp_b, g);
-    }
-    if (e == cudaSuccess && m > rb) {
-      g.c_row0 = r0 + rb;
-      g.a_row0 = (int)rb;
-      g.nt = NB / 128;
-      g.ntiles = ((m - rb) / 128) * g.nt;
-      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 8.0 * (double)(m - rb) * NB);
-      e = launch_gemm_t3(s, c->sp_a, c->sp_b, g);
-    }
-    if (e == cudaSuccess) {
-      ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)m * NB);
-      e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, c->sp_a, 0);
-    }
-    if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
-    // 4. trailing update: band tiles exact (OZ), the rest TF32x3
-    memset(&g, 0, sizeof(g));
-    g.C = a;
-    g.ldc = ld;
-    g.K = NB;
-    g.panel = NB;
-    g.st = c->d_status;
-    g.store = 0;
-    g.lower_mask = 1;
-    g.band = band;
-    g.c_row0 = g.c_col0 = r0;
-    const long long t128 = m / 128;
-    g.enum_mode = kEnumLowerOffBand;
-    g.ntiles = t128 * (t128 + 1) / 2;
-    long long t3_tiles = 0;  // tiles this launch computes (off the band)
-    for (long long bi = 0; bi < t128; ++bi) {
-      const long long lim = (long long)SUB * (bi / SUB - band);
-      if (lim > 0) t3_tiles += lim;
-    }
-    if (t3_tiles > 0) {
-      ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
-                   16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m * NB);
-      e = launch_gemm_t3(s, c->sp_a, c->sp_a, g);
-    }
-    if (e == cudaSuccess) {
-      const long long tr = m / NB;
-      long long pairs = 0;
-      for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
-      const long long per_pair = (long long)(NB / 128) * (NB / 32);
-      g.enum_mode = kEnumBand;
-      g.ntiles = pairs * per_pair;
-      // diagonal pairs skip their sub-tiles strictly above the diagonal
-      long long skipped = 0;
-      for (int h = 0; h < NB / 128; ++h)
-        for (int q = 0; q < NB / 32; ++q)
-          if ((long long)q * 32 > (long long)h * 128 + 127) ++skipped;
-      const double oz_tiles = (double)pairs * per_pair - (double)skipped * (double)tr;
-      ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles);
-      e = launch_gemm_oz(s, c->sp_a, c->sp_a, g);
-    }
-    if (e != cudaSuccess) return cuda_err(c, e, "trailing update launch");
   }
+  MixStep M{c, a, ld, npad, band, T};
+  cudaStream_t ms = c->stream, ss = c->side;
+  const int sms = tc_num_sms();
+  const int side_ctas = kLookaheadSMs;
+  const int main_ctas = sms - side_ctas;
+  SplitOperand* buf[2] = {&c->sp_a, &c->sp_a2};
+  // panel 0 on the main stream
+  if ((st = panel_factor(M, ms, 0, *buf[0], 0)) != EXA_OK) return st;
+  for (int k = 0; k + 1 < T; ++k) {
+    SplitOperand& cur = *buf[k & 1];
+    // block column k+1 first (everything the side stream needs), on the whole GPU
+    if ((st = trailing_update(M, ms, k, cur, true, 0)) != EXA_OK) return st;
+    cudaEventRecord(c->la_ev[0], ms);
+    cudaStreamWaitEvent(ss, c->la_ev[0], 0);
+    if ((st = panel_factor(M, ss, k + 1, *buf[(k + 1) & 1], side_ctas)) != EXA_OK) return st;
+    cudaEventRecord(c->la_ev[1], ss);
+    // the rest of the trailing matrix on the remaining SMs
+    if ((st = trailing_update(M, ms, k, cur, false, main_ctas)) != EXA_OK) return st;
+    cudaStreamWaitEvent(ms, c->la_ev[1], 0);
+  }
+  if (T == 1) return EXA_OK;
   return EXA_OK;
 }
 

@@ -3,7 +3,7 @@
 
 namespace exa {
 void release_extra(exa_ctx* c) {
-  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split_b, &c->mx_vec, &c->mx_w2, &c->mx_offmax, &c->gr_part, &c->gr_blocks,
+  DevBuf* bufs[] = {&c->mx_sigma, &c->mx_split, &c->mx_split2, &c->mx_split_b, &c->mx_vec, &c->mx_w2, &c->mx_offmax, &c->gr_part, &c->gr_blocks,
                     &c->bt_mat, &c->bt_meta, &c->bt_vec, &c->bt_work};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
@@ -11,6 +11,10 @@ void release_extra(exa_ctx* c) {
     b->p = nullptr;
     b->bytes = 0;
   }
+  if (c->side) cudaStreamDestroy(c->side);
+  c->side = nullptr;
+  for (int i = 0; i < 2; ++i)
+    if (c->la_ev[i]) cudaEventDestroy(c->la_ev[i]);
 }
 }  // namespace exa
 

@@ -22,15 +22,16 @@ static int take_event(Prof& p) {
   return (int)p.used++;
 }
 
-ProfScope::ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels)
-    : c_(c), kind_(kind), flops_(flops), bytes_(bytes) {
+ProfScope::ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels, cudaStream_t stream,
+                     bool on_stream)
+    : c_(c), s_(on_stream ? stream : c->stream), kind_(kind), flops_(flops), bytes_(bytes) {
   Prof& p = c->prof;
   p.launches[kind] += nkernels;
   p.flops[kind] += flops;
   p.bytes[kind] += bytes;
   if (p.on) {
     ev0_ = take_event(p);
-    if (ev0_ >= 0) cudaEventRecord(p.pool[ev0_], c->stream);
+    if (ev0_ >= 0) cudaEventRecord(p.pool[ev0_], s_);
   }
 }
 
@@ -39,7 +40,7 @@ ProfScope::~ProfScope() {
   if (!p.on || ev0_ < 0) return;
   const int ev1 = take_event(p);
   if (ev1 < 0) return;
-  cudaEventRecord(p.pool[ev1], c_->stream);
+  cudaEventRecord(p.pool[ev1], s_);
   p.recs.push_back({kind_, ev0_, ev1, flops_, bytes_});
 }
 
@@ -50,6 +51,7 @@ void prof_collect(exa_ctx* c) {
     return;
   }
   cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
   for (const ProfRec& r : p.recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.pool[r.ev0], p.pool[r.ev1]) == cudaSuccess) {

@@ -50,11 +50,13 @@ struct Prof {
 // Scope around the launch(es) of one kernel class on the context's stream.
 class ProfScope {
  public:
-  ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels = 1);
+  ProfScope(exa_ctx* c, int kind, double flops, double bytes, int nkernels = 1, cudaStream_t stream = nullptr,
+            bool on_stream = false);
   ~ProfScope();
 
  private:
   exa_ctx* c_;
+  cudaStream_t s_;
   int kind_;
   int ev0_ = -1;
   double flops_, bytes_;
