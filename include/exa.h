@@ -108,6 +108,11 @@ exa_status exa_ctx_set_stream(exa_ctx* ctx, void* cuda_stream);
  * definiteness the evaluation is repeated with every tile exact.           */
 exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
 
+/* Mixed precision: SMs left to the look-ahead stream (which factors the next
+ * diagonal block and runs the next panel solve) while the trailing update
+ * runs on the others.  0 restores the default (16).                        */
+exa_status exa_ctx_set_lookahead(exa_ctx* ctx, int sms);
+
 /* Message describing the last error on this context ("" if none).  The
  * string is owned by the context and valid until its next call.           */
 const char* exa_last_error(const exa_ctx* ctx);

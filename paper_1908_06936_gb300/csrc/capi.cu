@@ -216,6 +216,12 @@ exa_status exa_ctx_set_mixed_band(exa_ctx* c, int band) {
   return EXA_OK;
 }
 
+exa_status exa_ctx_set_lookahead(exa_ctx* c, int sms) {
+  if (!c || sms < 0 || sms > 128) return EXA_ERR_ARG;
+  c->lookahead_sms = sms;
+  return EXA_OK;
+}
+
 const char* exa_last_error(const exa_ctx* c) { return c ? c->err : "null context"; }
 
 int64_t exa_last_pivot(const exa_ctx* c) { return c ? c->last_pivot : -1; }

@@ -30,6 +30,7 @@ struct exa_ctx {
   size_t ws_limit = 0;   // 0: unbounded
   size_t held_bytes = 0;
   int tile_nb = 128;     // FP64 tile
+  int lookahead_sms = 0;  // SMs reserved for the look-ahead stream (0: default)
   int mixed_band = 0;    // exact-product band (256-wide tiles); 0: from Sigma; < 0: all tiles
   int64_t last_pivot = -1;
   char err[512];

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
 
 // ===========================================================================
 // Split kernel: FP64 rows -> T3 (tf32 hi/lo, row-major) and OZ digits.
-// One CTA per 32 rows; K <= 256.  src element (r, k) at src[r*rs + k*cs].
+// One CTA per kSplitRows rows; K <= kSplitMaxK.  src element (r, k) at src[r*rs + k*cs].
 // ===========================================================================
 __device__ __forceinline__ float tf32_rn(float f) {
   uint32_t b = __float_as_uint(f);
@@ -478,25 +478,25 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
                                                          int rows, int K, float* __restrict__ hi,
                                                          float* __restrict__ lo, __nv_bfloat16_raw* __restrict__ dig,
                                                          int64_t dig_stride, int* __restrict__ ex, int out_row0) {
-  extern __shared__ double tile[];  // 32 x (K + 1)
-  const int r0 = blockIdx.x * 32;
+  extern __shared__ double tile[];  // kSplitRows x (K + 1)
+  const int r0 = blockIdx.x * kSplitRows;
   const int tid = threadIdx.x;
   const int ld = K + 1;
   // coalesced along whichever source dimension is contiguous
   if (cs == 1) {
-    for (int idx = tid; idx < 32 * K; idx += blockDim.x) {
+    for (int idx = tid; idx < kSplitRows * K; idx += blockDim.x) {
       const int rr = idx / K, k = idx % K;
       tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + k] : 0.0;
     }
   } else {
-    for (int idx = tid; idx < 32 * K; idx += blockDim.x) {
-      const int rr = idx & 31, k = idx >> 5;
+    for (int idx = tid; idx < kSplitRows * K; idx += blockDim.x) {
+      const int rr = idx % kSplitRows, k = idx / kSplitRows;
       tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + (int64_t)k * cs] : 0.0;
     }
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  for (int rr = warp; rr < 32; rr += blockDim.x / 32) {
+  for (int rr = warp; rr < kSplitRows; rr += blockDim.x / 32) {
     const int row = r0 + rr;
     if (row >= rows) break;
     const int64_t orow = (int64_t)(out_row0 + row);
@@ -595,15 +595,15 @@ cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int
                               SplitOperand& op, int out_row0) {
   if (rows <= 0) return cudaSuccess;
   if (K > kSplitMaxK) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)32 * (K + 1) * sizeof(double);
+  const size_t smem = (size_t)kSplitRows * (K + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(split_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         32 * (kSplitMaxK + 1) * (int)sizeof(double));
+                                         kSplitRows * (kSplitMaxK + 1) * (int)sizeof(double));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  split_rows_kernel<<<(rows + 31) / 32, 256, smem, s>>>(src, rs, cs, rows, K, op.hi, op.lo,
+  split_rows_kernel<<<(rows + kSplitRows - 1) / kSplitRows, 256, smem, s>>>(src, rs, cs, rows, K, op.hi, op.lo,
                                                         (__nv_bfloat16_raw*)op.dig, (int64_t)op.rows * op.K, op.ex,
                                                         out_row0);
   return cudaGetLastError();

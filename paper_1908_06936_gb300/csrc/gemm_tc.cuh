@@ -11,6 +11,7 @@ namespace exa {
 
 constexpr int kOzSlices = 5;  // 7-bit digits per value in the exact (band) products
 constexpr int kSplitMaxK = 512;  // longest row the split kernel converts
+constexpr int kSplitRows = 16;   // rows per CTA of the split kernel
 
 // Tile enumeration of one launch.
 enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2 };

@@ -13,7 +13,7 @@ namespace exa {
 constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
-constexpr int kLookaheadSMs = 12;         // SMs left to the look-ahead stream during a trailing update
+constexpr int kLookaheadSMs = 16;         // SMs left to the look-ahead stream during a trailing update
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 
@@ -271,7 +271,7 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   MixStep M{c, a, ld, npad, band, T};
   cudaStream_t ms = c->stream, ss = c->side;
   const int sms = tc_num_sms();
-  const int side_ctas = kLookaheadSMs;
+  const int side_ctas = c->lookahead_sms > 0 ? c->lookahead_sms : kLookaheadSMs;
   const int main_ctas = sms - side_ctas;
   SplitOperand* buf[2] = {&c->sp_a, &c->sp_a2};
   // panel 0 on the main stream
