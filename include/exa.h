@@ -64,7 +64,8 @@ typedef enum {
 typedef enum {
   EXA_FP64 = 0,          /* all tiles FP64 (the exact variant, Fig. 1(a)) */
   EXA_MIXED_TF32X3 = 1,  /* off-diagonal TRSM/GEMM/SYRK products as 3 TF32 tensor-core products, FP32 accumulate */
-  EXA_MIXED_BF16X3 = 2   /* off-diagonal TRSM/GEMM/SYRK products as 3 BF16 tensor-core products, FP32 accumulate */
+  EXA_MIXED_BF16X3 = 2,  /* off-diagonal TRSM/GEMM/SYRK products as 3 BF16 tensor-core products, FP32 accumulate */
+  EXA_MIXED_FP32 = 3     /* batched form only: off-diagonal tile products in FP32 (FFMA), FP32 accumulate per tile */
 } exa_prec;
 
 typedef struct exa_ctx exa_ctx;
@@ -154,13 +155,23 @@ exa_status exa_loglik_grad(exa_ctx* ctx, const double* d_locs, const double* d_z
                            exa_prec prec, double* loglik, double grad[3]);
 
 /* Batched evaluation of nrep independent replicate fields of uneven sizes
- * (FP64; one persistent launch walks the tile tasks of every replicate).
+ * (one persistent launch walks the tile tasks of every replicate; the
+ * replicate studies of Section III, Example 2).
+ *   prec      EXA_FP64: every tile task in FP64.  EXA_MIXED_FP32 (the MP
+ *             variant of Section II-A): diagonal tiles factored in FP64, the
+ *             off-diagonal TRSM and update tiles computed from FP32-rounded
+ *             operands with FP32 accumulation over the tile and added to the
+ *             FP64 tile (tiles within the band set by exa_ctx_set_batched_mixed
+ *             stay FP64), then x = Sigma^-1 z refined in FP64 against an FP64
+ *             copy of Sigma, q = z^T x; a replicate whose refinement stalls
+ *             above a 1e-8 relative residual reports EXA_ERR_IR_NOCONV.
+ *             Other precisions return EXA_ERR_ARG.
  *   h_n       host array of nrep sizes (each >= 1).
  *   d_locs    host array of nrep DEVICE pointers, replicate r has h_n[r] x 2 locations.
  *   d_z       host array of nrep DEVICE pointers, h_n[r] observations each.
  *   d_theta   DEVICE array nrep x 3 (sigma^2, beta, nu per replicate), read at execution time,
  *             so a captured graph can be replayed with new parameters.
- *   d_loglik  DEVICE output, nrep values (NaN where the replicate is not SPD).
+ *   d_loglik  DEVICE output, nrep values (NaN where the replicate's status is not EXA_OK).
  *   d_status  DEVICE output, nrep exa_status codes.
  * Stream-asynchronous: returns once the work is enqueued; device memory is
  * allocated on the first call for a shape set, so make that call before any
@@ -209,6 +220,12 @@ int exa_profile_read(exa_ctx* ctx, exa_kernel_stat* out, int max, int reset);
  *                never met, so its wait runs out and the affected replicates report
  *                EXA_ERR_TIMEOUT (the path a real stall would take).                 */
 exa_status exa_ctx_set_batched(exa_ctx* ctx, int tile_nb, int ctas_per_sm, long long spin_cycles, int inject_stall);
+
+/* Options of the mixed-precision batched form:
+ *   band      TRSM / update tiles fewer than `band` tile diagonals away from the
+ *             diagonal stay FP64 (0: every off-diagonal product on tensor cores);
+ *   max_iter  refinement steps per replicate at most (0: 10).                    */
+exa_status exa_ctx_set_batched_mixed(exa_ctx* ctx, int band, int max_iter);
 
 /* Exact synthetic realisation (Section III, Example 1, simulate_obs_exact):
  * d_z = L d_eps with L L^T = Sigma(theta), both n FP64 device vectors.       */

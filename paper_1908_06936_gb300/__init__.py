@@ -16,17 +16,17 @@ import numpy as np
 
 __all__ = [
     "EXA_OK", "EXA_ERR_ARG", "EXA_ERR_NOT_SPD", "EXA_ERR_NOMEM", "EXA_ERR_CUDA", "EXA_ERR_TIMEOUT",
-    "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "ExaError", "Context", "lib",
+    "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "EXA_MIXED_FP32", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
-EXA_FP64, EXA_MIXED_TF32X3, EXA_MIXED_BF16X3 = 0, 1, 2
+EXA_FP64, EXA_MIXED_TF32X3, EXA_MIXED_BF16X3, EXA_MIXED_FP32 = 0, 1, 2, 3
 EXA_GEMM_T3, EXA_GEMM_OZ = 0, 1
-PREC = {"fp64": EXA_FP64, "tf32x3": EXA_MIXED_TF32X3, "bf16x3": EXA_MIXED_BF16X3}
+PREC = {"fp64": EXA_FP64, "tf32x3": EXA_MIXED_TF32X3, "bf16x3": EXA_MIXED_BF16X3, "fp32": EXA_MIXED_FP32}
 _STATUS = {0: "EXA_OK", 1: "EXA_ERR_ARG", 2: "EXA_ERR_NOT_SPD", 3: "EXA_ERR_NOMEM", 4: "EXA_ERR_CUDA",
            5: "EXA_ERR_TIMEOUT", 6: "EXA_ERR_IR_NOCONV"}
 
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
                 "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_loglik_noalloc": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
+                "exa_ctx_set_batched_mixed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
                 "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
@@ -287,6 +288,10 @@ def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
 def exa_ctx_set_batched(ctx: int, tile_nb: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,
                         inject_stall: int = 0) -> int:
     return lib().exa_ctx_set_batched(_P(ctx), int(tile_nb), int(ctas_per_sm), int(spin_cycles), int(inject_stall))
+
+
+def exa_ctx_set_batched_mixed(ctx: int, band: int = 0, max_iter: int = 0) -> int:
+    return lib().exa_ctx_set_batched_mixed(_P(ctx), int(band), int(max_iter))
 
 
 def exa_loglik_noalloc(cuda_stream: int, locs, z, theta, n: int, loglik: ctypes.c_double) -> int:

@@ -2,9 +2,11 @@
 // replicate studies of Section III, Example 2, run as one device workload).
 //
 // Stream-ordered, graph-capturable sequence (no host synchronisation):
-//   1. per-replicate Matérn constants from theta in device memory (so a captured
-//      graph can be replayed with new parameters);
-//   2. generation of every replicate's lower tiles in one launch;
+//   1. per-replicate Matérn constants and interpolation table of Eq. 3 from
+//      theta in device memory (so a captured graph can be replayed with new
+//      parameters);
+//   2. generation of every replicate's lower tiles in one launch (mixed
+//      precision also keeps an FP64 copy of Sigma for the refinement residual);
 //   3. ONE persistent launch that walks a work list of tile tasks
 //        POTRF(r, k)    L_kk = chol(A_kk), W_k = L_kk^-1, log-det part
 //        TRSM(r, i, k)  L_ik = A_ik W_k^T
@@ -12,15 +14,23 @@
 //      ordered by step k across replicates (a topological order of every
 //      replicate's DAG).  CTAs claim tasks in list order; a task waits on
 //      per-tile completion counters (bounded spin: on time-out the replicate
-//      reports EXA_ERR_TIMEOUT and every CTA stops claiming work), runs on
-//      FP64 DMMA, then bumps its tile's counter.  Since every dependency sits
-//      earlier in the list and all CTAs are co-resident, the walk cannot
-//      deadlock;
-//   4. one CTA per replicate: blocked forward solve, log-det, quadratic form,
-//      l = -n/2 log 2 pi - 1/2 log|Sigma| - 1/2 y^T y and the status.
+//      reports EXA_ERR_TIMEOUT and every CTA stops claiming work), runs, then
+//      bumps its tile's counter.  Since every dependency sits earlier in the
+//      list and all CTAs are co-resident, the walk cannot deadlock.
+//      FP64: every task on FP64 DMMA.  Mixed (the MP variant of Section II-A):
+//      POTRF stays FP64; TRSM and UPDATE tiles farther than `band` tile
+//      diagonals from the diagonal run as three TF32 tensor-core products
+//      (hi*hi + hi*lo + lo*hi, FP32 accumulation over the tile's K) added to
+//      the FP64 tile;
+//   4. FP64: one CTA per replicate: blocked forward solve, log-det, quadratic
+//      form, l = -n/2 log 2 pi - 1/2 log|Sigma| - 1/2 y^T y and the status.
+//      Mixed: one CTA per replicate refines x = Sigma^-1 z in FP64
+//      (x += L^-T L^-1 (z - Sigma x) with the FP64 copy of Sigma) and uses
+//      q = z^T x.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "bessel.cuh"
@@ -69,10 +79,27 @@ __global__ void batched_params_kernel(int nrep, const double* __restrict__ theta
   matern_params_hd(th, &P[r]);
 }
 
+// Per-replicate interpolation tables (blockIdx.y = replicate).
+__global__ void batched_table_nodes_kernel(const MaternParams* __restrict__ P, double* __restrict__ nodes) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int NN = kTabSeg * (kTabDeg + 1);
+  if (id >= NN) return;
+  nodes[(int64_t)blockIdx.y * NN + id] = table_node_value(P[blockIdx.y], id);
+}
+
+__global__ void batched_table_coef_kernel(const double* __restrict__ nodes, MaternTable* __restrict__ T) {
+  const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sgi >= kTabSeg) return;
+  table_segment_coefs(nodes + (int64_t)blockIdx.y * kTabSeg * (kTabDeg + 1), sgi, &T[blockIdx.y]);
+}
+
 // Generation: block b -> replicate (binary search over first-block offsets) and lower tile.
+// mat2 (mixed precision) receives a second copy of every entry.
 template <int NB>
 __global__ void __launch_bounds__(256) batched_gen_kernel(int nrep, const BMeta* __restrict__ M,
-                                                          const MaternParams* __restrict__ P, double* __restrict__ mat) {
+                                                          const MaternParams* __restrict__ P,
+                                                          const MaternTable* __restrict__ tabs,
+                                                          double* __restrict__ mat, double* __restrict__ mat2) {
   int lo = 0, hi = nrep - 1;
   const int64_t b = blockIdx.x;
   while (lo < hi) {
@@ -82,6 +109,7 @@ __global__ void __launch_bounds__(256) batched_gen_kernel(int nrep, const BMeta*
   const int r = lo;
   const BMeta m = M[r];
   const MaternParams& Pr = P[r];
+  const MaternTable* tab = tabs + r;
   int64_t t = b - m.gt;
   int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while ((int64_t)ti * (ti + 1) / 2 > t) --ti;
@@ -105,9 +133,10 @@ __global__ void __launch_bounds__(256) batched_gen_kernel(int nrep, const BMeta*
       v = Pr.sigma2;
     } else {
       const double dx = xi - m.locs[2 * j], dy = yi - m.locs[2 * j + 1];
-      v = matern_value(Pr, sqrt(dx * dx + dy * dy));
+      v = matern_value_tab(Pr, tab, sqrt(dx * dx + dy * dy));
     }
     a[i + j * m.npad] = v;
+    if (mat2) mat2[m.mo + i + j * m.npad] = v;
   }
 }
 
@@ -135,29 +164,54 @@ __device__ __forceinline__ bool wait_count(const int* p, int want, volatile int*
   }
 }
 
+constexpr int kBThreads = 128;  // threads of the persistent factorisation CTA
+
+// Modes of the persistent factorisation: every task in FP64; FP32 off-diagonal tiles
+// with a band of FP64 tiles next to the diagonal; FP32 off-diagonal tiles everywhere.
+enum : int { MODE_FP64 = 0, MODE_F32_BAND = 1, MODE_F32 = 2 };
+
 template <int NB>
 struct Tile {
-  static constexpr int SS = NB + 4;  // padded smem row stride for the GEMM operands
+  static constexpr int SS = NB + 4;   // padded smem row stride of the FP64 operands
+  static constexpr int SA = NB + 4;   // padded smem stride of the FP32 operands (k-major)
+  static constexpr int PER = NB * NB / kBThreads;       // tile elements per thread
+  static constexpr int CH = PER < 16 ? PER : 16;        // loads in flight per operand
+  static constexpr size_t smem(int mode) {
+    const size_t f64 = (size_t)2 * NB * SS * sizeof(double);
+    const size_t f32 = (size_t)2 * NB * SA * sizeof(float);
+    const size_t po = (size_t)(NB * (NB + 1) + NB) * sizeof(double);
+    const size_t m = f32 > po ? f32 : po;
+    return mode == MODE_F32 ? m : (f64 > m ? f64 : m);
+  }
 };
 
-// C (NB x NB) [-]= A B^T with A(r, t) from tile a (column-major, ld), B(c, t) from
-// either a tile (column-major) or a row-major NB x NB matrix; result kept in acc.
-// 4 warps in 2 x 2, each (NB/2) x (NB/2) = MI x MI m8n8 blocks.
 template <int NB>
 __device__ __forceinline__ void tile_gemm(const double* a, int64_t lda, const double* b, int64_t ldb, bool b_rowmajor,
                                           double* As, double* Bs, double (&acc)[NB / 16][NB / 16][2]) {
   constexpr int MI = NB / 16, SS = Tile<NB>::SS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, q = lane & 3, wm = warp >> 1, wn = warp & 1;
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int r = idx % NB, t = idx / NB;  // rows fastest: column-major tiles coalesce
-    // L2-only loads: tiles are written by other SMs during this launch and L1 is not coherent
-    As[r * SS + t] = __ldcg(a + r + (int64_t)t * lda);
-    if (b_rowmajor) {
-      const int c2 = idx / NB, t2 = idx % NB;
-      Bs[c2 * SS + t2] = __ldcg(b + (int64_t)c2 * ldb + t2);
-    } else {
-      Bs[r * SS + t] = __ldcg(b + r + (int64_t)t * ldb);
+  // rows fastest: column-major tiles coalesce.  L2-only loads (tiles are written by
+  // other SMs during this launch and L1 is not coherent), CH of each operand in flight.
+  constexpr int PER = Tile<NB>::PER, CH = Tile<NB>::CH;
+#pragma unroll
+  for (int c0 = 0; c0 < PER; c0 += CH) {
+    double va[CH], vb[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = tid + (c0 + u) * kBThreads;
+      const int r = idx % NB, t = idx / NB;
+      va[u] = __ldcg(a + r + (int64_t)t * lda);
+      // row-major B: element (row t, col r) at b[t ldb + r], also read along r
+      vb[u] = b_rowmajor ? __ldcg(b + (int64_t)t * ldb + r) : __ldcg(b + r + (int64_t)t * ldb);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = tid + (c0 + u) * kBThreads;
+      const int r = idx % NB, t = idx / NB;
+      As[r * SS + t] = va[u];
+      if (b_rowmajor) Bs[t * SS + r] = vb[u];
+      else Bs[r * SS + t] = vb[u];
     }
   }
   __syncthreads();
@@ -180,13 +234,88 @@ __device__ __forceinline__ void tile_gemm(const double* a, int64_t lda, const do
   __syncthreads();
 }
 
+// ---- FP32 tile product (mixed precision) ----
+// out (NB x NB, column-major, ld) = / -= A B^T with A(r, t) = a[r + t ld] and B(c, t) from
+// either a column-major tile (b[c + t ld]) or a row-major NB x NB matrix (b[c NB + t]).
+// Operands rounded to FP32, products accumulated in FP32 over the tile's K = NB (FFMA),
+// the result added to the FP64 tile.  Thread (tr, tc) owns rows tr + (NB/4) i, i < 4, and
+// the CT consecutive columns tc CT .. tc CT + CT - 1.
 template <int NB>
-__global__ void __launch_bounds__(128) batched_chol_kernel(const BTask* __restrict__ tasks, int ntasks,
+__device__ __forceinline__ void tile_f32(const double* a, const double* b, bool b_rowmajor, double* out, int64_t ld,
+                                         bool store, bool lower_only, float* sm) {
+  constexpr int SA = Tile<NB>::SA, RG = NB / 4, CT = NB * NB / (kBThreads * 4);
+  constexpr int PER = Tile<NB>::PER, CH = Tile<NB>::CH;
+  float* As = sm;            // k-major: element (row, k) at As[k SA + row]
+  float* Bs = sm + NB * SA;  // element (col, k) at Bs[k SA + col]
+  const int tid = threadIdx.x, tr = tid % RG, tc = tid / RG;
+#pragma unroll
+  for (int c0 = 0; c0 < PER; c0 += CH) {
+    double va[CH], vb[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = tid + (c0 + u) * kBThreads;
+      const int r = idx % NB, t = idx / NB;
+      va[u] = __ldcg(a + r + (int64_t)t * ld);
+      // row-major B (NB x NB): element (row t, col r) at b[t NB + r]
+      vb[u] = b_rowmajor ? __ldcg(b + (int64_t)t * NB + r) : __ldcg(b + r + (int64_t)t * ld);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = tid + (c0 + u) * kBThreads;
+      const int r = idx % NB, t = idx / NB;
+      As[t * SA + r] = (float)va[u];
+      if (b_rowmajor) Bs[r * SA + t] = (float)vb[u];  // B operand column t, k = r
+      else Bs[t * SA + r] = (float)vb[u];
+    }
+  }
+  __syncthreads();
+  float acc[4][CT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CT; ++j) acc[i][j] = 0.0f;
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    float av[4], bv[CT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = As[k * SA + tr + RG * i];
+    if constexpr (CT % 4 == 0) {
+#pragma unroll
+      for (int j = 0; j < CT; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(Bs + k * SA + tc * CT + j);
+        bv[j] = v.x;
+        bv[j + 1] = v.y;
+        bv[j + 2] = v.z;
+        bv[j + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < CT; ++j) bv[j] = Bs[k * SA + tc * CT + j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CT; ++j) {
+      const int rr = tr + RG * i, cc = tc * CT + j;
+      if (lower_only && cc > rr) continue;
+      double* p = out + rr + (int64_t)cc * ld;
+      *p = store ? (double)acc[i][j] : __ldcg(p) - (double)acc[i][j];
+    }
+}
+
+template <int NB, int MODE>
+__global__ void __launch_bounds__(kBThreads) batched_chol_kernel(const BTask* __restrict__ tasks, int ntasks,
                                                            const BMeta* __restrict__ M, double* __restrict__ mat,
                                                            double* __restrict__ wbuf, double* __restrict__ ldpart,
                                                            int* __restrict__ cnt, BCtl* ctl,
                                                            int32_t* __restrict__ rstatus, DevStatus* st,
-                                                           long long spin_limit) {
+                                                           long long spin_limit, int band) {
   constexpr int MI = NB / 16, SS = Tile<NB>::SS;
   extern __shared__ double sm[];
   double* As = sm;
@@ -238,9 +367,19 @@ __global__ void __launch_bounds__(128) batched_chol_kernel(const BTask* __restri
       double* tmp = As + NB * (NB + 1);
       const int sd = NB + 1;
       double* T = a + (int64_t)tk.k * NB + (int64_t)tk.k * NB * ld;
-      for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-        const int i = idx % NB, j = idx / NB;
-        S[i * sd + j] = (i >= j) ? __ldcg(T + i + (int64_t)j * ld) : 0.0;
+#pragma unroll
+      for (int c0 = 0; c0 < Tile<NB>::PER; c0 += Tile<NB>::CH) {
+        double v[Tile<NB>::CH];
+#pragma unroll
+        for (int u = 0; u < Tile<NB>::CH; ++u) {
+          const int idx = tid + (c0 + u) * kBThreads, i = idx % NB, j = idx / NB;
+          v[u] = (i >= j) ? __ldcg(T + i + (int64_t)j * ld) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < Tile<NB>::CH; ++u) {
+          const int idx = tid + (c0 + u) * kBThreads;
+          S[(idx % NB) * sd + idx / NB] = v[u];
+        }
       }
       __syncthreads();
       int bad = -1;
@@ -295,7 +434,19 @@ __global__ void __launch_bounds__(128) batched_chol_kernel(const BTask* __restri
         const int rr = idx / NB, cc = idx % NB;
         W[idx] = (cc <= rr) ? S[rr * sd + cc] : 0.0;
       }
-    } else if (tk.op == OP_TRSM || tk.op == OP_UPDATE) {
+    } else if (MODE != MODE_FP64 && (tk.op == OP_TRSM || tk.op == OP_UPDATE) &&
+               (MODE == MODE_F32 || (tk.op == OP_TRSM ? tk.i - tk.k : tk.i - tk.j) >= band)) {
+      if (tk.op == OP_TRSM) {
+        const double* W = wbuf + m.wo + (int64_t)tk.k * NB * NB;
+        double* out = a + (int64_t)tk.i * NB + (int64_t)tk.k * NB * ld;
+        tile_f32<NB>(out, W, true, out, ld, true, false, (float*)sm);
+      } else {
+        const double* ai = a + (int64_t)tk.i * NB + (int64_t)tk.k * NB * ld;
+        const double* aj = a + (int64_t)tk.j * NB + (int64_t)tk.k * NB * ld;
+        double* out = a + (int64_t)tk.i * NB + (int64_t)tk.j * NB * ld;
+        tile_f32<NB>(ai, aj, false, out, ld, false, tk.i == tk.j, (float*)sm);
+      }
+    } else if (MODE != MODE_F32 && (tk.op == OP_TRSM || tk.op == OP_UPDATE)) {
       double acc[MI][MI][2];
       double* out;
       if (tk.op == OP_TRSM) {
@@ -400,23 +551,322 @@ __global__ void __launch_bounds__(256) batched_solve_kernel(int nrep, const BMet
 }
 
 // ---------------------------------------------------------------------------
+// Mixed precision: per-replicate FP64 refinement of x = Sigma^-1 z (one CTA of
+// kIrThreads per replicate, largest replicates first).
+// ---------------------------------------------------------------------------
+constexpr int kIrThreads = 1024;
+constexpr double kIrFail = 1e-8;  // relative residual above which a replicate reports EXA_ERR_IR_NOCONV
+
+// Block-wide sum, the same order on every call (warp shuffles, then warp 0).
+__device__ __forceinline__ double ir_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// y = L^-1 b, blocked by NB with the stored inverses W_k of the diagonal tiles:
+// y_k = W_k (b_k - sum_{j < k} L_kj y_j).  Columns of the sum are split over
+// kIrThreads / NB slices (fixed order), eight loads in flight per thread.
+template <int NB>
+__device__ void ir_forward(const double* __restrict__ L, const double* __restrict__ W, int64_t ld, int T,
+                           const double* b, double* y, double (*part)[NB], double* sv) {
+  constexpr int NS = kIrThreads / NB;
+  const int tid = threadIdx.x, row = tid % NB, slice = tid / NB;
+  for (int k = 0; k < T; ++k) {
+    const int64_t kc = (int64_t)k * NB;
+    const double* Lr = L + kc + row;
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t jc = slice;
+    for (; jc + 7 * NS < kc; jc += 8 * NS) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] = fma(__ldcs(Lr + (jc + u * NS) * ld), y[jc + u * NS], s[u]);
+    }
+    for (; jc < kc; jc += NS) s[0] = fma(__ldcs(Lr + jc * ld), y[jc], s[0]);
+    part[slice][row] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    __syncthreads();
+    if (tid < NB) {
+      double v = b[kc + tid];
+      for (int q = 0; q < NS; ++q) v -= part[q][tid];
+      sv[tid] = v;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const double* Wk = W + kc * NB;
+      double yk = 0.0;
+      for (int t = 0; t <= tid; ++t) yk = fma(Wk[tid * NB + t], sv[t], yk);
+      y[kc + tid] = yk;
+    }
+    __syncthreads();
+  }
+}
+
+// y := L^-T y in place: d_k = W_k^T (y_k - sum_{i > k} L_ik^T d_i).  Column c of
+// the sum is contiguous below the tile: one warp per column, lanes over rows.
+template <int NB>
+__device__ void ir_backward(const double* __restrict__ L, const double* __restrict__ W, int64_t ld, int T,
+                            int64_t npad, double* y, double* sv) {
+  constexpr int NW = kIrThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = T - 1; k >= 0; --k) {
+    const int64_t kc = (int64_t)k * NB, r0 = kc + NB;
+    for (int c = warp; c < NB; c += NW) {
+      const double* col = L + (kc + c) * ld;
+      double s[4] = {0, 0, 0, 0};
+      int64_t i = r0 + lane;
+      for (; i + 96 < npad; i += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fma(__ldcs(col + i + 32 * u), y[i + 32 * u], s[u]);
+      }
+      for (; i < npad; i += 32) s[0] = fma(__ldcs(col + i), y[i], s[0]);
+      double v = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sv[c] = y[kc + c] - v;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const double* Wk = W + kc * NB;
+      double d = 0.0;
+      for (int u = tid; u < NB; ++u) d = fma(Wk[u * NB + tid], sv[u], d);
+      y[kc + tid] = d;
+    }
+    __syncthreads();
+  }
+}
+
+// r = z - Sigma x from the lower triangle of Sigma (FP64 copy), returns ||r||^2.
+// Row part sum_{j <= i} S_ij x_j: thread per row (coalesced along the column);
+// column part sum_{j > i} S_ji x_j: warp per column.  Fixed order.
+__device__ double ir_residual(const double* __restrict__ S, int64_t ld, int64_t n, int64_t npad,
+                              const double* __restrict__ z, const double* x, double* rv, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kIrThreads / 32;
+  // column part first, into rv
+  for (int64_t c = warp; c < npad; c += NW) {
+    const double* col = S + c * ld;
+    double s[4] = {0, 0, 0, 0};
+    int64_t i = c + 1 + lane;
+    for (; i + 96 < npad; i += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] = fma(__ldcs(col + i + 32 * u), x[i + 32 * u], s[u]);
+    }
+    for (; i < npad; i += 32) s[0] = fma(__ldcs(col + i), x[i], s[0]);
+    double v = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) rv[c] = v;
+  }
+  __syncthreads();
+  double rr = 0.0;
+  for (int64_t i0 = 0; i0 < npad; i0 += kIrThreads) {
+    const int64_t i = i0 + tid;
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < npad) {
+      const double* rowp = S + i;
+      int64_t j = 0;
+      for (; j + 7 <= i; j += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] = fma(__ldcs(rowp + (j + u) * ld), x[j + u], s[u]);
+      }
+      for (; j <= i; ++j) s[0] = fma(__ldcs(rowp + j * ld), x[j], s[0]);
+      const double sx = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + rv[i];
+      const double ri = (i < n) ? z[i] - sx : 0.0;
+      rv[i] = ri;
+      rr = fma(ri, ri, rr);
+    }
+  }
+  return ir_block_sum(rr, red);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kIrThreads) batched_ir_kernel(
+    const int* __restrict__ order, const BMeta* __restrict__ M, const double* __restrict__ mat,
+    const double* __restrict__ sig, const double* __restrict__ wbuf, const double* __restrict__ ldpart,
+    const int* __restrict__ cnt, double* __restrict__ vec, int64_t vtot, double* __restrict__ loglik,
+    int32_t* __restrict__ rstatus, int max_iter) {
+  __shared__ double part[kIrThreads / NB][NB];
+  __shared__ double sv[NB];
+  __shared__ double red[33];
+  const int r = order[blockIdx.x];
+  const BMeta m = M[r];
+  const int tid = threadIdx.x;
+  const int T = (int)m.T;
+  const bool done = cnt[m.co + tri_index(T - 1, T - 1)] == T;
+  __syncthreads();
+  if (tid == 0 && !done && rstatus[r] == EXA_OK) rstatus[r] = EXA_ERR_TIMEOUT;
+  __syncthreads();
+  if (rstatus[r] != EXA_OK) {
+    if (tid == 0) loglik[r] = NAN;
+    return;
+  }
+  const double* L = mat + m.mo;
+  const double* S = sig + m.mo;
+  const double* W = wbuf + m.wo;
+  const int64_t ld = m.npad, npad = m.npad, n = m.n;
+  double* x = vec + m.vo;
+  double* rv = vec + vtot + m.vo;
+  double* y = vec + 2 * vtot + m.vo;
+  double zz = 0.0;
+  for (int64_t i = tid; i < npad; i += kIrThreads) {
+    const double zi = (i < n) ? m.z[i] : 0.0;
+    x[i] = 0.0;
+    rv[i] = zi;
+    zz = fma(zi, zi, zz);
+  }
+  const double zn2 = ir_block_sum(zz, red);
+  double prev = 1e300, rel = 1e300;
+  for (int it = 0; it < max_iter; ++it) {
+    ir_forward<NB>(L, W, ld, T, rv, y, part, sv);
+    ir_backward<NB>(L, W, ld, T, npad, y, sv);
+    for (int64_t i = tid; i < npad; i += kIrThreads) x[i] += y[i];
+    __syncthreads();
+    const double rn2 = ir_residual(S, ld, n, npad, m.z, x, rv, red);
+    rel = zn2 > 0.0 ? sqrt(rn2 / zn2) : 0.0;
+    if (!(rel > 1e-15) || rel > 0.5 * prev) break;  // converged, or no longer contracting
+    prev = rel;
+  }
+  double zx = 0.0;
+  for (int64_t i = tid; i < n; i += kIrThreads) zx = fma(m.z[i], x[i], zx);
+  const double q = ir_block_sum(zx, red);
+  if (tid == 0) {
+    double ldet = 0.0;
+    for (int k = 0; k < T; ++k) ldet += ldpart[m.lo + k];
+    ldet *= 2.0;
+    if (rel <= kIrFail) {
+      loglik[r] = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * ldet - 0.5 * q;
+    } else {
+      loglik[r] = NAN;
+      rstatus[r] = EXA_ERR_IR_NOCONV;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 struct BatchPlan {
   std::vector<int64_t> ns;
   int nb = 0;
   int stall = 0;
-  int64_t mat_doubles = 0, w_doubles = 0, cnt_ints = 0, ld_doubles = 0, vec_doubles = 0, gen_blocks = 0;
+  bool mixed = false;
   int ntasks = 0;
-  size_t meta_off = 0, params_off = 0, tasks_off = 0, ctl_off = 0, cnt_off = 0, meta_bytes = 0;
 };
 
-template <int NB>
+// Work-list order.  Every task gets its bottom level: the longest path, in
+// estimated task durations, from the task to the end of its replicate's
+// factorisation.  The list is sorted by decreasing bottom level (counting sort,
+// stable).  A predecessor's bottom level exceeds each successor's by at least
+// its own duration, so the order is topological (no CTA can wait on a task
+// claimed after its own); and the long chains through the diagonal tiles come
+// first, so CTAs rarely sit on a claimed task whose inputs are still being
+// computed.  Relative durations: POTRF (FP64, unblocked, one CTA) dP, TRSM and
+// UPDATE one unit each (in mixed precision those run on tensor cores).
+static void build_task_list(const std::vector<BMeta>& meta, bool mixed, bool stall, std::vector<BTask>& tasks) {
+  const int dP = mixed ? 16 : 2, dS = 1, dU = 1;
+  std::vector<int> keys;
+  std::vector<BTask> raw;
+  int kmax = 0;
+  const int nrep = (int)meta.size();
+  for (int r = 0; r < nrep; ++r) {
+    const int T = (int)meta[r].T;
+    // bottom levels: U of step k+1 (cur, then swapped), S(i, k) over all (i, k), P(k)
+    std::vector<int> bS((size_t)T * T, 0), bP(T, 0), un((size_t)T * T, 0), uc((size_t)T * T, 0);
+    for (int k = T - 1; k >= 0; --k) {
+      // UPDATE(i, j, k), k < j <= i: its successor is the next operation on tile (i, j)
+      for (int i = k + 1; i < T; ++i)
+        for (int j = k + 1; j <= i; ++j) {
+          const int nxt = (j == k + 1) ? (i == j ? bP[j] : bS[(size_t)i * T + j]) : un[(size_t)i * T + j];
+          const int key = dU + nxt;
+          uc[(size_t)i * T + j] = key;
+          raw.push_back({r, (short)OP_UPDATE, (short)k, (short)i, (short)j, 0, 0});
+          keys.push_back(key);
+        }
+      // TRSM(i, k): feeds UPDATE(i, j, k) for k < j <= i and UPDATE(i2, i, k) for i2 > i
+      for (int i = k + 1; i < T; ++i) {
+        int m = 0;
+        for (int j = k + 1; j <= i; ++j) m = std::max(m, uc[(size_t)i * T + j]);
+        for (int i2 = i + 1; i2 < T; ++i2) m = std::max(m, uc[(size_t)i2 * T + i]);
+        bS[(size_t)i * T + k] = dS + m;
+        raw.push_back({r, (short)OP_TRSM, (short)k, (short)i, (short)k, 0, 0});
+        keys.push_back(dS + m);
+      }
+      int m = 0;
+      for (int i = k + 1; i < T; ++i) m = std::max(m, bS[(size_t)i * T + k]);
+      bP[k] = dP + m;
+      raw.push_back({r, (short)OP_POTRF, (short)k, (short)k, (short)k, 0, 0});
+      keys.push_back(dP + m);
+      std::swap(un, uc);
+    }
+  }
+  for (int key : keys) kmax = std::max(kmax, key);
+  std::vector<int64_t> start((size_t)kmax + 2, 0);
+  for (int key : keys) ++start[(size_t)(kmax - key) + 1];
+  for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+  tasks.assign(raw.size(), BTask{});
+  for (size_t t = 0; t < raw.size(); ++t) tasks[(size_t)start[(size_t)(kmax - keys[t])]++] = raw[t];
+  if (stall) {
+    // test hook: a task whose dependency nothing satisfies, early in the list
+    const size_t at = tasks.size() < 8 ? tasks.size() : 8;
+    tasks.insert(tasks.begin() + (int64_t)at, BTask{0, (short)OP_STALL, 0, 0, 0, 0, 0});
+  }
+}
+
+struct CholArgs {
+  const BTask* tasks;
+  int ntasks;
+  const BMeta* M;
+  double* mat;
+  double* wbuf;
+  double* ldpart;
+  int* cnt;
+  BCtl* ctl;
+  int32_t* rstatus;
+  DevStatus* st;
+  long long spin;
+  int band;
+  int ctas_per_sm;
+};
+
+// The persistent factorisation: as many CTAs per SM as fit (or the requested
+// number, capped there: the walk relies on every CTA being resident).
+template <int NB, int MODE>
+static exa_status launch_chol(exa_ctx* c, cudaStream_t s, const CholArgs& a) {
+  const size_t smem = Tile<NB>::smem(MODE);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(batched_chol_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_chol_kernel<NB, MODE>, kBThreads, smem);
+  int want = a.ctas_per_sm > 0 ? a.ctas_per_sm : per_sm;
+  if (want > per_sm) want = per_sm;
+  if (want < 1) return set_err(c, EXA_ERR_CUDA, "batched kernel cannot be resident");
+  batched_chol_kernel<NB, MODE><<<want * sms, kBThreads, smem, s>>>(a.tasks, a.ntasks, a.M, a.mat, a.wbuf, a.ldpart,
+                                                                    a.cnt, a.ctl, a.rstatus, a.st, a.spin, a.band);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EXA_OK : cuda_err(c, e, "batched factorisation launch");
+}
+
+template <int NB, bool MIXED>
 static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const double* const* d_locs,
                               const double* const* d_z, const double* d_theta, double* d_loglik, int32_t* d_status) {
   cudaStream_t s = c->stream;
   BatchPlan& P = *c->bplan;
-  const bool same = P.nb == NB && P.stall == c->batched_stall && (int)P.ns.size() == nrep &&
+  const bool same = P.nb == NB && P.mixed == MIXED && P.stall == c->batched_stall && (int)P.ns.size() == nrep &&
                     std::equal(P.ns.begin(), P.ns.end(), h_n);
   std::vector<BMeta> meta(nrep);
   int64_t mo = 0, wo = 0, co = 0, lo = 0, vo = 0, gt = 0;
@@ -440,52 +890,54 @@ static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const do
     vo += m.npad;
     gt += m.T * (m.T + 1) / 2;
   }
+  // replicates by decreasing size: the refinement CTAs of the largest start first
+  std::vector<int> order(nrep);
+  for (int r = 0; r < nrep; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return h_n[x] > h_n[y]; });
   std::vector<BTask> tasks;
   if (!same) {
     int Tmax = 0;
     for (int r = 0; r < nrep; ++r) Tmax = meta[r].T > Tmax ? (int)meta[r].T : Tmax;
     if (Tmax > 32000) return set_err(c, EXA_ERR_ARG, "replicate too large for the batched form");
-    for (int k = 0; k < Tmax; ++k) {
-      for (int r = 0; r < nrep; ++r) {
-        const int T = (int)meta[r].T;
-        if (k >= T) continue;
-        tasks.push_back({r, (short)OP_POTRF, (short)k, (short)k, (short)k, 0, 0});
-        for (int i = k + 1; i < T; ++i) tasks.push_back({r, (short)OP_TRSM, (short)k, (short)i, (short)k, 0, 0});
-        for (int i = k + 1; i < T; ++i)
-          for (int j = k + 1; j <= i; ++j) tasks.push_back({r, (short)OP_UPDATE, (short)k, (short)i, (short)j, 0, 0});
-      }
-      if (c->batched_stall && k == 0) tasks.push_back({0, (short)OP_STALL, 0, 0, 0, 0, 0});
-    }
+    build_task_list(meta, MIXED, c->batched_stall != 0, tasks);
     P.ns.assign(h_n, h_n + nrep);
     P.nb = NB;
     P.stall = c->batched_stall;
+    P.mixed = MIXED;
     P.ntasks = (int)tasks.size();
   }
-  P.mat_doubles = mo;
-  P.w_doubles = wo;
-  P.cnt_ints = co;
-  P.ld_doubles = lo;
-  P.vec_doubles = vo;
-  P.gen_blocks = gt;
-  // device layout of bt_meta: meta | params | ctl | counters | tasks
+  // device layout of bt_meta: meta | order | params | tables | ctl | counters | tasks
+  constexpr int64_t kNodes = kTabSeg * (kTabDeg + 1);
   const size_t meta_b = round_up((int64_t)nrep * sizeof(BMeta), 256);
+  const size_t ord_b = round_up((int64_t)nrep * sizeof(int), 256);
   const size_t par_b = round_up((int64_t)nrep * sizeof(MaternParams), 256);
+  const size_t tab_b = round_up((int64_t)nrep * sizeof(MaternTable), 256);
   const size_t ctl_b = 256;
   const size_t cnt_b = round_up(co * (int64_t)sizeof(int), 256);
   const size_t task_b = round_up((int64_t)P.ntasks * sizeof(BTask), 256);
+  const size_t nodes_b = (size_t)nrep * kNodes * sizeof(double);
   exa_status st;
-  if ((st = ensure(c, c->bt_meta, meta_b + par_b + ctl_b + cnt_b + task_b, "batched metadata")) != EXA_OK) return st;
+  if ((st = ensure(c, c->bt_meta, meta_b + ord_b + par_b + tab_b + ctl_b + cnt_b + task_b, "batched metadata")) !=
+      EXA_OK)
+    return st;
   if ((st = ensure(c, c->bt_mat, (size_t)mo * sizeof(double), "batched matrices")) != EXA_OK) return st;
-  if ((st = ensure(c, c->bt_work, (size_t)(wo + lo) * sizeof(double), "batched inverses")) != EXA_OK) return st;
-  if ((st = ensure(c, c->bt_vec, (size_t)vo * sizeof(double), "batched vectors")) != EXA_OK) return st;
+  if (MIXED && (st = ensure(c, c->bt_mat2, (size_t)mo * sizeof(double), "batched FP64 copies")) != EXA_OK) return st;
+  const size_t work_b = (size_t)(wo + lo) * sizeof(double);
+  if ((st = ensure(c, c->bt_work, work_b > nodes_b ? work_b : nodes_b, "batched inverses")) != EXA_OK) return st;
+  if ((st = ensure(c, c->bt_vec, (size_t)(MIXED ? 3 : 1) * vo * sizeof(double), "batched vectors")) != EXA_OK)
+    return st;
   uint8_t* base = (uint8_t*)c->bt_meta.p;
   BMeta* dM = (BMeta*)base;
-  MaternParams* dP = (MaternParams*)(base + meta_b);
-  BCtl* dC = (BCtl*)(base + meta_b + par_b);
-  int* dCnt = (int*)(base + meta_b + par_b + ctl_b);
-  BTask* dT = (BTask*)(base + meta_b + par_b + ctl_b + cnt_b);
+  int* dOrd = (int*)(base + meta_b);
+  MaternParams* dP = (MaternParams*)(base + meta_b + ord_b);
+  MaternTable* dTab = (MaternTable*)(base + meta_b + ord_b + par_b);
+  BCtl* dC = (BCtl*)(base + meta_b + ord_b + par_b + tab_b);
+  int* dCnt = (int*)(base + meta_b + ord_b + par_b + tab_b + ctl_b);
+  BTask* dT = (BTask*)(base + meta_b + ord_b + par_b + tab_b + ctl_b + cnt_b);
+  // the table nodes are scratch until the factorisation overwrites bt_work
+  double* dNodes = (double*)c->bt_work.p;
   // host staging (pinned, owned by the context so captured copies stay valid)
-  const size_t stage_need = meta_b + (same ? 0 : task_b);
+  const size_t stage_need = meta_b + ord_b + (same ? 0 : task_b);
   if (c->bt_stage_bytes < stage_need) {
     if (c->bt_stage) cudaFreeHost(c->bt_stage);
     c->bt_stage = nullptr;
@@ -493,56 +945,58 @@ static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const do
     if (cudaMallocHost(&c->bt_stage, stage_need) != cudaSuccess) return set_err(c, EXA_ERR_NOMEM, "pinned staging");
     c->bt_stage_bytes = stage_need;
   }
-  memcpy(c->bt_stage, meta.data(), nrep * sizeof(BMeta));
-  cudaError_t e = cudaMemcpyAsync(dM, c->bt_stage, nrep * sizeof(BMeta), cudaMemcpyHostToDevice, s);
+  uint8_t* hs = (uint8_t*)c->bt_stage;
+  memcpy(hs, meta.data(), nrep * sizeof(BMeta));
+  memcpy(hs + meta_b, order.data(), nrep * sizeof(int));
+  cudaError_t e = cudaMemcpyAsync(dM, hs, meta_b + ord_b, cudaMemcpyHostToDevice, s);
   if (!same && e == cudaSuccess) {
-    memcpy((uint8_t*)c->bt_stage + meta_b, tasks.data(), tasks.size() * sizeof(BTask));
-    e = cudaMemcpyAsync(dT, (uint8_t*)c->bt_stage + meta_b, tasks.size() * sizeof(BTask), cudaMemcpyHostToDevice, s);
+    memcpy(hs + meta_b + ord_b, tasks.data(), tasks.size() * sizeof(BTask));
+    e = cudaMemcpyAsync(dT, hs + meta_b + ord_b, tasks.size() * sizeof(BTask), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(dC, 0, ctl_b + cnt_b, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(DevStatus), s);
   if (e != cudaSuccess) return cuda_err(c, e, "batched setup");
   {
-    ProfScope ps(c, PK_BATCH, 0.0, 0.0);
+    ProfScope ps(c, PK_OTHER, 0.0, 0.0, 3);
     batched_params_kernel<<<(nrep + 63) / 64, 64, 0, s>>>(nrep, d_theta, dP, d_status);
+    batched_table_nodes_kernel<<<dim3((unsigned)((kNodes + 127) / 128), (unsigned)nrep), 128, 0, s>>>(dP, dNodes);
+    batched_table_coef_kernel<<<dim3(1, (unsigned)nrep), 128, 0, s>>>(dNodes, dTab);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    ProfScope ps(c, PK_GEN, 0.0, 8.0 * (double)gt * NB * NB / 2);
-    batched_gen_kernel<NB><<<(unsigned)gt, 256, 0, s>>>(nrep, dM, dP, (double*)c->bt_mat.p);
+    ProfScope ps(c, PK_GEN, 0.0, (MIXED ? 16.0 : 8.0) * (double)gt * NB * NB / 2);
+    batched_gen_kernel<NB><<<(unsigned)gt, 256, 0, s>>>(nrep, dM, dP, dTab, (double*)c->bt_mat.p,
+                                                        MIXED ? (double*)c->bt_mat2.p : nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_err(c, e, "batched generation");
   double flops = 0.0;
   for (int r = 0; r < nrep; ++r) flops += (double)meta[r].npad * meta[r].npad * meta[r].npad / 3.0;
-  {
-    const size_t smem = (size_t)2 * NB * Tile<NB>::SS * sizeof(double) > (size_t)(NB * (NB + 1) + NB) * sizeof(double)
-                            ? (size_t)2 * NB * Tile<NB>::SS * sizeof(double)
-                            : (size_t)(NB * (NB + 1) + NB) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(batched_chol_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_chol_kernel<NB>, 128, smem);
-    int want = c->batched_ctas_per_sm > 0 ? c->batched_ctas_per_sm : per_sm;
-    if (want > per_sm) want = per_sm;  // every CTA must be resident: the walk relies on it
-    if (want < 1) return set_err(c, EXA_ERR_CUDA, "batched kernel cannot be resident");
-    const int grid = want * sms;
-    ProfScope ps(c, PK_BATCH, 2.0 * flops, 0.0);
-    batched_chol_kernel<NB><<<grid, 128, smem, s>>>(dT, P.ntasks, dM, (double*)c->bt_mat.p, (double*)c->bt_work.p,
-                                                     (double*)c->bt_work.p + wo, dCnt, dC, d_status, c->d_status,
-                                                     c->batched_spin);
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess) {
+    const int mode = !MIXED ? MODE_FP64 : (c->batched_band > 0 ? MODE_F32_BAND : MODE_F32);
+    ProfScope ps(c, PK_BATCH, 2.0 * flops, 0.0);
+    const CholArgs ca{dT, P.ntasks, dM, (double*)c->bt_mat.p, (double*)c->bt_work.p, (double*)c->bt_work.p + wo,
+                      dCnt, dC, d_status, c->d_status, c->batched_spin, c->batched_band, c->batched_ctas_per_sm};
+    if (mode == MODE_FP64) st = launch_chol<NB, MODE_FP64>(c, s, ca);
+    else if (mode == MODE_F32_BAND) st = launch_chol<NB, MODE_F32_BAND>(c, s, ca);
+    else st = launch_chol<NB, MODE_F32>(c, s, ca);
+    if (st != EXA_OK) return st;
+  }
+  if (e == cudaSuccess && !MIXED) {
     ProfScope ps(c, PK_TRSV, 0.0, 4.0 * (double)vo * vo / nrep);
     batched_solve_kernel<NB><<<nrep, 256, 0, s>>>(nrep, dM, (double*)c->bt_mat.p, (double*)c->bt_work.p,
                                                    (double*)c->bt_work.p + wo, dCnt, (double*)c->bt_vec.p, d_loglik,
                                                    d_status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && MIXED) {
+    double lower = 0.0;
+    for (int r = 0; r < nrep; ++r) lower += 0.5 * (double)meta[r].npad * (double)(meta[r].npad + 1);
+    ProfScope ps(c, PK_TRSV, 0.0, 16.0 * lower);  // bytes of one refinement step
+    batched_ir_kernel<NB><<<nrep, kIrThreads, 0, s>>>(dOrd, dM, (double*)c->bt_mat.p, (double*)c->bt_mat2.p,
+                                                       (double*)c->bt_work.p, (double*)c->bt_work.p + wo, dCnt,
+                                                       (double*)c->bt_vec.p, vo, d_loglik, d_status,
+                                                       c->batched_max_iter);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_err(c, e, "batched launch");
@@ -570,10 +1024,15 @@ extern "C" exa_status exa_loglik_batched(exa_ctx* c, int32_t nrep, const int64_t
     return set_err(c, EXA_ERR_ARG, "bad batched arguments");
   for (int r = 0; r < nrep; ++r)
     if (h_n[r] < 1 || !d_locs[r] || !d_z[r]) return set_err(c, EXA_ERR_ARG, "replicate %d: bad size or pointer", r);
-  if (prec != EXA_FP64) return set_err(c, EXA_ERR_ARG, "the batched form runs in EXA_FP64");
+  if (prec != EXA_FP64 && prec != EXA_MIXED_FP32)
+    return set_err(c, EXA_ERR_ARG, "the batched form runs in EXA_FP64 or EXA_MIXED_FP32");
   if (!c->bplan) c->bplan = new BatchPlan();
-  if (c->batched_nb == 32) return batched_run<32>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status);
-  return batched_run<64>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status);
+  const bool mixed = prec == EXA_MIXED_FP32;
+  if (c->batched_nb == 32)
+    return mixed ? batched_run<32, true>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status)
+                 : batched_run<32, false>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status);
+  return mixed ? batched_run<64, true>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status)
+               : batched_run<64, false>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status);
 }
 
 extern "C" exa_status exa_ctx_set_batched(exa_ctx* c, int tile_nb, int ctas_per_sm, long long spin_cycles,
@@ -585,5 +1044,13 @@ extern "C" exa_status exa_ctx_set_batched(exa_ctx* c, int tile_nb, int ctas_per_
   c->batched_ctas_per_sm = ctas_per_sm;
   c->batched_spin = spin_cycles ? spin_cycles : 2000000000LL;
   c->batched_stall = inject_stall ? 1 : 0;
+  return EXA_OK;
+}
+
+extern "C" exa_status exa_ctx_set_batched_mixed(exa_ctx* c, int band, int max_iter) {
+  if (!c) return EXA_ERR_ARG;
+  if (band < 0 || max_iter < 0) return set_err(c, EXA_ERR_ARG, "bad batched mixed option");
+  c->batched_band = band;
+  c->batched_max_iter = max_iter ? max_iter : 10;
   return EXA_OK;
 }

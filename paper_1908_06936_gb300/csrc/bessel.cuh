@@ -179,6 +179,61 @@ __device__ __forceinline__ int table_segment(double x) {
   return (e - kTabE0) * kTabSub + sub;
 }
 
+// Table construction.  Segment sgi covers [lo, lo + w) with lo = 2^e (1 + sub / kTabSub),
+// w = 2^e / kTabSub.  Node id = sgi (kTabDeg + 1) + k is q at the k-th Chebyshev point.
+__device__ __forceinline__ void segment_geometry(int sgi, double& centre, double& half) {
+  const int e = kTabE0 + sgi / kTabSub, sub = sgi % kTabSub;
+  const double lo = ldexp(1.0 + (double)sub / kTabSub, e);
+  const double w = ldexp(1.0 / kTabSub, e);
+  centre = lo + 0.5 * w;
+  half = 0.5 * w;
+}
+
+__device__ __forceinline__ double table_node_value(const MaternParams& P, int id) {
+  const int sgi = id / (kTabDeg + 1), k = id % (kTabDeg + 1);
+  double centre, half;
+  segment_geometry(sgi, centre, half);
+  const double tk = cos(3.14159265358979323846 * (k + 0.5) / (kTabDeg + 1));
+  const double x = centre + half * tk;
+  const double lnx = log(x);
+  double knu, knum1;
+  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
+  return P.logc + P.nu * lnx + log(knu) + (scaled ? 0.0 : x);
+}
+
+// Chebyshev coefficients of segment sgi from its nodes, then their monomial form in t.
+__device__ __forceinline__ void table_segment_coefs(const double* __restrict__ nodes, int sgi,
+                                                    MaternTable* __restrict__ T) {
+  constexpr int N = kTabDeg + 1;
+  const double* q = nodes + sgi * N;
+  double cheb[N];
+  for (int j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += q[k] * cos(3.14159265358979323846 * j * (k + 0.5) / N);
+    cheb[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+  }
+  // T_0 = 1, T_1 = t, T_{j+1} = 2 t T_j - T_{j-1}
+  double a[N], tm1[N], t0[N], t1[N];
+  for (int i = 0; i < N; ++i) a[i] = tm1[i] = t0[i] = 0.0;
+  tm1[0] = 1.0;
+  t0[1] = 1.0;
+  a[0] = cheb[0];
+  for (int i = 0; i < N; ++i) a[i] += cheb[1] * t0[i];
+  for (int j = 2; j < N; ++j) {
+    for (int i = 0; i < N; ++i) t1[i] = (i > 0 ? 2.0 * t0[i - 1] : 0.0) - tm1[i];
+    for (int i = 0; i < N; ++i) a[i] += cheb[j] * t1[i];
+    for (int i = 0; i < N; ++i) {
+      tm1[i] = t0[i];
+      t0[i] = t1[i];
+    }
+  }
+  double centre, half;
+  segment_geometry(sgi, centre, half);
+  T->ih[sgi] = 1.0 / half;
+  T->mc[sgi] = -centre / half;
+  for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
+}
+
 // Sigma at distance r from the table (exact routine below 2^kTabE0).
 __device__ __forceinline__ double matern_value_tab(const MaternParams& P, const MaternTable* __restrict__ T, double r) {
   if (r == 0.0) return P.sigma2;

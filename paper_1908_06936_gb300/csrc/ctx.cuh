@@ -55,7 +55,7 @@ struct exa_ctx {
   exa::DevBuf gr_part;      // second n x n buffer: Sigma^-1 for the gradient trace term
   exa::DevBuf gr_blocks;    // per-block gradient partial sums
   // batched
-  exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work;
+  exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work, bt_mat2;
   exa::BatchPlan* bplan = nullptr;  // cached work list of the last shape set
   void* bt_stage = nullptr;         // pinned host staging for the work list / metadata
   size_t bt_stage_bytes = 0;
@@ -63,6 +63,8 @@ struct exa_ctx {
   int batched_ctas_per_sm = 0;      // 0: as many as fit
   long long batched_spin = 2000000000LL;  // bound of one dependency wait (SM cycles)
   int batched_stall = 0;            // test hook: add a task whose dependency is never met
+  int batched_band = 0;             // mixed: tile updates within this many tile diagonals stay FP64
+  int batched_max_iter = 10;        // mixed: refinement steps per replicate at most
   // status and small results
   exa::DevStatus* d_status = nullptr;
   exa::DevStatus* h_status = nullptr;  // pinned

@@ -88,62 +88,19 @@ cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int
 }
 
 // ---------------------------------------------------------------------------
-// Table construction: q at the kTabDeg + 1 Chebyshev points of every segment by
-// the exact routine, then Chebyshev coefficients and their monomial form.
+// Table construction (the per-segment arithmetic lives in bessel.cuh, shared
+// with the batched form's per-replicate tables).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void segment_geometry(int sgi, double& centre, double& half) {
-  const int e = kTabE0 + sgi / kTabSub, sub = sgi % kTabSub;
-  const double lo = ldexp(1.0 + (double)sub / kTabSub, e);
-  const double w = ldexp(1.0 / kTabSub, e);
-  centre = lo + 0.5 * w;
-  half = 0.5 * w;
-}
-
 __global__ void matern_table_nodes_kernel(const __grid_constant__ MaternParams P, double* __restrict__ nodes) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= kTabSeg * (kTabDeg + 1)) return;
-  const int sgi = id / (kTabDeg + 1), k = id % (kTabDeg + 1);
-  double centre, half;
-  segment_geometry(sgi, centre, half);
-  const double tk = cos(3.14159265358979323846 * (k + 0.5) / (kTabDeg + 1));
-  const double x = centre + half * tk;
-  const double lnx = log(x);
-  double knu, knum1;
-  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
-  nodes[id] = P.logc + P.nu * lnx + log(knu) + (scaled ? 0.0 : x);
+  nodes[id] = table_node_value(P, id);
 }
 
 __global__ void matern_table_coef_kernel(const double* __restrict__ nodes, MaternTable* __restrict__ T) {
   const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
   if (sgi >= kTabSeg) return;
-  constexpr int N = kTabDeg + 1;
-  const double* q = nodes + sgi * N;
-  double cheb[N];
-  for (int j = 0; j < N; ++j) {
-    double s = 0.0;
-    for (int k = 0; k < N; ++k) s += q[k] * cos(3.14159265358979323846 * j * (k + 0.5) / N);
-    cheb[j] = (j == 0 ? 1.0 : 2.0) * s / N;
-  }
-  // monomial coefficients: T_0 = 1, T_1 = t, T_{j+1} = 2 t T_j - T_{j-1}
-  double a[N], tm1[N], t0[N], t1[N];
-  for (int i = 0; i < N; ++i) a[i] = tm1[i] = t0[i] = 0.0;
-  tm1[0] = 1.0;  // T_0
-  t0[1] = 1.0;   // T_1
-  a[0] = cheb[0];
-  for (int i = 0; i < N; ++i) a[i] += cheb[1] * t0[i];
-  for (int j = 2; j < N; ++j) {
-    for (int i = 0; i < N; ++i) t1[i] = (i > 0 ? 2.0 * t0[i - 1] : 0.0) - tm1[i];
-    for (int i = 0; i < N; ++i) a[i] += cheb[j] * t1[i];
-    for (int i = 0; i < N; ++i) {
-      tm1[i] = t0[i];
-      t0[i] = t1[i];
-    }
-  }
-  double centre, half;
-  segment_geometry(sgi, centre, half);
-  T->ih[sgi] = 1.0 / half;
-  T->mc[sgi] = -centre / half;
-  for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
+  table_segment_coefs(nodes, sgi, T);
 }
 
 cudaError_t launch_matern_table(cudaStream_t s, const MaternParams& p, MaternTable* tab, double* nodes) {

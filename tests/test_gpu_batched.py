@@ -145,3 +145,125 @@ def test_batched_full_config_sigma2_scaling(ctx):
     for r in np.argsort(n)[:3]:
         ref = oracle.loglik(locs[r], zs[r], (1.0, 0.1, 0.5))["l"]
         assert abs(res[1.0][r] - ref) <= 1e-10 * abs(ref)
+
+
+# ---- mixed precision (FP32 off-diagonal tiles, FP64 diagonal tiles, FP64 refinement) ----
+MIXED = 3  # EXA_MIXED_FP32
+MIXED_TOL = 1e-6  # stated bound for a reduced-precision log-likelihood, |dl|/|l|
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_batched_mixed_vs_oracle(ctx, tile):
+    import paper_1908_06936_gb300 as exa
+
+    sides = [5, 9, 12, 17, 20, 1, 3, 25, 8, 14, 31]
+    locs, zs = make_batch(sides, seed=50)
+    thetas = synth.theta_perturbations((1.0, 0.1, 0.5), len(sides), seed=4)
+    exa.exa_ctx_set_batched(ctx.handle, tile, 0, 0, 0)
+    try:
+        got, st = run(ctx, locs, zs, thetas, prec=MIXED)
+    finally:
+        exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
+    assert np.all(st == 0), st
+    for r in range(len(sides)):
+        ref = oracle.loglik(locs[r], zs[r], thetas[r])["l"]
+        assert abs(got[r] - ref) <= MIXED_TOL * abs(ref), (r, got[r], ref)
+
+
+def test_batched_mixed_all_fp64_band_is_exact(ctx):
+    # a band wider than every replicate keeps every tile in FP64: the refinement
+    # then starts from an FP64 factor and the result matches the oracle to FP64 accuracy
+    import paper_1908_06936_gb300 as exa
+
+    sides = [6, 13, 22, 30]
+    locs, zs = make_batch(sides, seed=60)
+    thetas = synth.theta_perturbations((1.0, 0.1, 0.5), len(sides), seed=5)
+    exa.exa_ctx_set_batched_mixed(ctx.handle, 1000, 0)
+    try:
+        got, st = run(ctx, locs, zs, thetas, prec=MIXED)
+    finally:
+        exa.exa_ctx_set_batched_mixed(ctx.handle, 0, 0)
+    assert np.all(st == 0)
+    for r in range(len(sides)):
+        ref = oracle.loglik(locs[r], zs[r], thetas[r])["l"]
+        assert abs(got[r] - ref) <= 1e-10 * abs(ref), (r, got[r], ref)
+
+
+def test_batched_mixed_one_step_reports_unconverged(ctx):
+    # one refinement step from an FP32 factor of a smooth field cannot reach the
+    # 1e-8 residual: such replicates must say so (status 6, NaN), the rest be right
+    import paper_1908_06936_gb300 as exa
+
+    sides = [20, 24, 28]
+    theta = (1.0, 0.3, 1.5)
+    locs, zs = make_batch(sides, seed=70, theta0=theta)
+    exa.exa_ctx_set_batched_mixed(ctx.handle, 0, 1)
+    try:
+        got, st = run(ctx, locs, zs, np.tile(theta, (3, 1)), prec=MIXED)
+    finally:
+        exa.exa_ctx_set_batched_mixed(ctx.handle, 0, 0)
+    assert set(st.tolist()) <= {0, exa.EXA_ERR_IR_NOCONV, exa.EXA_ERR_NOT_SPD}
+    for r in range(3):
+        if st[r] == 0:
+            ref = oracle.loglik(locs[r], zs[r], theta)["l"]
+            assert abs(got[r] - ref) <= MIXED_TOL * abs(ref)
+        else:
+            assert math.isnan(got[r])
+
+
+def test_batched_mixed_graph_replay(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    sides = [11, 19, 16]
+    locs, zs = make_batch(sides, seed=80)
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.tile([1.0, 0.1, 0.5], 3))
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    st = torch.empty(3, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        exa.exa_ctx_set_stream(ctx.handle, s.cuda_stream)
+        ctx.check(exa.exa_loglik_batched(ctx.handle, 3, ns, dl, dz, th, MIXED, out, st))
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctx.check(exa.exa_loglik_batched(ctx.handle, 3, ns, dl, dz, th, MIXED, out, st))
+    exa.exa_ctx_set_stream(ctx.handle, torch.cuda.current_stream().cuda_stream)
+    for new in ([1.3, 0.08, 0.7], [0.6, 0.15, 0.4]):
+        th.copy_(torch.tensor(new * 3, dtype=torch.float64))
+        g.replay()
+        torch.cuda.synchronize()
+        res, sts = out.cpu().numpy(), st.cpu().numpy()
+        assert np.all(sts == 0)
+        for r in range(3):
+            ref = oracle.loglik(locs[r], zs[r], new)["l"]
+            assert abs(res[r] - ref) <= MIXED_TOL * abs(ref)
+
+
+def test_batched_mixed_full_config_vs_fp64(ctx):
+    # 256 replicates, n_i = m_i^2 with m_i ~ U{20..80}, theta0 = (1, 0.1, 0.5), Z = L eps per replicate
+    sides = synth.replicate_sides(256, seed=5)
+    locs = [synth.jittered_grid(int(m), 1000 + r) for r, m in enumerate(sides)]
+    zs = [synth.normals(int(m) ** 2, 1000 + r) for r, m in enumerate(sides)]
+    th = np.tile([1.0, 0.1, 0.5], (256, 1))
+    ref, st64 = run(ctx, locs, zs, th, prec=0)
+    got, st = run(ctx, locs, zs, th, prec=MIXED)
+    assert np.all(st64 == 0) and np.all(st == 0)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= MIXED_TOL, (rel.max(), int(rel.argmax()))
+
+
+def test_batched_rejects_tensor_core_split_precisions(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    locs, zs = make_batch([6], seed=90)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    th = to_dev(np.array([1.0, 0.1, 0.5]))
+    for prec in (exa.EXA_MIXED_TF32X3, exa.EXA_MIXED_BF16X3, 7):
+        rc = exa.exa_loglik_batched(ctx.handle, 1, [36], [to_dev(locs[0])], [to_dev(zs[0])], th, prec, out, st)
+        assert rc == exa.EXA_ERR_ARG
