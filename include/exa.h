@@ -221,6 +221,18 @@ int exa_profile_read(exa_ctx* ctx, exa_kernel_stat* out, int max, int reset);
  *                EXA_ERR_TIMEOUT (the path a real stall would take).                 */
 exa_status exa_ctx_set_batched(exa_ctx* ctx, int tile_nb, int ctas_per_sm, long long spin_cycles, int inject_stall);
 
+/* Tile autotuner of the batched form.  Runs the batch (same arguments as
+ * exa_loglik_batched) with every candidate configuration -- tile 64 and 32,
+ * each with the largest and the next-largest number of resident CTAs per SM --
+ * twice (plan + buffers, then a run timed with CUDA events on the context
+ * stream), keeps the fastest in the context and returns it (tile_nb,
+ * ctas_per_sm, best_ms: host outputs).  Synchronises the stream.  d_loglik /
+ * d_status hold the last candidate's results.  On any failure the previous
+ * configuration is kept and the error returned.                            */
+exa_status exa_batched_autotune(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, const double* const* d_locs,
+                                const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
+                                int32_t* d_status, int* tile_nb, int* ctas_per_sm, float* best_ms);
+
 /* Options of the mixed-precision batched form:
  *   band      TRSM / update tiles fewer than `band` tile diagonals away from the
  *             diagonal stay FP64 (0: every off-diagonal product on tensor cores);

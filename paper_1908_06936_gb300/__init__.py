@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -93,6 +93,10 @@ def lib() -> ctypes.CDLL:
                 "exa_loglik_noalloc": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
                 "exa_ctx_set_batched_mixed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+                "exa_batched_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                                        ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P,
+                                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                        ctypes.POINTER(ctypes.c_float)]),
                 "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
@@ -262,6 +266,19 @@ def exa_loglik_batched(ctx: int, nrep: int, ns, locs_list, z_list, theta_dev, pr
     return lib().exa_loglik_batched(_P(ctx), nrep, h_n, pl, pz, _P(_dev_ptr(theta_dev, "theta", 3 * nrep)),
                                     int(prec), _P(_dev_ptr(loglik_dev, "loglik", nrep)),
                                     _P(status_dev.data_ptr()))
+
+
+def exa_batched_autotune(ctx: int, nrep: int, ns, locs_list, z_list, theta_dev, prec: int, loglik_dev,
+                         status_dev) -> tuple:
+    """Native tile autotuner of the batched form; returns (status, tile_nb, ctas_per_sm, best_ms)."""
+    h_n = (_I64 * nrep)(*[int(v) for v in ns])
+    pl = (_P * nrep)(*[_dev_ptr(t, "locs[%d]" % i, 2 * int(ns[i])) for i, t in enumerate(locs_list)])
+    pz = (_P * nrep)(*[_dev_ptr(t, "z[%d]" % i, int(ns[i])) for i, t in enumerate(z_list)])
+    nb, cps, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0.0)
+    rc = lib().exa_batched_autotune(_P(ctx), nrep, h_n, pl, pz, _P(_dev_ptr(theta_dev, "theta", 3 * nrep)), int(prec),
+                                    _P(_dev_ptr(loglik_dev, "loglik", nrep)), _P(status_dev.data_ptr()),
+                                    ctypes.byref(nb), ctypes.byref(cps), ctypes.byref(ms))
+    return rc, nb.value, cps.value, ms.value
 
 
 def exa_simulate(ctx: int, locs, eps, theta, n: int, prec: int, z) -> int:

@@ -861,6 +861,23 @@ static exa_status launch_chol(exa_ctx* c, cudaStream_t s, const CholArgs& a) {
   return e == cudaSuccess ? EXA_OK : cuda_err(c, e, "batched factorisation launch");
 }
 
+template <int NB, int MODE>
+static int max_ctas_per_sm() {
+  const size_t smem = Tile<NB>::smem(MODE);
+  cudaFuncSetAttribute(batched_chol_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_chol_kernel<NB, MODE>, kBThreads, smem);
+  return per_sm;
+}
+
+static int max_ctas_per_sm(int nb, int mode) {
+  if (nb == 32)
+    return mode == MODE_FP64 ? max_ctas_per_sm<32, MODE_FP64>()
+                             : (mode == MODE_F32_BAND ? max_ctas_per_sm<32, MODE_F32_BAND>() : max_ctas_per_sm<32, MODE_F32>());
+  return mode == MODE_FP64 ? max_ctas_per_sm<64, MODE_FP64>()
+                           : (mode == MODE_F32_BAND ? max_ctas_per_sm<64, MODE_F32_BAND>() : max_ctas_per_sm<64, MODE_F32>());
+}
+
 template <int NB, bool MIXED>
 static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const double* const* d_locs,
                               const double* const* d_z, const double* d_theta, double* d_loglik, int32_t* d_status) {
@@ -1044,6 +1061,64 @@ extern "C" exa_status exa_ctx_set_batched(exa_ctx* c, int tile_nb, int ctas_per_
   c->batched_ctas_per_sm = ctas_per_sm;
   c->batched_spin = spin_cycles ? spin_cycles : 2000000000LL;
   c->batched_stall = inject_stall ? 1 : 0;
+  return EXA_OK;
+}
+
+// Tile autotuner: times every candidate (tile 32 / 64, the largest and the next
+// CTAs-per-SM count that fit) on the caller's batch and keeps the fastest.
+extern "C" exa_status exa_batched_autotune(exa_ctx* c, int32_t nrep, const int64_t* h_n, const double* const* d_locs,
+                                           const double* const* d_z, const double* d_theta, exa_prec prec,
+                                           double* d_loglik, int32_t* d_status, int* tile_nb, int* ctas_per_sm,
+                                           float* best_ms) {
+  if (!c || !tile_nb || !ctas_per_sm || !best_ms) return c ? set_err(c, EXA_ERR_ARG, "null output") : EXA_ERR_ARG;
+  const int mode = prec == EXA_FP64 ? MODE_FP64 : (c->batched_band > 0 ? MODE_F32_BAND : MODE_F32);
+  const int keep_nb = c->batched_nb, keep_cps = c->batched_ctas_per_sm;
+  float best = 3.4e38f;
+  int bnb = keep_nb, bcps = keep_cps;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_err(c, cudaGetLastError(), "autotune events");
+  }
+  exa_status st = EXA_OK;
+  for (int nb : {64, 32}) {
+    const int top = max_ctas_per_sm(nb, mode);
+    for (int cps : {top, top - 1}) {
+      if (cps < 1 || st != EXA_OK) continue;
+      c->batched_nb = nb;
+      c->batched_ctas_per_sm = cps;
+      // first call builds the plan and the buffers for this tile; the second is timed
+      st = exa_loglik_batched(c, nrep, h_n, d_locs, d_z, d_theta, prec, d_loglik, d_status);
+      if (st == EXA_OK) {
+        cudaEventRecord(e0, c->stream);
+        st = exa_loglik_batched(c, nrep, h_n, d_locs, d_z, d_theta, prec, d_loglik, d_status);
+        cudaEventRecord(e1, c->stream);
+      }
+      if (st == EXA_OK) {
+        const cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          st = cuda_err(c, e != cudaSuccess ? e : cudaGetLastError(), "autotune timing");
+        } else if (ms < best) {
+          best = ms;
+          bnb = nb;
+          bcps = cps;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EXA_OK) {
+    c->batched_nb = keep_nb;
+    c->batched_ctas_per_sm = keep_cps;
+    return st;
+  }
+  c->batched_nb = bnb;
+  c->batched_ctas_per_sm = bcps;
+  *tile_nb = bnb;
+  *ctas_per_sm = bcps;
+  *best_ms = best;
   return EXA_OK;
 }
 

@@ -267,3 +267,30 @@ def test_batched_rejects_tensor_core_split_precisions(ctx):
     for prec in (exa.EXA_MIXED_TF32X3, exa.EXA_MIXED_BF16X3, 7):
         rc = exa.exa_loglik_batched(ctx.handle, 1, [36], [to_dev(locs[0])], [to_dev(zs[0])], th, prec, out, st)
         assert rc == exa.EXA_ERR_ARG
+
+
+def test_batched_autotune_picks_a_candidate_and_keeps_results(ctx, tmp_path):
+    import torch
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import tune
+
+    sides = [8, 15, 21, 12]
+    locs, zs = make_batch(sides, seed=95)
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.tile([1.0, 0.1, 0.5], 4))
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    st = torch.empty(4, dtype=torch.int32, device="cuda")
+    try:
+        r = tune.autotune_batched(ctx, ns, dl, dz, th, MIXED, out, st, cache_path=str(tmp_path / "t.json"))
+        assert r["tile_nb"] in (32, 64) and r["ctas_per_sm"] >= 1 and r["ms"] > 0 and not r["cached"]
+        r2 = tune.autotune_batched(ctx, ns, dl, dz, th, MIXED, out, st, cache_path=str(tmp_path / "t.json"))
+        assert r2["cached"] and r2["tile_nb"] == r["tile_nb"]
+        got, sts = run(ctx, locs, zs, np.tile([1.0, 0.1, 0.5], (4, 1)), prec=MIXED)
+    finally:
+        exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
+    assert np.all(sts == 0)
+    for r_ in range(4):
+        ref = oracle.loglik(locs[r_], zs[r_], (1.0, 0.1, 0.5))["l"]
+        assert abs(got[r_] - ref) <= MIXED_TOL * abs(ref)
