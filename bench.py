@@ -252,6 +252,52 @@ def batched_leg(args, ctx) -> dict:
     return leg
 
 
+def batched_mle_leg(args) -> dict:
+    """theta-hat distribution of the 256 config-5 replicates: every replicate fitted by its
+    own bounded Nelder-Mead in log(theta), all advanced in lockstep by one CUDA-graph replay
+    of the mixed-precision batch per step; the smallest replicates are re-fitted with the
+    same search on the FP64 oracle (host cores) for comparison."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+    from paper_1908_06936_gb300.mle import fit_replicates, fit_replicates_with
+
+    nrep = 256
+    sides = synth.replicate_sides(nrep, seed=5)
+    locs = [synth.jittered_grid(int(m), 2000 + r) for r, m in enumerate(sides)]
+    eps = [synth.normals(int(m) ** 2, 2000 + r) for r, m in enumerate(sides)]
+    ns = [l.shape[0] for l in locs]
+    dl = [torch.as_tensor(l, device="cuda") for l in locs]
+    # exact realisations Z = L eps at theta0 (the library's FP64 factor)
+    dz = []
+    with exa.Context() as c:
+        for l, e in zip(dl, eps):
+            z = torch.empty(l.shape[0], dtype=torch.float64, device="cuda")
+            c.check(exa.exa_simulate(c.handle, l, torch.as_tensor(e, device="cuda"), [1.0, 0.1, 0.5],
+                                     l.shape[0], exa.EXA_FP64, z))
+            dz.append(z)
+    torch.cuda.synchronize()
+    kw = dict(x0=None, ftol=1e-5, xtol=1e-4, max_evals=args.batched_mle_evals)
+    res = fit_replicates(ns, dl, dz, exa.EXA_MIXED_FP32, **kw)
+    th = res["theta"]
+    small = list(np.argsort(ns)[:2])
+    zs_host = [dz[r].cpu().numpy() for r in small]
+    ref = fit_replicates_with(lambda i, t: oracle.loglik(locs[small[i]], zs_host[i], t)["l"], len(small), **kw)
+    return {"workload": "256 replicates (config 5 sizes), Z = L eps at theta0 = (1, 0.1, 0.5); start at the lower "
+                        "bounds; mixed-precision batched evaluations",
+            "steps": res["steps"], "seconds": res["seconds"], "replicate_evals_per_s": res["replicate_evals_per_s"],
+            "evals_mean": float(np.mean(res["evals"])), "converged_before_budget": int(np.sum(res["evals"] < kw["max_evals"])),
+            "theta_hat_median": np.median(th, axis=0).tolist(), "theta_hat_mean": np.mean(th, axis=0).tolist(),
+            "theta_hat_std": np.std(th, axis=0).tolist(),
+            "theta_hat_q10_q90": [np.quantile(th, 0.1, axis=0).tolist(), np.quantile(th, 0.9, axis=0).tolist()],
+            "oracle_check": [{"replicate": int(r), "n": int(ns[r]), "theta_gpu": th[r].tolist(),
+                              "theta_oracle": ref["theta"][i].tolist(), "loglik_gpu": float(res["loglik"][r]),
+                              "loglik_oracle": float(ref["loglik"][i])} for i, r in enumerate(small)]}
+
+
 def run_ours(args, rank: int, world: int) -> dict | None:
     import numpy as np
     import torch
@@ -336,6 +382,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         pk = peaks()
         rl = roofline(stats, pk)
         batched = batched_leg(args, ctx) if args.batched_steps > 0 else None
+        batched_mle = batched_mle_leg(args) if args.batched_mle_evals > 0 else None
         # CPU oracle baseline on a bounded sample of the same field
         n_s = args.cpu_sample
         cs = oracle_sample(locs, z_host, n_s)
@@ -356,6 +403,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "speedup_mixed_vs_fp64": (fp64["ms_per_eval"] / (ms_max / args.steps)) if fp64 else None,
             "roofline": rl,
             "batched": batched,
+            "batched_mle": batched_mle,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()} for st in stats],
             "cpu_baseline": cpu_baseline_entry(n, n_s, cs["seconds"], cs["threads"]),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -402,6 +450,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 evaluations at the same n (0 to skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="graph replays of the 256-replicate mixed batch (0 skips the batched leg)")
+    ap.add_argument("--batched-mle-evals", type=int, default=0,
+                    help="fit theta for the 256 batched replicates with this many evaluations each (0 skips)")
     ap.add_argument("--batched-fp64-steps", type=int, default=1, help="timed FP64 runs of the same batch")
     ap.add_argument("--cpu-sample", type=int, default=3600, help="oracle sample size for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=2500, help="oracle sample size per reference step")

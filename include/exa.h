@@ -75,7 +75,8 @@ typedef struct {
   double loglik;      /* l(theta) */
   double logdet;      /* log|Sigma| = 2 sum log L_ii */
   double quad;        /* z^T Sigma^-1 z */
-  double ir_resid;    /* mixed: final ||z - Sigma x||_2 / ||z||_2; FP64: 0 */
+  double ir_resid;    /* mixed: last computed ||z - Sigma x||_2 / ||z||_2 (taken before the final
+                         correction when the quadratic form settled first); FP64: 0 */
   int32_t ir_iters;   /* mixed: refinement steps taken; FP64: 0 */
   int32_t tile_nb;    /* tile size used by the factorisation */
   int32_t exact_band; /* mixed: tile rows next to the diagonal with exact products (all tiles when = T) */

@@ -49,8 +49,9 @@ struct exa_ctx {
   exa::DevBuf mx_split_b;   // split-precision operands (B role: inverse diagonal block / test B)
   exa::SplitOperand sp_a, sp_a2, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
-  exa::DevBuf mx_w2;        // inverses of the 256-wide diagonal blocks (for the solves)
+  exa::DevBuf mx_w2;        // inverse of the panel-wide diagonal block (row-major)
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
+  exa::DevBuf mx_symv;      // partial sums of the tiled symmetric product
   // gradient
   exa::DevBuf gr_part;      // second n x n buffer: Sigma^-1 for the gradient trace term
   exa::DevBuf gr_blocks;    // per-block gradient partial sums

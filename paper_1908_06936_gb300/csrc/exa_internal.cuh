@@ -121,12 +121,20 @@ cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double al
                                   int64_t ac, const double* b, int64_t br, int64_t bc, double beta, double* c,
                                   int64_t cr, int64_t cc, const DevStatus* st);
 cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w);
-// Persistent forward + backward solve with 128-wide tiles: x = (L L^T)^-1 rhs.
-// rhs_work (npad, overwritten), sbuf (npad), flags (2 npad/128 + 1 ints) are scratch.
+// Persistent forward + backward solve with 128-wide tiles: x = (L L^T)^-1 rhs.  The
+// strictly upper off-diagonal tiles of a must hold L^T (launch_transpose_lower_to_upper).
+// rhs_work (npad, overwritten) and flags (2 npad/128 + 1 ints) are scratch.
 cudaError_t launch_llt_solve_persistent(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* w,
-                                        double* rhs_work, double* x, double* sbuf, int* flags, DevStatus* st);
+                                        double* rhs_work, double* x, int* flags, DevStatus* st);
+// Writes L^T into the strictly upper off-diagonal 128-tiles of a (npad % 128 == 0).
+cudaError_t launch_transpose_lower_to_upper(cudaStream_t s, double* a, int64_t ld, int64_t npad);
 // Refinement helpers.
 cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y);
+// Same product in one pass over 128 x 128 tiles (npad % 128 == 0); partials holds
+// symv_tiled_partials(npad) doubles.  Fixed summation order.
+int64_t symv_tiled_partials(int64_t npad);
+cudaError_t launch_symv_lower_tiled(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* x,
+                                    double* y, double* partials);
 cudaError_t launch_residual(cudaStream_t s, const double* z, const double* y, double* r, int64_t n);
 cudaError_t launch_axpy(cudaStream_t s, double a, const double* x, double* y, int64_t n);
 cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t n, double* partial, double* out);

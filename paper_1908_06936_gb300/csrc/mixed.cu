@@ -13,6 +13,7 @@ namespace exa {
 constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
+constexpr double kIrQuadTol = 1e-10;  // refinement stops once |z^T d| <= kIrQuadTol |z^T x|
 constexpr int kLookaheadSMs = 16;         // SMs left to the look-ahead stream during a trailing update
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
@@ -294,14 +295,14 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
 
 // x = (L L^T)^-1 rhs with the FP64-stored factor, on 128-wide tiles with the
 // stored inverses of the diagonal sub-tiles.
+// x = (L L^T)^-1 rhs; the upper tiles of a hold L^T.  flags: scratch for the solves' flags.
 static cudaError_t solve_llt(exa_ctx* c, const double* a, int64_t ld, int64_t npad, const double* rhs, double* x,
-                             double* work, double* part) {
-  // part holds the backward partial sums (npad doubles) followed by the flags
+                             double* work, int* flags) {
   cudaError_t e = cudaMemcpyAsync(work, rhs, npad * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return e;
   ProfScope ps(c, PK_TRSV, 2.0 * (double)npad * (double)npad, 8.0 * (double)npad * (double)npad, 2);
-  return launch_llt_solve_persistent(c->stream, a, ld, npad, (const double*)c->w_all.p, work, x, part,
-                                     (int*)(part + npad), c->d_status);
+  return launch_llt_solve_persistent(c->stream, a, ld, npad, (const double*)c->w_all.p, work, x, flags,
+                                     c->d_status);
 }
 
 // Generation (FP64, with the per-offset maxima for the precision map), the
@@ -390,7 +391,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   double* y = d + npad;
   double* work = y + npad;
   double* part = (double*)c->partial.p;
-  double* red = part + 2 * kRedPartials;  // backward-solve partials live after the reduction partials
+  double* red = part + 2 * kRedPartials;  // the solves' flags live after the reduction partials
   cudaStream_t s = c->stream;
   cudaEventRecord(c->ev[0], s);
   int band = 0;
@@ -401,16 +402,29 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   if (e == cudaSuccess) e = launch_pad_vector(s, d_z, n, npad, zp);
   if (e == cudaSuccess) e = launch_sumsq(s, zp, npad, part, c->d_scalars + 2);
   double* A = (double*)c->mat.p;
-  if (e == cudaSuccess) e = solve_llt(c, A, npad, npad, zp, x, work, red);
+  if (e == cudaSuccess) {
+    // L^T into the unused upper triangle: the backward solves stream contiguous columns
+    ProfScope ps(c, PK_OTHER, 0.0, 8.0 * (double)npad * (double)npad);
+    e = launch_transpose_lower_to_upper(s, A, npad, npad);
+  }
+  if (e == cudaSuccess) e = solve_llt(c, A, npad, npad, zp, x, work, (int*)red);
   if (e != cudaSuccess) return cuda_err(c, e, "solve launch");
-  // iterative refinement of x = Sigma^-1 z with the FP64 residual
+  // iterative refinement of x = Sigma^-1 z with the FP64 residual.  It stops when the
+  // residual no longer halves or reaches rounding level, or once a correction d
+  // changes the quadratic form z^T x by less than kIrQuadTol relative: later
+  // corrections are smaller still, so q (and l) are final to that accuracy.
+  if ((st = ensure(c, c->mx_symv, (size_t)symv_tiled_partials(npad) * sizeof(double), "symmetric product partials")) !=
+      EXA_OK)
+    return st;
+  double* sp = (double*)c->mx_symv.p;
   double rel = 0.0, prev = 1e300;
+  bool q_done = false;
   int it = 0;
   const int kMaxIt = 10;
   for (;; ++it) {
     {
-      ProfScope ps(c, PK_SYMV, 2.0 * (double)npad * (double)npad, 8.0 * (double)npad * (double)(npad + 1), 2);
-      e = launch_symv_lower(s, S, npad, npad, x, y);
+      ProfScope ps(c, PK_SYMV, 2.0 * (double)npad * (double)npad, 8.0 * (double)npad * (double)(npad + 1) / 2.0, 2);
+      e = launch_symv_lower_tiled(s, S, npad, npad, x, y, sp);
     }
     if (e == cudaSuccess) e = launch_residual(s, zp, y, r, npad);
     if (e == cudaSuccess) e = launch_sumsq(s, r, npad, part, c->d_scalars + 3);
@@ -420,9 +434,19 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     rel = sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]);
     if (!(rel > 1e-15) || it >= kMaxIt || rel > 0.5 * prev) break;
     prev = rel;
-    e = solve_llt(c, A, npad, npad, r, d, work, red);
+    e = solve_llt(c, A, npad, npad, r, d, work, (int*)red);
     if (e == cudaSuccess) e = launch_axpy(s, 1.0, d, x, npad);
+    if (e == cudaSuccess) e = launch_dot(s, zp, d, npad, part, c->d_scalars + 4);
+    if (e == cudaSuccess) e = launch_dot(s, zp, x, npad, part, c->d_scalars + 5);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->h_scalars + 4, c->d_scalars + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
+    if ((st = read_status(c)) != EXA_OK) return st;
+    if (fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
+      q_done = true;
+      ++it;
+      break;
+    }
   }
   e = launch_dot(s, zp, x, npad, part, c->d_scalars + 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -441,7 +465,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   out->quad = c->h_scalars[0];
   out->logdet = 2.0 * c->h_scalars[1];
   out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * out->logdet - 0.5 * out->quad;
-  if (!(rel <= kIrFailTol))
+  if (!q_done && !(rel <= kIrFailTol))
     return set_err(c, EXA_ERR_IR_NOCONV, "refinement stalled at relative residual %.3e", rel);
   return EXA_OK;
 }

@@ -205,6 +205,102 @@ __global__ void __launch_bounds__(256) symv_lower_cols_kernel(const double* __re
   if (lane == 0) y[i] += acc;
 }
 
+// One pass over the lower triangle in 128 x 128 tiles: tile (I, J), I >= J, is read
+// once and gives both of its contributions,
+//   rowpart[I][J][r] = sum_c S_IJ(r, c) x_J(c)          (to y_I)
+//   colpart[J][I][c] = sum_r S_IJ(r, c) x_I(r)          (to y_J, I > J)
+// A diagonal tile uses only its lower half: rows take c <= r, columns r > c.
+// Each warp takes 16 columns, four at a time (16 loads in flight per lane); the
+// row partials of the 8 warps are summed in a fixed order.
+constexpr int kSymvNB = 128;
+
+__global__ void __launch_bounds__(256) symv_tile_kernel(const double* __restrict__ S, int64_t ld, int T,
+                                                        const double* __restrict__ x, double* __restrict__ rowpart,
+                                                        double* __restrict__ colpart) {
+  __shared__ double xi[kSymvNB], xj[kSymvNB];
+  __shared__ double racc[8][kSymvNB];
+  // tiles column block by column block (J outer, I = J..T-1 inner): CTAs running at the
+  // same time stream neighbouring rows of the same 128 columns
+  const long long b = blockIdx.x, TT = T;
+  // first tile of column block J: S(J) = J T - J (J - 1) / 2
+  long long J = (long long)(((2.0 * TT + 1.0) - sqrt((2.0 * TT + 1.0) * (2.0 * TT + 1.0) - 8.0 * (double)b)) * 0.5);
+  if (J < 0) J = 0;
+  while (J > 0 && J * TT - J * (J - 1) / 2 > b) --J;
+  while ((J + 1) * TT - (J + 1) * J / 2 <= b) ++J;
+  const long long I = J + (b - (J * TT - J * (J - 1) / 2));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < kSymvNB) xj[tid] = x[J * kSymvNB + tid];
+  else xi[tid - kSymvNB] = x[I * kSymvNB + tid - kSymvNB];
+  __syncthreads();
+  const bool diag = (I == J);
+  const double* base = S + I * kSymvNB + J * kSymvNB * ld;
+  double ra[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c0 = warp * 16; c0 < warp * 16 + 16; c0 += 4) {
+    double v[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double* col = base + (int64_t)(c0 + u) * ld;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) v[u][rr] = __ldcs(col + lane + 32 * rr);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      double cs = 0.0;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int r = lane + 32 * rr;
+        const double e = v[u][rr];
+        const double er = (!diag || c <= r) ? e : 0.0;  // the upper half of a diagonal tile is not data
+        const double ec = (!diag || r > c) ? e : 0.0;
+        ra[rr] = fma(er, xj[c], ra[rr]);
+        cs = fma(ec, xi[r], cs);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+      if (lane == 0) colpart[(J * T + I) * kSymvNB + c] = cs;
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) racc[warp][lane + 32 * rr] = ra[rr];
+  __syncthreads();
+  if (tid < kSymvNB) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += racc[w][tid];
+    rowpart[(I * T + J) * kSymvNB + tid] = t;
+  }
+}
+
+// y_I = sum_{J <= I} rowpart[I][J] + sum_{I' >= I} colpart[I][I'], in that order.
+__global__ void __launch_bounds__(kSymvNB) symv_tile_reduce_kernel(int T, const double* __restrict__ rowpart,
+                                                                    const double* __restrict__ colpart,
+                                                                    double* __restrict__ y) {
+  const int64_t I = blockIdx.x;
+  const int r = threadIdx.x;
+  double t = 0.0;
+  for (int64_t J = 0; J <= I; ++J) t += rowpart[(I * T + J) * kSymvNB + r];
+  for (int64_t I2 = I; I2 < T; ++I2) t += colpart[(I * T + I2) * kSymvNB + r];
+  y[I * kSymvNB + r] = t;
+}
+
+int64_t symv_tiled_partials(int64_t npad) {
+  const int64_t T = npad / kSymvNB;
+  return 2 * T * T * kSymvNB;
+}
+
+cudaError_t launch_symv_lower_tiled(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* x,
+                                    double* y, double* partials) {
+  if (npad % kSymvNB) return cudaErrorInvalidValue;
+  const int64_t T = npad / kSymvNB;
+  if (T < 1) return cudaSuccess;
+  double* rowpart = partials;
+  double* colpart = partials + T * T * kSymvNB;
+  symv_tile_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(a, ld, (int)T, x, rowpart, colpart);
+  symv_tile_reduce_kernel<<<(unsigned)T, kSymvNB, 0, s>>>((int)T, rowpart, colpart, y);
+  return cudaGetLastError();
+}
+
 // r = z - y ; elementwise helpers
 __global__ void residual_kernel(const double* __restrict__ z, const double* __restrict__ y, double* __restrict__ r,
                                 int64_t n) {
@@ -300,33 +396,60 @@ __device__ __forceinline__ void ptrsv_fail(const PTrsvArgs& g, int site) {
   if (atomicExch(g.abort, 1) == 0 && atomicExch(&g.st->timeout, 1) == 0) g.st->timeout_where = site;
 }
 
+// Forward: y = L^-1 z.  The owner of block k+1 finalises y_{k+1} = W_{k+1} z_{k+1}
+// right after applying column k to z_{k+1} (its first block of that column), so the
+// chain of diagonal blocks advances one block GEMV per step; the rest of column k
+// is applied afterwards.  y_k is double-buffered in shared memory by parity.
+__device__ __forceinline__ void ptrsv_fwd_finalize(const PTrsvArgs& g, int k, double (*red)[kPNB], double* ybuf) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t k0 = (int64_t)k * kPNB;
+  const double* W = g.w + (int64_t)k * kPNB * kPNB;
+  double* zk = red[0];  // the final right-hand side of block k
+  if (tid < kPNB) zk[tid] = __ldcg(&g.z[k0 + tid]);
+  __syncthreads();
+  // warp per row of W (row-major, lower), four rows at a time, lanes along the row
+  for (int r0 = warp * 16; r0 < warp * 16 + 16; r0 += 4) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = lane + 32 * q;
+        const double w = W[(r0 + u) * kPNB + t];
+        s[u] = fma(t <= r0 + u ? w : 0.0, zk[t], s[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+    }
+    if (lane < 4) {
+      const double v = lane == 0 ? s[0] : lane == 1 ? s[1] : lane == 2 ? s[2] : s[3];
+      ybuf[r0 + lane] = v;
+      g.y[k0 + r0 + lane] = v;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicExch(&g.flags[k], 1);
+  }
+}
+
 __global__ void __launch_bounds__(256) trsv_fwd_persistent_kernel(PTrsvArgs g) {
-  __shared__ double yk[kPNB];
+  __shared__ double ybuf[2][kPNB];
   __shared__ double red[2][kPNB];
   __shared__ int ok;
   const int tid = threadIdx.x, row = tid & (kPNB - 1), half = tid >> 7;
   const int G = gridDim.x, me = blockIdx.x;
   if (*(volatile const int*)&g.st->info) return;
+  if (me == 0) ptrsv_fwd_finalize(g, 0, red, ybuf[0]);
   for (int k = 0; k < g.T; ++k) {
     const int64_t k0 = (int64_t)k * kPNB;
-    if (k % G == me) {
-      // z_k is final: every update to it was applied by this CTA, in order
-      const double* W = g.w + (int64_t)k * kPNB * kPNB;
-      double s = 0.0;
-      for (int t = half * 64; t < half * 64 + 64 && t <= row; ++t) s = fma(W[row * kPNB + t], __ldcg(&g.z[k0 + t]), s);
-      red[half][row] = s;
-      __syncthreads();
-      if (tid < kPNB) {
-        const double v = red[0][tid] + red[1][tid];
-        yk[tid] = v;
-        g.y[k0 + tid] = v;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        atomicExch(&g.flags[k], 1);
-      }
-    } else {
+    // this CTA's first block below k (blocks b with b % G == me); none now means none later
+    int b = k + 1 + ((me - (k + 1)) % G + G) % G;
+    if (b >= g.T) break;
+    if (k % G != me) {
       if (tid == 0) {
         ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
         if (!ok) ptrsv_fail(g, 41);
@@ -334,51 +457,83 @@ __global__ void __launch_bounds__(256) trsv_fwd_persistent_kernel(PTrsvArgs g) {
       }
       __syncthreads();
       if (!ok) return;
-      if (tid < kPNB) yk[tid] = __ldcg(&g.y[k0 + tid]);
-      __syncthreads();
+      if (tid < kPNB) ybuf[k & 1][tid] = __ldcg(&g.y[k0 + tid]);
     }
+    __syncthreads();
+    const double* yk = ybuf[k & 1];
     // z_b -= L_bk y_k for this CTA's blocks b > k, nearest first
-    int b = k + 1 + ((me - (k + 1)) % G + G) % G;
     for (; b < g.T; b += G) {
       const int64_t r = (int64_t)b * kPNB + row;
-      const double* col = g.a + r + k0 * g.ld;
-      double s = 0.0;
-#pragma unroll 8
-      for (int t = half * 64; t < half * 64 + 64; ++t) s = fma(__ldcg(col + (int64_t)t * g.ld), yk[t], s);
-      red[half][row] = s;
+      const double* col = g.a + r + (k0 + half * 64) * g.ld;
+      const double* yh = yk + half * 64;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+      for (int t = 0; t < 64; t += 4) {
+        s0 = fma(__ldcg(col + (int64_t)t * g.ld), yh[t], s0);
+        s1 = fma(__ldcg(col + (int64_t)(t + 1) * g.ld), yh[t + 1], s1);
+        s2 = fma(__ldcg(col + (int64_t)(t + 2) * g.ld), yh[t + 2], s2);
+        s3 = fma(__ldcg(col + (int64_t)(t + 3) * g.ld), yh[t + 3], s3);
+      }
+      red[half][row] = (s0 + s1) + (s2 + s3);
       __syncthreads();
       if (tid < kPNB) g.z[r] = g.z[r] - (red[0][tid] + red[1][tid]);
       __syncthreads();
+      if (b == k + 1) ptrsv_fwd_finalize(g, k + 1, red, ybuf[(k + 1) & 1]);
     }
   }
 }
 
+// Backward: x = L^-T y with U = L^T held in the strictly upper off-diagonal tiles of
+// the same matrix (launch_transpose_lower_to_upper), in place on y.  Mirror of the
+// forward solve: blocks from the bottom, x_k = W_k^T z_k; once x_k is known,
+// z_i -= U_ik x_k for i < k, where U_ik is column block k above the diagonal
+// (contiguous in memory).  The owner of block k-1 finalises it right after
+// applying x_k to it.
+__device__ __forceinline__ void ptrsv_bwd_finalize(const PTrsvArgs& g, int k, double* zk, double* xbuf) {
+  const int tid = threadIdx.x, t = tid & (kPNB - 1), h = tid >> 7;
+  const int64_t k0 = (int64_t)k * kPNB;
+  __shared__ double part[2][kPNB];
+  if (tid < kPNB) zk[tid] = __ldcg(&g.y[k0 + tid]);
+  __syncthreads();
+  // x_k[t] = sum_{u >= t} W_k[u][t] z_k[u]; W row-major: consecutive t are contiguous
+  const double* W = g.w + (int64_t)k * kPNB * kPNB;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+  for (int u = h * 64; u < h * 64 + 64; u += 4) {
+    s0 = fma(u >= t ? W[u * kPNB + t] : 0.0, zk[u], s0);
+    s1 = fma(u + 1 >= t ? W[(u + 1) * kPNB + t] : 0.0, zk[u + 1], s1);
+    s2 = fma(u + 2 >= t ? W[(u + 2) * kPNB + t] : 0.0, zk[u + 2], s2);
+    s3 = fma(u + 3 >= t ? W[(u + 3) * kPNB + t] : 0.0, zk[u + 3], s3);
+  }
+  part[h][t] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (tid < kPNB) {
+    const double v = part[0][tid] + part[1][tid];
+    xbuf[tid] = v;
+    g.y[k0 + tid] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicExch(&g.flags[k], 1);
+  }
+}
+
 __global__ void __launch_bounds__(256) trsv_bwd_persistent_kernel(PTrsvArgs g) {
-  __shared__ double ak[kPNB];
-  __shared__ double v[kPNB];
+  __shared__ double xbuf[2][kPNB];
+  __shared__ double zk[kPNB];
+  __shared__ double red[2][kPNB];
   __shared__ int ok;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, row = tid & (kPNB - 1), half = tid >> 7;
   const int G = gridDim.x, me = blockIdx.x;
   if (*(volatile const int*)&g.st->info) return;
-  for (int k = g.T - 1; k >= 0; --k) {
+  if ((g.T - 1) % G == me) ptrsv_bwd_finalize(g, g.T - 1, zk, xbuf[(g.T - 1) & 1]);
+  for (int k = g.T - 1; k >= 1; --k) {
     const int64_t k0 = (int64_t)k * kPNB;
-    if (k % G == me) {
-      // a_k = W_k^T (y_k - s_k); s_k was accumulated by this CTA, in order
-      if (tid < kPNB) v[tid] = g.y[k0 + tid] - g.z[k0 + tid];
-      __syncthreads();
-      const double* W = g.w + (int64_t)k * kPNB * kPNB;
-      if (tid < kPNB) {
-        double s = 0.0;
-        for (int t = tid; t < kPNB; ++t) s = fma(W[t * kPNB + tid], v[t], s);
-        ak[tid] = s;
-        g.y[k0 + tid] = s;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        atomicExch(&g.flags[k], 1);
-      }
-    } else {
+    // this CTA's first block above k, nearest first; none now means none later
+    int i = k - 1 - ((k - 1 - me) % G + G) % G;
+    if (i < 0) break;
+    if (k % G != me) {
       if (tid == 0) {
         ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
         if (!ok) ptrsv_fail(g, 42);
@@ -386,24 +541,63 @@ __global__ void __launch_bounds__(256) trsv_bwd_persistent_kernel(PTrsvArgs g) {
       }
       __syncthreads();
       if (!ok) return;
-      if (tid < kPNB) ak[tid] = __ldcg(&g.y[k0 + tid]);
-      __syncthreads();
-    }
-    // s_j += L_kj^T a_k for this CTA's blocks j < k, nearest first: warp per column
-    int j = k - 1 - ((k - 1 - me) % G + G) % G;
-    for (; j >= 0; j -= G) {
-      for (int c = warp; c < kPNB; c += 8) {
-        const double* col = g.a + k0 + ((int64_t)j * kPNB + c) * g.ld;
-        double s = 0.0;
-#pragma unroll
-        for (int r = lane; r < kPNB; r += 32) s = fma(__ldcg(col + r), ak[r], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g.z[(int64_t)j * kPNB + c] += s;
-      }
+      if (tid < kPNB) xbuf[k & 1][tid] = __ldcg(&g.y[k0 + tid]);
     }
     __syncthreads();
+    const double* xk = xbuf[k & 1];
+    for (; i >= 0; i -= G) {
+      // z_i -= U_ik x_k, U_ik(row, t) = a[i*128 + row + (k0 + t) ld]
+      const int64_t r = (int64_t)i * kPNB + row;
+      const double* col = g.a + r + (k0 + half * 64) * g.ld;
+      const double* xh = xk + half * 64;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+      for (int t = 0; t < 64; t += 4) {
+        s0 = fma(__ldcg(col + (int64_t)t * g.ld), xh[t], s0);
+        s1 = fma(__ldcg(col + (int64_t)(t + 1) * g.ld), xh[t + 1], s1);
+        s2 = fma(__ldcg(col + (int64_t)(t + 2) * g.ld), xh[t + 2], s2);
+        s3 = fma(__ldcg(col + (int64_t)(t + 3) * g.ld), xh[t + 3], s3);
+      }
+      red[half][row] = (s0 + s1) + (s2 + s3);
+      __syncthreads();
+      if (tid < kPNB) g.y[r] = g.y[r] - (red[0][tid] + red[1][tid]);
+      __syncthreads();
+      if (i == k - 1) ptrsv_bwd_finalize(g, k - 1, zk, xbuf[(k - 1) & 1]);
+    }
   }
+}
+
+// Strictly upper off-diagonal tiles <- L^T: tile (I, J), I > J, of the lower
+// triangle is written transposed to tile (J, I), in 32 x 32 pieces through
+// shared memory (both the reads and the writes run along columns).
+__global__ void __launch_bounds__(256) transpose_lower_to_upper_kernel(double* __restrict__ a, int64_t ld, int T) {
+  __shared__ double t[32][33];
+  // strictly lower tiles, column block by column block: column J holds T - 1 - J tiles
+  const long long b = blockIdx.x, TT = T;
+  long long J = (long long)(((2.0 * TT - 1.0) - sqrt((2.0 * TT - 1.0) * (2.0 * TT - 1.0) - 8.0 * (double)b)) * 0.5);
+  if (J < 0) J = 0;
+  while (J > 0 && J * (TT - 1) - J * (J - 1) / 2 > b) --J;
+  while ((J + 1) * (TT - 1) - (J + 1) * J / 2 <= b) ++J;
+  const long long I = J + 1 + (b - (J * (TT - 1) - J * (J - 1) / 2));
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int sj = 0; sj < 4; ++sj)
+    for (int si = 0; si < 4; ++si) {
+      const int64_t r0 = I * kPNB + si * 32, c0 = J * kPNB + sj * 32;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[ty + 8 * q][tx] = a[(r0 + tx) + (c0 + ty + 8 * q) * ld];  // t[c][r] = L(r, c)
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[(c0 + tx) + (r0 + ty + 8 * q) * ld] = t[tx][ty + 8 * q];  // U(c, r) = L(r, c)
+      __syncthreads();
+    }
+}
+
+cudaError_t launch_transpose_lower_to_upper(cudaStream_t s, double* a, int64_t ld, int64_t npad) {
+  const int64_t T = npad / kPNB;
+  if (npad % kPNB) return cudaErrorInvalidValue;
+  if (T < 2) return cudaSuccess;
+  transpose_lower_to_upper_kernel<<<(unsigned)(T * (T - 1) / 2), 256, 0, s>>>(a, ld, (int)T);
+  return cudaGetLastError();
 }
 
 static int ptrsv_grid() {
@@ -421,20 +615,20 @@ static int ptrsv_grid() {
   return grid;
 }
 
-// Forward (x = L^-1 rhs, rhs overwritten) then backward (x = L^-T x) solve.
-// work: npad doubles; flags: 2 T + 1 ints (zeroed here).
+// Forward (x = L^-1 rhs, rhs overwritten) then backward (x = L^-T x) solve.  The
+// strictly upper off-diagonal 128-tiles of a must hold L^T.  flags: 2 T + 1 ints
+// (zeroed here).
 cudaError_t launch_llt_solve_persistent(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* w,
-                                        double* rhs_work, double* x, double* sbuf, int* flags, DevStatus* st) {
+                                        double* rhs_work, double* x, int* flags, DevStatus* st) {
   const int T = (int)(npad / kPNB);
   cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)(2 * T + 1) * sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf, 0, (size_t)npad * sizeof(double), s);
   if (e != cudaSuccess) return e;
   const int grid = ptrsv_grid() < T ? ptrsv_grid() : T;
   PTrsvArgs g{a, ld, npad, T, w, rhs_work, x, flags, flags + 2 * T, st, 2000000000LL};
   void* args[] = {&g};
   e = cudaLaunchCooperativeKernel((const void*)trsv_fwd_persistent_kernel, grid, 256, args, 0, s);
   if (e != cudaSuccess) return e;
-  PTrsvArgs g2{a, ld, npad, T, w, sbuf, x, flags + T, flags + 2 * T, st, 2000000000LL};
+  PTrsvArgs g2{a, ld, npad, T, w, nullptr, x, flags + T, flags + 2 * T, st, 2000000000LL};
   void* args2[] = {&g2};
   return cudaLaunchCooperativeKernel((const void*)trsv_bwd_persistent_kernel, grid, 256, args2, 0, s);
 }
