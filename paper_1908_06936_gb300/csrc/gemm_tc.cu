@@ -48,8 +48,19 @@ __device__ __forceinline__ bool decode_tile(const GemmArgs& g, long long t, int&
     bj = (int)(t % g.nt);
     return true;
   }
-  if (g.enum_mode == kEnumLowerOffBand) {  // TM == TN == 128, band measured in panel-wide tiles
-    tile_tri_decode(t, bi, bj);
+  if (g.enum_mode == kEnumLowerOffBand) {
+    // TM == TN == 128, g.nt tile rows, band measured in panel-wide tiles.  Tiles are
+    // taken in supertiles of kSuper x kSuper (lower-triangle order of supertiles,
+    // row-major inside), so the CTAs of one wave share a few operand row blocks
+    // in L2 instead of streaming a different B row block each from DRAM.
+    constexpr int kSuper = kRasterSuper;
+    const long long sidx = t / (kSuper * kSuper);
+    const int loc = (int)(t % (kSuper * kSuper));
+    int SI, SJ;
+    tile_tri_decode(sidx, SI, SJ);
+    bi = SI * kSuper + loc / kSuper;
+    bj = SJ * kSuper + loc % kSuper;
+    if (bi >= g.nt || bj > bi) return false;
     const int per = g.panel / 128;
     return (bi / per - bj / per) > g.band;
   }
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(kGemmThreads)
           for (int j = 0; j < 16; ++j) {
             const int cc = cb + c * 16 + j;
             if (diag && cc > r) continue;
-            const double v = (double)__uint_as_float(acc[j]);
+            const double v = f32_bits_to_f64(acc[j]);
             cp[(int64_t)cc * g.ldc] = g.store ? v : cv[c * 16 + j] - v;
           }
         }
@@ -430,17 +441,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
       double cv[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)j * g.ldc];
-      double v[16];
+      // group g holds an exact integer a_g (|a_g| < 2^24) of weight 2^(-7(g+2)):
+      // V = sum_g a_g 2^(7(4-g)) is an integer below 2^53, combined exactly in int64
+      long long V[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = 0.0;
+      for (int j = 0; j < 16; ++j) V[j] = 0;
 #pragma unroll
-      for (int gs = S - 1; gs >= 0; --gs) {  // smallest group first
+      for (int gs = 0; gs < S; ++gs) {
         uint32_t acc[16];
         tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS + 16 * half, acc);
         tmem_ld_wait();
-        const double sc = ldexp(1.0, -7 * (gs + 2));
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fma((double)__uint_as_float(acc[j]), sc, v[j]);
+        for (int j = 0; j < 16; ++j) V[j] = V[j] * 128 + (long long)__float2int_rn(__uint_as_float(acc[j]));
       }
       fence_before();
       mbar_arrive(&accempty[b]);
@@ -450,7 +462,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
       for (int j = 0; j < 16; ++j) {
         if (lower && col0 + j > row) continue;
         const int ec = g.eb[g.b_row0 + bj * TN + 16 * half + j];
-        const double x = ldexp(v[j], er + ec);
+        const double x = i53_to_f64_scaled(V[j], er + ec - 7 * (S + 1));
         cp[(int64_t)j * g.ldc] = g.store ? x : cv[j] - x;
       }
       ++it;

@@ -15,6 +15,7 @@ constexpr int kSplitRows = 16;   // rows per CTA of the split kernel
 
 // Tile enumeration of one launch.
 enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2 };
+constexpr int kRasterSuper = 16;  // supertile edge (in 128-tiles) of the lower off-band enumeration
 
 struct OzMaps {
   CUtensorMap m[kOzSlices];
@@ -28,7 +29,7 @@ struct GemmArgs {
   int a_row0, b_row0;         // operand row origins
   int K;                      // reduction length (T3: % 32, OZ: % 64, <= 256 for OZ)
   int enum_mode;              // kEnum*
-  int nt;                     // tiles along N (kEnumFull)
+  int nt;                     // tiles along N (kEnumFull); tile rows (kEnumLowerOffBand)
   int band;                   // band width in panel tiles (kEnumLowerOffBand / kEnumBand)
   int panel;                  // panel width (256 or 512) that `band` is measured in
   long long ntiles;           // number of enumerated tiles

@@ -209,8 +209,10 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
     g.c_row0 = g.c_col0 = r0 + NB;
     g.a_row0 = g.b_row0 = NB;
     const long long t128 = m2 / 128;
+    const long long ts = (t128 + kRasterSuper - 1) / kRasterSuper;  // supertile rows
     g.enum_mode = kEnumLowerOffBand;
-    g.ntiles = t128 * (t128 + 1) / 2;
+    g.nt = (int)t128;
+    g.ntiles = ts * (ts + 1) / 2 * kRasterSuper * kRasterSuper;
     long long t3_tiles = 0;
     for (long long bi = 0; bi < t128; ++bi) {
       const long long lim = (long long)SUB * (bi / SUB - band);

@@ -155,5 +155,41 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------------------
+// Epilogue arithmetic on the integer pipe.  FP64 instructions issue at ~1.6 per
+// clock per SM on this part, so per-element FP64 work in an epilogue costs more
+// than the tile's tensor-core time; the conversions below use integer
+// instructions only.
+// ---------------------------------------------------------------------------
+
+// FP32 bit pattern -> double, exact for normal values; zero and FP32 subnormals
+// give a signed zero, infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f32_bits_to_f64(uint32_t u) {
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t m = u & 0x7FFFFFu;
+  const uint32_t de = (e == 0xFFu) ? 0x7FFu : e + 896u;  // rebias 127 -> 1023
+  uint32_t hi = sign | (de << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  if (e == 0) {
+    hi = sign;
+    lo = 0;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// V * 2^sh for an integer |V| < 2^53 (exactly representable): the double is built
+// from V's bits; results below the normal range flush to zero.
+__device__ __forceinline__ double i53_to_f64_scaled(long long V, int sh) {
+  if (V == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)V & 0x8000000000000000ull;
+  const unsigned long long M = V < 0 ? (unsigned long long)(-V) : (unsigned long long)V;
+  const int lz = __clzll((long long)M);
+  const unsigned long long frac = (M << (lz + 1)) >> 12;  // the bits below the leading one
+  const long long be = (long long)(63 - lz) + 1023 + sh;
+  if (be <= 0) return __longlong_as_double((long long)sgn);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
+}
+
 }  // namespace tc
 }  // namespace exa
