@@ -190,12 +190,19 @@ exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, co
  * major FP64 device matrix with leading dimension ldc >= m.  kind selects
  * the arithmetic: EXA_GEMM_T3 (three TF32 products, FP32 accumulation) or
  * EXA_GEMM_OZ (five exact 7-bit BF16 digit slices per row, exact FP32
- * accumulation, FP64 combination).  Shapes: m % 128 == 0, k % 64 == 0,
- * n % 128 == 0 (T3) or n % 32 == 0 (OZ), and k <= 512 (the digit sums of OZ  *
- * stay below 2^24 up to k = 512, so its accumulation is exact).             */
-typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1 } exa_gemm_kind;
+ * accumulation, FP64 combination), or EXA_GEMM_T3_PAIR (T3 on pairs of SMs
+ * with 256 x 256 tiles, tcgen05 .cta_group::2).  Shapes: m % 128 == 0 (256 for
+ * T3_PAIR), k % 64 == 0, n % 128 == 0 (T3), n % 32 == 0 (OZ) or n % 256 == 0
+ * (T3_PAIR), and k <= 512 (the digit sums of OZ stay below 2^24 up to
+ * k = 512, so its accumulation is exact).                                    */
+typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1, EXA_GEMM_T3_PAIR = 2 } exa_gemm_kind;
 exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
                            const double* d_b, double* d_c, int64_t ldc, int store);
+
+/* Off-band trailing updates of the mixed factorisation on pairs of SMs
+ * (256 x 256 tiles, tcgen05 .cta_group::2; default on) or on single SMs
+ * (128 x 128 tiles).  Both compute the same products.                       */
+exa_status exa_ctx_set_tc_pairs(exa_ctx* ctx, int on);
 
 /* Kernel accounting.  Launch counts and the algorithmic flops / bytes of every
  * kernel class are always accumulated; with profiling enabled each launch is

@@ -64,6 +64,7 @@ struct exa_ctx {
   int batched_ctas_per_sm = 0;      // 0: as many as fit
   long long batched_spin = 2000000000LL;  // bound of one dependency wait (SM cycles)
   int batched_stall = 0;            // test hook: add a task whose dependency is never met
+  int tc_pairs = 1;                 // mixed trailing update on CTA pairs (tcgen05 .cta_group::2)
   int batched_band = 0;             // mixed: tile updates within this many tile diagonals stay FP64
   int batched_max_iter = 10;        // mixed: refinement steps per replicate at most
   // status and small results

@@ -282,6 +282,238 @@ __global__ void __launch_bounds__(kGemmThreads)
 }
 
 // ===========================================================================
+// T3 on CTA pairs: a 256 x 256 output tile per cluster of two CTAs.  Each CTA
+// stages its 128 rows of A and its 128 rows of B (TF32 halves); the leader's
+// tcgen05.mma.cta_group::2 (M = N = 256) reads both CTAs' stages, so every
+// staged byte feeds twice the products of the single-CTA kernel.  Each CTA's
+// TMEM receives its own 128 rows x 256 columns; both epilogues drain their own.
+// Barriers: full[] lives in the leader (both CTAs' TMA loads complete on it,
+// the leader expects both byte counts); empty[] and accfull[] in both (the
+// leader's commits multicast to the pair); accempty[] in the leader (every
+// epilogue warp of both CTAs arrives on it).
+// ===========================================================================
+namespace t3p {
+constexpr int KC = 32, STAGES = 3;
+constexpr int HALF_ROWS = 128;                  // rows of A (and of B) staged by one CTA
+constexpr int OP_BYTES = HALF_ROWS * KC * 4;    // 16 KB
+constexpr int STAGE_BYTES = 4 * OP_BYTES;       // A_hi, A_lo, B_hi, B_lo halves
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TILE = 256;
+constexpr uint32_t IDESC = idesc(kFmtTF32, TILE, TILE);
+constexpr int TMEM_COLS = 512;                  // 2 accumulator buffers x 256 columns
+constexpr int kSuper = kRasterSuper / 2;        // supertile edge in 256-tiles
+}  // namespace t3p
+
+// Pair tiles (units of 256): kEnumFull (bi = t / nt) or kEnumLowerOffBand (supertiles of the
+// lower triangle, g.nt tile rows, band in panel-wide tiles).
+__device__ __forceinline__ bool decode_pair_tile(const GemmArgs& g, long long t, int& bi, int& bj) {
+  if (g.enum_mode == kEnumFull) {
+    bi = (int)(t / g.nt);
+    bj = (int)(t % g.nt);
+    return true;
+  }
+  constexpr int S = t3p::kSuper;
+  const long long sidx = t / (S * S);
+  const int loc = (int)(t % (S * S));
+  int SI, SJ;
+  tile_tri_decode(sidx, SI, SJ);
+  bi = SI * S + loc / S;
+  bj = SJ * S + loc % S;
+  if (bi >= g.nt || bj > bi) return false;
+  const int per = g.panel / t3p::TILE;
+  return (bi / per - bj / per) > g.band;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
+    gemm_t3_pair_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                        const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                        const __grid_constant__ GemmArgs g) {
+  using namespace t3p;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accfull = empty + STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint64_t* drain = accempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = (rank == 0);
+  const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 2 * (kEpiThreads / 32));
+    }
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc_pair(tmem_slot, TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers are initialised before any remote arrival or copy
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int kchunks = g.K / KC;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    prefetch_tmap(&tA_hi);
+    prefetch_tmap(&tA_lo);
+    prefetch_tmap(&tB_hi);
+    prefetch_tmap(&tB_lo);
+    int stage = 0;
+    uint32_t phase = 0;
+    int last_par[STAGES];
+    for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
+    for (long long t = pair; t < g.ntiles && !*abort; t += npairs) {
+      int bi, bj;
+      if (!decode_pair_tile(g, t, bi, bj)) continue;
+      const int ya = g.a_row0 + bi * TILE + (int)rank * HALF_ROWS;
+      const int yb = g.b_row0 + bj * TILE + (int)rank * HALF_ROWS;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 51);
+          break;
+        }
+        uint8_t* sb = smem + stage * STAGE_BYTES;
+        if (leader) mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
+        const uint32_t fl = map_to_rank(smem_u32(&full[stage]), 0);
+        tma_load_2d_pair(sb, &tA_hi, fl, kc * KC, ya);
+        tma_load_2d_pair(sb + OP_BYTES, &tA_lo, fl, kc * KC, ya);
+        tma_load_2d_pair(sb + 2 * OP_BYTES, &tB_hi, fl, kc * KC, yb);
+        tma_load_2d_pair(sb + 3 * OP_BYTES, &tB_lo, fl, kc * KC, yb);
+        last_par[stage] = (int)phase;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (*abort && leader) {  // the leader's full barriers also count the peer's bytes
+      for (int s = 0; s < STAGES; ++s)
+        if (last_par[s] >= 0) {
+          volatile int never = 0;
+          mbar_wait(&full[s], (uint32_t)last_par[s], &never);
+        }
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader only) ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int it = 0;
+    for (long long t = pair; t < g.ntiles && !*abort; t += npairs) {
+      int bi, bj;
+      if (!decode_pair_tile(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accempty[b], ap ^ 1, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 52);
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + b * TILE;
+      bool ok = true;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(&full[stage], phase, abort)) {
+          *abort = 1;
+          record_timeout(g.st, 53);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
+        const uint64_t ahi = sdesc_sw128(sb), alo = sdesc_sw128(sb + OP_BYTES);
+        const uint64_t bhi = sdesc_sw128(sb + 2 * OP_BYTES), blo = sdesc_sw128(sb + 3 * OP_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < KC / 8; ++kk) {  // K = 8 per instruction: advance 32 bytes
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_tf32_pair(d, ahi + o, bhi + o, IDESC, (kc | kk) ? 1u : 0u);
+          mma_tf32_pair(d, ahi + o, blo + o, IDESC, 1u);
+          mma_tf32_pair(d, alo + o, bhi + o, IDESC, 1u);
+        }
+        mma_commit_pair(&empty[stage], (uint16_t)0x3);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit_pair(&accfull[b], (uint16_t)0x3);
+      ++it;
+    }
+    // every MMA issued has finished before the pair leaves (matters after a time-out)
+    mma_commit_pair(drain, (uint16_t)0x1);
+    volatile int never = 0;
+    mbar_wait(drain, 0, &never);
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs): own TMEM -> FP64 C ----------------
+    // warp w drains TMEM lanes 32*(w%4).. and the 128-column half (w-2)/4 of the 256 columns
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t accempty_l[2] = {map_to_rank(smem_u32(&accempty[0]), 0), map_to_rank(smem_u32(&accempty[1]), 0)};
+    int it = 0;
+    for (long long t = pair; t < g.ntiles && !*abort; t += npairs) {
+      int bi, bj;
+      if (!decode_pair_tile(g, t, bi, bj)) continue;
+      const int b = it & 1;
+      const uint32_t ap = (it >> 1) & 1;
+      if (!mbar_wait(&accfull[b], ap, abort)) {
+        *abort = 1;
+        record_timeout(g.st, 54);
+        break;
+      }
+      fence_after();
+      const int64_t row = g.c_row0 + (int64_t)bi * TILE + (int64_t)rank * HALF_ROWS + r;
+      const int64_t col0 = g.c_col0 + (int64_t)bj * TILE;
+      double* cp = g.C + row + col0 * g.ldc;
+#pragma unroll 1
+      for (int h2 = 0; h2 < 4; ++h2) {
+        const int cb = half * 128 + h2 * 32;
+        double cv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(cb + j) * g.ldc];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint32_t acc[16];
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * TILE + cb + c * 16, acc);
+          tmem_ld_wait();
+          if (h2 == 3 && c == 1) {
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(accempty_l[b]);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const double v = f32_bits_to_f64(acc[j]);
+            cp[(int64_t)(cb + c * 16 + j) * g.ldc] = g.store ? v : cv[c * 16 + j] - v;
+          }
+        }
+      }
+      ++it;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync();  // the leader's MMAs read this CTA's shared memory: both stay until both are done
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc_pair(tmem, TMEM_COLS);
+  }
+}
+
+// ===========================================================================
 // OZ kernel: tile 128 x 32, K chunks of 64 BF16 digits, S = 5 slices, 2 stages.
 // ===========================================================================
 namespace oz {
@@ -648,6 +880,24 @@ cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOpe
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
   const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
   gemm_t3_kernel<<<grid, kGemmThreads, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                                int max_ctas) {
+  if (g.ntiles <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm_t3_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3p::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int cap = num_sms();
+  if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
+  const long long pairs = g.ntiles < cap / 2 ? g.ntiles : cap / 2;
+  if (pairs < 1) return cudaErrorInvalidValue;
+  gemm_t3_pair_kernel<<<(unsigned)(2 * pairs), kGemmThreads, t3p::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,10 @@ cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOpe
                            int max_ctas = 0);
 cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
                            int max_ctas = 0);
+// T3 on CTA pairs, 256 x 256 tiles (kEnumFull with g.nt = n / 256, or kEnumLowerOffBand with
+// g.nt = tile rows of 256); no lower_mask.  Uses pairs of SMs (max_ctas rounded down to even).
+cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
+                                int max_ctas = 0);
 int tc_num_sms();
 
 }  // namespace exa

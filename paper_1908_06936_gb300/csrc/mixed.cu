@@ -209,10 +209,17 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
     g.c_row0 = g.c_col0 = r0 + NB;
     g.a_row0 = g.b_row0 = NB;
     const long long t128 = m2 / 128;
-    const long long ts = (t128 + kRasterSuper - 1) / kRasterSuper;  // supertile rows
     g.enum_mode = kEnumLowerOffBand;
-    g.nt = (int)t128;
-    g.ntiles = ts * (ts + 1) / 2 * kRasterSuper * kRasterSuper;
+    if (c->tc_pairs) {  // 256-tiles on CTA pairs (m2 is a multiple of the 512 panel)
+      const long long t256 = m2 / 256, sp2 = kRasterSuper / 2;
+      const long long ts = (t256 + sp2 - 1) / sp2;
+      g.nt = (int)t256;
+      g.ntiles = ts * (ts + 1) / 2 * sp2 * sp2;
+    } else {
+      const long long ts = (t128 + kRasterSuper - 1) / kRasterSuper;  // supertile rows
+      g.nt = (int)t128;
+      g.ntiles = ts * (ts + 1) / 2 * kRasterSuper * kRasterSuper;
+    }
     long long t3_tiles = 0;
     for (long long bi = 0; bi < t128; ++bi) {
       const long long lim = (long long)SUB * (bi / SUB - band);
@@ -221,7 +228,7 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
     if (t3_tiles > 0) {
       ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
                    16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m2 * NB, 1, s, true);
-      e = launch_gemm_t3(s, sp, sp, g, ctas);
+      e = c->tc_pairs ? launch_gemm_t3_pair(s, sp, sp, g, ctas) : launch_gemm_t3(s, sp, sp, g, ctas);
     }
     if (e == cudaSuccess) {
       const long long tr = m2 / NB;
@@ -476,6 +483,12 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
 
 using namespace exa;
 
+extern "C" exa_status exa_ctx_set_tc_pairs(exa_ctx* c, int on) {
+  if (!c) return EXA_ERR_ARG;
+  c->tc_pairs = on ? 1 : 0;
+  return EXA_OK;
+}
+
 extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k,
                                       const double* d_a, const double* d_b, double* d_c, int64_t ldc, int store) {
   if (!c) return EXA_ERR_ARG;
@@ -483,8 +496,9 @@ extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m,
   if (!d_a || !d_b || !d_c || m <= 0 || n <= 0 || k <= 0 || ldc < m)
     return set_err(c, EXA_ERR_ARG, "bad gemm arguments");
   const bool oz = (kind == EXA_GEMM_OZ);
-  if (kind != EXA_GEMM_T3 && kind != EXA_GEMM_OZ) return set_err(c, EXA_ERR_ARG, "unknown gemm kind");
-  if (m % 128 || k % 64 || k > kSplitMaxK || (oz ? (n % 32) : (n % 128)))
+  const bool pair = (kind == EXA_GEMM_T3_PAIR);
+  if (kind != EXA_GEMM_T3 && kind != EXA_GEMM_OZ && !pair) return set_err(c, EXA_ERR_ARG, "unknown gemm kind");
+  if (m % (pair ? 256 : 128) || k % 64 || k > kSplitMaxK || (oz ? (n % 32) : (n % (pair ? 256 : 128))))
     return set_err(c, EXA_ERR_ARG, "gemm shape m=%lld n=%lld k=%lld not supported", (long long)m, (long long)n,
                    (long long)k);
   exa_status st;
@@ -506,6 +520,10 @@ extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m,
     g.nt = (int)(n / 32);
     g.ntiles = (m / 128) * (n / 32);
     e = launch_gemm_oz(c->stream, c->sp_a, c->sp_b, g);
+  } else if (pair) {
+    g.nt = (int)(n / 256);
+    g.ntiles = (m / 256) * (n / 256);
+    e = launch_gemm_t3_pair(c->stream, c->sp_a, c->sp_b, g);
   } else {
     g.nt = (int)(n / 128);
     g.ntiles = (m / 128) * (n / 128);

@@ -91,3 +91,20 @@ def test_bad_shapes(ctx):
     b = torch.zeros(128 * 64, dtype=torch.float64, device="cuda")
     c = torch.zeros(128 * 128, dtype=torch.float64, device="cuda")
     assert exa.exa_gemm_update(ctx.handle, exa.EXA_GEMM_T3, 100, 128, 64, a, b, c, 128, 0) == exa.EXA_ERR_ARG
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 64), (512, 768, 256), (768, 256, 512), (1024, 1024, 512)])
+@pytest.mark.parametrize("store", [0, 1])
+def test_t3_pair_product(ctx, m, n, k, store):
+    # the CTA-pair kernel (256 x 256 tiles, tcgen05 .cta_group::2) computes the same
+    # three-product TF32 arithmetic: same bound, and the single-CTA kernel's result to FP32 rounding
+    import paper_1908_06936_gb300 as exa
+
+    A, B = operands(m, n, k, seed=3 * m + n + k, spread=2)
+    C0 = np.random.default_rng(3).standard_normal((m, n))
+    got = run(ctx, exa.EXA_GEMM_T3_PAIR, A, B, C0, store)
+    ref = A @ B.T if store else C0 - A @ B.T
+    bound = 2.0 ** -19 * (np.abs(A) @ np.abs(B).T) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+    single = run(ctx, exa.EXA_GEMM_T3, A, B, C0, store)
+    assert np.all(np.abs(got - single) <= 2.0 ** -22 * (np.abs(A) @ np.abs(B).T) + 1e-300)

@@ -147,3 +147,22 @@ def test_mixed_ill_conditioned_reports_nonconvergence_or_is_accurate(ctx):
         assert e.status == exa.EXA_ERR_IR_NOCONV
         return
     assert abs(got["loglik"] - ref["l"]) <= 1e-6 * abs(ref["l"])
+
+
+def test_mixed_pair_and_single_cta_updates_agree(ctx):
+    # the off-band trailing update on CTA pairs and on single CTAs accumulate the same
+    # products in the same order per tile: the log-likelihoods agree to rounding
+    import paper_1908_06936_gb300 as exa
+
+    theta = (1.0, 0.05, 1.0)
+    locs, Z = workload(72, seed=72, theta0=theta)
+    dl, dz = to_dev(locs), to_dev(Z)
+    exa.exa_ctx_set_tc_pairs(ctx.handle, 0)
+    try:
+        single = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+    finally:
+        exa.exa_ctx_set_tc_pairs(ctx.handle, 1)
+    pair = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+    assert abs(pair["loglik"] - single["loglik"]) <= 1e-12 * abs(single["loglik"])
+    ref = oracle.loglik(locs, Z, theta)["l"]
+    assert abs(pair["loglik"] - ref) <= 1e-6 * abs(ref)
