@@ -712,10 +712,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
 // Split kernel: FP64 rows -> T3 (tf32 hi/lo, row-major) and OZ digits.
 // One CTA per kSplitRows rows; K <= kSplitMaxK.  src element (r, k) at src[r*rs + k*cs].
 // ===========================================================================
-__device__ __forceinline__ float tf32_rn(float f) {
-  uint32_t b = __float_as_uint(f);
-  b += 0xFFFu + ((b >> 13) & 1u);
-  return __uint_as_float(b & 0xFFFFE000u);
+// TF32 rounding (11 significant bits, half away from zero in magnitude) of the
+// double with bit pattern D, as FP32 bits; |a| below the FP32 normal range -> 0.
+// Integer instructions only (FP64 instructions are the scarce resource here).
+__device__ __forceinline__ uint32_t tf32_bits_of(unsigned long long D, unsigned long long* rounded) {
+  const unsigned long long sign = D & 0x8000000000000000ull;
+  unsigned long long mag = (D & 0x7FFFFFFFFFFFFFFFull) + (1ull << 41);
+  mag &= ~((1ull << 42) - 1);
+  const int fe = (int)(mag >> 52) - 896;  // FP64 bias 1023 -> FP32 bias 127
+  if (fe <= 0) {
+    *rounded = sign;
+    return (uint32_t)(sign >> 32);
+  }
+  *rounded = sign | mag;
+  return (uint32_t)(sign >> 32) | ((uint32_t)fe << 23) | (uint32_t)((mag >> 29) & 0x7FFFFFu);
 }
 
 __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
@@ -726,16 +736,29 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
   const int r0 = blockIdx.x * kSplitRows;
   const int tid = threadIdx.x;
   const int ld = K + 1;
-  // coalesced along whichever source dimension is contiguous
-  if (cs == 1) {
-    for (int idx = tid; idx < kSplitRows * K; idx += blockDim.x) {
-      const int rr = idx / K, k = idx % K;
-      tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + k] : 0.0;
+  // coalesced along whichever source dimension is contiguous; 16 loads in flight per thread
+  constexpr int CH = 16;
+  const int total = kSplitRows * K;
+  for (int base = 0; base < total; base += CH * 256) {
+    double v[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = base + u * 256 + tid;
+      v[u] = 0.0;
+      if (idx < total) {
+        const int rr = (cs == 1) ? idx / K : idx % kSplitRows;
+        const int k = (cs == 1) ? idx % K : idx / kSplitRows;
+        if (r0 + rr < rows) v[u] = src[(int64_t)(r0 + rr) * rs + (int64_t)k * cs];
+      }
     }
-  } else {
-    for (int idx = tid; idx < kSplitRows * K; idx += blockDim.x) {
-      const int rr = idx % kSplitRows, k = idx / kSplitRows;
-      tile[rr * ld + k] = (r0 + rr < rows) ? src[(int64_t)(r0 + rr) * rs + (int64_t)k * cs] : 0.0;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = base + u * 256 + tid;
+      if (idx < total) {
+        const int rr = (cs == 1) ? idx / K : idx % kSplitRows;
+        const int k = (cs == 1) ? idx % K : idx / kSplitRows;
+        tile[rr * ld + k] = v[u];
+      }
     }
   }
   __syncthreads();
@@ -744,29 +767,47 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
     const int row = r0 + rr;
     if (row >= rows) break;
     const int64_t orow = (int64_t)(out_row0 + row);
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(tile[rr * ld + k]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) {
-      frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |a| 2^-e <= 1
+    // row maximum of |a| on the bit patterns (non-negative doubles order like their bits)
+    unsigned long long mxb = 0;
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(tile[rr * ld + k]) & 0x7FFFFFFFFFFFFFFFull;
+      mxb = b > mxb ? b : mxb;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, mxb, o);
+      mxb = ob > mxb ? ob : mxb;
+    }
+    // max = f 2^e with f in [0.5, 1): e = biased exponent - 1022 (0 for an all-zero row)
+    const int e = mxb ? (int)(mxb >> 52) - 1022 : 0;
     if (lane == 0 && ex) ex[orow] = e;
-    const double sc = ldexp(1.0, 35 - e);
     for (int k = lane; k < K; k += 32) {
       const double a = tile[rr * ld + k];
+      const unsigned long long D = (unsigned long long)__double_as_longlong(a);
       if (hi) {
-        const float h = tf32_rn((float)a);
-        const float l = tf32_rn((float)(a - (double)h));
-        hi[orow * K + k] = h;
-        lo[orow * K + k] = l;
+        unsigned long long hd, ld2;
+        const uint32_t h = tf32_bits_of(D, &hd);
+        const double rem = a - __longlong_as_double((long long)hd);  // exact: a's bits below the rounding point
+        const uint32_t l = tf32_bits_of((unsigned long long)__double_as_longlong(rem), &ld2);
+        hi[orow * K + k] = __uint_as_float(h);
+        lo[orow * K + k] = __uint_as_float(l);
       }
       if (dig) {
-        // N = round(a 2^(35-e)), |N| <= 2^35; balanced base-128 digits from the least
-        // significant end: d = ((N + 64) mod 128) - 64, N = (N - d) / 128.  The leading
-        // digit keeps the rest (|d_0| <= 128, |d_s| <= 64 otherwise); all exact in BF16.
-        long long N = llrint(a * sc);
+        // N = round(a 2^(35-e)) from the bits: a = M 2^(E-1075) with M the 53-bit significand,
+        // so a 2^(35-e) = M 2^-(1040+e-E); |a| < 2^e makes the shift >= 18 and |N| <= 2^35.
+        long long N = 0;
+        const int E = (int)((D >> 52) & 0x7FF);
+        if (E != 0) {
+          const unsigned long long M = (D & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const int sh = 1040 + e - E;
+          if (sh >= 64) N = 0;
+          else if (sh > 0) N = (long long)((M + (1ull << (sh - 1))) >> sh);
+          else N = (long long)(M << (-sh));
+          if (D >> 63) N = -N;
+        }
+        // balanced base-128 digits from the least significant end: d = ((N + 64) mod 128) - 64,
+        // N = (N - d) / 128.  The leading digit keeps the rest (|d_0| <= 128, |d_s| <= 64
+        // otherwise); all are exact in BF16.
         short d[kOzSlices];
 #pragma unroll
         for (int s2 = kOzSlices - 1; s2 >= 1; --s2) {
