@@ -204,6 +204,17 @@ exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t 
  * (128 x 128 tiles).  Both compute the same products.                       */
 exa_status exa_ctx_set_tc_pairs(exa_ctx* ctx, int on);
 
+/* Far tiles of the mixed factorisation (the MP variant's precision map, taken
+ * per tile from the data): an off-band 256 x 256 trailing-update tile whose two
+ * operand blocks have largest magnitudes 2^eA and 2^eB with eA + eB at least
+ * `bits` binades below sigma^2 is computed with the single TF32 product hi*hi
+ * (relative error ~2^-10, absolute error below that of the three-product form
+ * on entries of size sigma^2 when bits >= 12).  bits = 0 turns it off; the
+ * default is 16 (at n = 90,000, theta = (1, 0.03, 1): |dl|/|l| vs FP64 5.1e-8
+ * with 16 or with the feature off, 1.2e-7 with 12, 5.7e-6 with 8).
+ * Ignored when exa_ctx_set_tc_pairs is off.                                 */
+exa_status exa_ctx_set_far_tile_margin(exa_ctx* ctx, int bits);
+
 /* Kernel accounting.  Launch counts and the algorithmic flops / bytes of every
  * kernel class are always accumulated; with profiling enabled each launch is
  * also bracketed by CUDA events on the context stream (adds ~2 us per launch). */

@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
                 "exa_ctx_set_batched_mixed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
                 "exa_ctx_set_tc_pairs": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_ctx_set_far_tile_margin": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_batched_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                                         ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P,
                                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -314,6 +315,10 @@ def exa_ctx_set_batched_mixed(ctx: int, band: int = 0, max_iter: int = 0) -> int
 
 def exa_ctx_set_tc_pairs(ctx: int, on: int) -> int:
     return lib().exa_ctx_set_tc_pairs(_P(ctx), int(on))
+
+
+def exa_ctx_set_far_tile_margin(ctx: int, bits: int) -> int:
+    return lib().exa_ctx_set_far_tile_margin(_P(ctx), int(bits))
 
 
 def exa_loglik_noalloc(cuda_stream: int, locs, z, theta, n: int, loglik: ctypes.c_double) -> int:

@@ -65,6 +65,7 @@ struct exa_ctx {
   long long batched_spin = 2000000000LL;  // bound of one dependency wait (SM cycles)
   int batched_stall = 0;            // test hook: add a task whose dependency is never met
   int tc_pairs = 1;                 // mixed trailing update on CTA pairs (tcgen05 .cta_group::2)
+  int far_tile_margin = 16;         // single-product far tiles below sigma^2 by this many binades (0: off)
   int batched_band = 0;             // mixed: tile updates within this many tile diagonals stay FP64
   int batched_max_iter = 10;        // mixed: refinement steps per replicate at most
   // status and small results
@@ -87,7 +88,7 @@ exa_status check_theta(exa_ctx* c, const double theta[3]);
 exa_status reset_status(exa_ctx* c);
 exa_status read_status(exa_ctx* c);
 exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb);
-exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band);
+exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band, int far_thr);
 // Generate Sigma into `sigma_keep` (or straight into the factor buffer) and factor it in mixed precision.
 exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, const double theta[3], int64_t npad,
                                  exa_prec prec, double* sigma_keep, int* band_used);

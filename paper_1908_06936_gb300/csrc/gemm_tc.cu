@@ -23,6 +23,8 @@
 #include <cuda.h>
 #include <math.h>
 
+#include <climits>
+
 #include "ctx.cuh"
 #include "gemm_tc.cuh"
 #include "tc_common.cuh"
@@ -324,6 +326,16 @@ __device__ __forceinline__ bool decode_pair_tile(const GemmArgs& g, long long t,
   return (bi / per - bj / per) > g.band;
 }
 
+// Far tiles: when the largest |entries| of the two operand blocks are at most 2^eA and 2^eB
+// with eA + eB <= far_thr, the single product hi * hi (relative error ~2^-10 per term) has
+// an absolute error no larger than the three-product form makes on blocks of size 1; the
+// caller sets far_thr from the scale of Sigma.  Producer and MMA issuer decide alike.
+__device__ __forceinline__ bool far_tile(const GemmArgs& g, int bi, int bj) {
+  if (g.far_thr == INT_MIN || !g.ea_blk || !g.eb_blk) return false;
+  const int ea = g.ea_blk[g.a_row0 / t3p::TILE + bi], eb = g.eb_blk[g.b_row0 / t3p::TILE + bj];
+  return (long long)ea + (long long)eb <= (long long)g.far_thr;
+}
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     gemm_t3_pair_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                         const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
@@ -379,6 +391,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       if (!decode_pair_tile(g, t, bi, bj)) continue;
       const int ya = g.a_row0 + bi * TILE + (int)rank * HALF_ROWS;
       const int yb = g.b_row0 + bj * TILE + (int)rank * HALF_ROWS;
+      const bool one = far_tile(g, bi, bj);
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
           *abort = 1;
@@ -386,12 +399,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
           break;
         }
         uint8_t* sb = smem + stage * STAGE_BYTES;
-        if (leader) mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
+        if (leader) mbar_expect_tx(&full[stage], (one ? 1 : 2) * STAGE_BYTES);
         const uint32_t fl = map_to_rank(smem_u32(&full[stage]), 0);
         tma_load_2d_pair(sb, &tA_hi, fl, kc * KC, ya);
-        tma_load_2d_pair(sb + OP_BYTES, &tA_lo, fl, kc * KC, ya);
+        if (!one) tma_load_2d_pair(sb + OP_BYTES, &tA_lo, fl, kc * KC, ya);
         tma_load_2d_pair(sb + 2 * OP_BYTES, &tB_hi, fl, kc * KC, yb);
-        tma_load_2d_pair(sb + 3 * OP_BYTES, &tB_lo, fl, kc * KC, yb);
+        if (!one) tma_load_2d_pair(sb + 3 * OP_BYTES, &tB_lo, fl, kc * KC, yb);
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -423,6 +436,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       }
       fence_after();
       const uint32_t d = tmem + b * TILE;
+      const bool one = far_tile(g, bi, bj);
       bool ok = true;
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&full[stage], phase, abort)) {
@@ -439,8 +453,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
         for (int kk = 0; kk < KC / 8; ++kk) {  // K = 8 per instruction: advance 32 bytes
           const uint64_t o = (uint64_t)(kk * 2);
           mma_tf32_pair(d, ahi + o, bhi + o, IDESC, (kc | kk) ? 1u : 0u);
-          mma_tf32_pair(d, ahi + o, blo + o, IDESC, 1u);
-          mma_tf32_pair(d, alo + o, bhi + o, IDESC, 1u);
+          if (!one) {
+            mma_tf32_pair(d, ahi + o, blo + o, IDESC, 1u);
+            mma_tf32_pair(d, alo + o, bhi + o, IDESC, 1u);
+          }
         }
         mma_commit_pair(&empty[stage], (uint16_t)0x3);
         if (++stage == STAGES) {
@@ -827,6 +843,23 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
   }
 }
 
+// Per 256-row block maximum of the row exponents (rows past the end count as -infinity).
+__global__ void __launch_bounds__(256) row_exp_blockmax_kernel(const int* __restrict__ ex, int64_t rows,
+                                                               int* __restrict__ exb) {
+  const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  int v = r < rows ? ex[r] : INT_MIN;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ int w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = w[0];
+    for (int i = 1; i < 8; ++i) m = max(m, w[i]);
+    exb[blockIdx.x] = m;
+  }
+}
+
 // ===========================================================================
 // host side
 // ===========================================================================
@@ -921,6 +954,12 @@ cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOpe
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
   const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
   gemm_t3_kernel<<<grid, kGemmThreads, t3::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_exp_blockmax(cudaStream_t s, SplitOperand& op, int64_t rows) {
+  if (!op.ex || !op.exb || rows <= 0) return cudaSuccess;
+  row_exp_blockmax_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(op.ex, rows, op.exb);
   return cudaGetLastError();
 }
 

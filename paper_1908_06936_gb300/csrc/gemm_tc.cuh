@@ -37,6 +37,11 @@ struct GemmArgs {
   int lower_mask;             // skip entries above the diagonal
   const int* ea;              // OZ: per-row power-of-two exponents of A (set by the launcher)
   const int* eb;              // OZ: per-row exponents of B
+  // T3 on CTA pairs: with far_thr set (> INT_MIN), a 256 x 256 tile whose operand blocks have
+  // maximum exponents eA + eB <= far_thr takes the single hi * hi product (see the kernel)
+  const int* ea_blk;          // per 256-row block maximum exponent of A
+  const int* eb_blk;          // per 256-row block maximum exponent of B
+  int far_thr;
   DevStatus* st;
 };
 
@@ -49,12 +54,15 @@ struct SplitOperand {
   float* lo = nullptr;
   void* dig = nullptr;
   int* ex = nullptr;
+  int* exb = nullptr;         // per 256-row block maximum of ex
   CUtensorMap t_hi, t_lo;     // boxes 32 x 128
   OzMaps oz_a;                // boxes 64 x 128 (A role)
   OzMaps oz_b;                // boxes 64 x 32  (B role)
 };
 
 cudaError_t make_split_maps(SplitOperand& op);
+// exb[b] = max(ex[256 b .. 256 b + 255]) over the first `rows` rows
+cudaError_t launch_row_exp_blockmax(cudaStream_t s, SplitOperand& op, int64_t rows);
 // rows [0, rows) of src (element (r, k) at src[r*rs + k*cs]) -> operand rows [out_row0, ...)
 cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int64_t cs, int rows, int K,
                               SplitOperand& op, int out_row0);

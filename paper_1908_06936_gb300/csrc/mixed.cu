@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <climits>
+
 #include "ctx.cuh"
 #include "gemm_tc.cuh"
 #include "util.cuh"
@@ -22,7 +24,8 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
   const size_t t3_bytes = t3 ? (size_t)rows * K * 4 : 0;
   const size_t dig_bytes = oz ? (size_t)kOzSlices * rows * K * 2 : 0;
   const size_t ex_bytes = oz ? (size_t)round_up(rows, 64) * 4 : 0;
-  const size_t total = 2 * t3_bytes + dig_bytes + ex_bytes + 1024;
+  const size_t exb_bytes = oz ? (size_t)round_up((rows + 255) / 256, 64) * 4 : 0;
+  const size_t total = 2 * t3_bytes + dig_bytes + ex_bytes + exb_bytes + 1024;
   void* old = buf.p;
   exa_status st = ensure(c, buf, total, "split operands");
   if (st != EXA_OK) return st;
@@ -36,6 +39,7 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
   op.lo = t3 ? (float*)(base + t3_bytes) : nullptr;
   op.dig = oz ? (void*)(base + 2 * t3_bytes) : nullptr;
   op.ex = oz ? (int*)(base + 2 * t3_bytes + dig_bytes) : nullptr;
+  op.exb = oz ? (int*)(base + 2 * t3_bytes + dig_bytes + ex_bytes) : nullptr;
   cudaError_t e = make_split_maps(op);
   if (e != cudaSuccess) {
     op.rows = 0;
@@ -60,6 +64,7 @@ struct MixStep {
   double* a;
   int64_t ld, npad;
   int band, T;
+  int far_thr;  // single-product far tiles when eA + eB <= far_thr (INT_MIN: never)
 };
 
 // FP64 diagonal block k, its inverse, the panel splits and the tensor-core TRSM
@@ -152,8 +157,9 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
     e = launch_gemm_t3(s, sp, c->sp_b, g, ctas);
   }
   if (e == cudaSuccess) {
-    ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)m * NB, 1, s, true);
+    ProfScope ps(c, PK_SPLIT, 0.0, 26.0 * (double)m * NB, 2, s, true);
     e = launch_split_rows(s, panel_src, 1, ld, (int)m, NB, sp, 0);
+    if (e == cudaSuccess) e = launch_row_exp_blockmax(s, sp, m);
   }
   if (e != cudaSuccess) return cuda_err(c, e, "panel trsm launch");
   return EXA_OK;
@@ -228,7 +234,15 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
     if (t3_tiles > 0) {
       ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
                    16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m2 * NB, 1, s, true);
-      e = c->tc_pairs ? launch_gemm_t3_pair(s, sp, sp, g, ctas) : launch_gemm_t3(s, sp, sp, g, ctas);
+      if (c->tc_pairs) {
+        g.ea_blk = g.eb_blk = sp.exb;
+        g.far_thr = M.far_thr;
+        e = launch_gemm_t3_pair(s, sp, sp, g, ctas);
+        g.ea_blk = g.eb_blk = nullptr;
+        g.far_thr = INT_MIN;
+      } else {
+        e = launch_gemm_t3(s, sp, sp, g, ctas);
+      }
     }
     if (e == cudaSuccess) {
       const long long tr = m2 / NB;
@@ -255,7 +269,7 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
 // SMs), the side stream factors diagonal block k+1, inverts it and runs the
 // TRSM of panel k+1 on the reserved SMs.  Panel splits alternate between two
 // buffers so the side stream never overwrites operands still in use.
-exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band) {
+exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band, int far_thr) {
   const int NB = kMixNB, nb = kMixSub;
   const int T = (int)(npad / NB);
   const int T128 = (int)(npad / nb);
@@ -278,7 +292,7 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
       return set_err(c, EXA_ERR_CUDA, "look-ahead stream creation failed");
     }
   }
-  MixStep M{c, a, ld, npad, band, T};
+  MixStep M{c, a, ld, npad, band, T, far_thr};
   cudaStream_t ms = c->stream, ss = c->side;
   const int sms = tc_num_sms();
   const int side_ctas = c->lookahead_sms > 0 ? c->lookahead_sms : kLookaheadSMs;
@@ -361,7 +375,12 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   } else if (band < 0) {
     band = T;
   }
-  st = factor_mixed(c, A, npad, npad, prec, band);
+  // far tiles: operand blocks bounded by 2^eA and 2^eB with eA + eB at least far_tile_margin
+  // below the exponent of sigma^2 (the largest |Sigma_ij|) take one TF32 product
+  int es = 0;
+  frexp(theta[0], &es);
+  const int far_thr = c->far_tile_margin > 0 ? es - c->far_tile_margin : INT_MIN;
+  st = factor_mixed(c, A, npad, npad, prec, band, far_thr);
   if (st != EXA_OK) return st;
   st = read_status(c);
   if (st == EXA_ERR_NOT_SPD && band < T && sigma_keep) {
@@ -370,7 +389,7 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
     e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refactor copy");
     band = T;
-    st = factor_mixed(c, A, npad, npad, prec, band);
+    st = factor_mixed(c, A, npad, npad, prec, band, INT_MIN);
     if (st == EXA_OK) st = read_status(c);
   }
   if (band_used) *band_used = band;
@@ -482,6 +501,12 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
 }  // namespace exa
 
 using namespace exa;
+
+extern "C" exa_status exa_ctx_set_far_tile_margin(exa_ctx* c, int bits) {
+  if (!c || bits < 0) return c ? set_err(c, EXA_ERR_ARG, "far-tile margin must be >= 0") : EXA_ERR_ARG;
+  c->far_tile_margin = bits;
+  return EXA_OK;
+}
 
 extern "C" exa_status exa_ctx_set_tc_pairs(exa_ctx* c, int on) {
   if (!c) return EXA_ERR_ARG;

@@ -157,12 +157,38 @@ def test_mixed_pair_and_single_cta_updates_agree(ctx):
     theta = (1.0, 0.05, 1.0)
     locs, Z = workload(72, seed=72, theta0=theta)
     dl, dz = to_dev(locs), to_dev(Z)
+    exa.exa_ctx_set_far_tile_margin(ctx.handle, 0)  # every off-band tile with three products
     exa.exa_ctx_set_tc_pairs(ctx.handle, 0)
     try:
         single = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+        exa.exa_ctx_set_tc_pairs(ctx.handle, 1)
+        pair = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
     finally:
         exa.exa_ctx_set_tc_pairs(ctx.handle, 1)
-    pair = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+        exa.exa_ctx_set_far_tile_margin(ctx.handle, 16)
     assert abs(pair["loglik"] - single["loglik"]) <= 1e-12 * abs(single["loglik"])
     ref = oracle.loglik(locs, Z, theta)["l"]
     assert abs(pair["loglik"] - ref) <= 1e-6 * abs(ref)
+
+
+def test_far_tiles_single_product_keeps_accuracy(ctx):
+    # with a short correlation length most of the trailing matrix is far from the diagonal and its
+    # panel blocks are tiny: those tiles take one TF32 product.  The result must stay within the
+    # mixed bound of the FP64 evaluation and close to the all-three-product result.
+    import paper_1908_06936_gb300 as exa
+
+    theta = (1.0, 0.03, 1.0)
+    m = 100
+    locs = synth.jittered_grid(m, 11)
+    z = synth.normals(m * m, 11)
+    dl, dz = to_dev(locs), to_dev(z)
+    l64 = ctx.loglik(dl, dz, theta, exa.EXA_FP64)
+    far = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)["loglik"]
+    exa.exa_ctx_set_far_tile_margin(ctx.handle, 0)
+    try:
+        three = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)["loglik"]
+    finally:
+        exa.exa_ctx_set_far_tile_margin(ctx.handle, 16)
+    print("far %.3e three %.3e" % (abs(far - l64) / abs(l64), abs(three - l64) / abs(l64)))
+    assert abs(far - l64) <= 1e-6 * abs(l64)
+    assert abs(far - three) <= 1e-7 * abs(l64)
