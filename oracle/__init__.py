@@ -64,6 +64,7 @@ def _load():
                 "oracle_loglik_grad": (_I64, [_I64, _PD, _PD, _PD, _PD, _PD]),
                 "oracle_simulate": (_I64, [_I64, _PD, _PD, _PD, _PD]),
                 "oracle_factor": (_I64, [_I64, _PD, _PD, _PD]),
+                "oracle_predict": (_I64, [_I64, _PD, _PD, _PD, _I64, _PD, _PD, _PD]),
                 "oracle_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -186,3 +187,18 @@ def simulate(locs, theta, eps) -> np.ndarray:
     if info != 0:
         raise ValueError("Sigma(theta) is not positive definite (pivot %d)" % (info - 1))
     return Z
+
+
+def predict(locs, Z, theta, new_locs) -> tuple[np.ndarray, np.ndarray]:
+    """Kriging at new locations: (mean, variance), zero mean (Section IV's exact_predict)."""
+    locs = _f64(locs).reshape(-1, 2)
+    new_locs = _f64(new_locs).reshape(-1, 2)
+    Z = _f64(Z)
+    th = _f64(theta)
+    m = new_locs.shape[0]
+    mean = np.empty(m)
+    var = np.empty(m)
+    info = int(_load().oracle_predict(locs.shape[0], _p(locs), _p(Z), _p(th), m, _p(new_locs), _p(mean), _p(var)))
+    if info != 0:
+        raise ValueError("Sigma(theta) is not positive definite (pivot %d)" % (info - 1))
+    return mean, var

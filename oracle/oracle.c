@@ -386,3 +386,55 @@ int64_t oracle_factor(int64_t n, const double* locs, const double theta[3], doub
     for (int64_t j = i + 1; j < n; ++j) L[i * n + j] = 0.0;
   return info;
 }
+
+/* Spatial prediction (kriging, the conditional expectation the paper's
+ * exact_predict computes for the sea-surface-temperature tutorial of Section IV)
+ * at m new locations from n observed ones, zero mean:
+ *   mean_i = c_i^T Sigma^-1 Z,   var_i = sigma^2 - c_i^T Sigma^-1 c_i,
+ *   c_i = (Sigma(new_i, obs_j))_j  (Eq. 3 at the cross distances).
+ * Through the Cholesky factor: a = L^-T L^-1 Z, mean_i = c_i^T a;
+ * w_i = L^-1 c_i, var_i = sigma^2 - w_i^T w_i.
+ * Returns 0, or the not-positive-definite pivot + 1 (outputs NaN).          */
+int64_t oracle_predict(int64_t n, const double* locs, const double* Z, const double theta[3], int64_t m,
+                       const double* new_locs, double* mean, double* var) {
+  double* A = (double*)malloc((size_t)n * (size_t)n * sizeof(double));
+  double* y = (double*)malloc((size_t)n * sizeof(double));
+  double* a = (double*)malloc((size_t)n * sizeof(double));
+  if (!A || !y || !a) {
+    free(A);
+    free(y);
+    free(a);
+    return -1;
+  }
+  oracle_covariance(n, locs, theta, A);
+  const int64_t info = oracle_cholesky(n, A);
+  if (info != 0) {
+    for (int64_t i = 0; i < m; ++i) mean[i] = var[i] = NAN;
+  } else {
+    oracle_forward_solve(n, A, Z, y);
+    oracle_backward_solve(n, A, y, a);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < m; ++i) {
+      double* c = (double*)malloc((size_t)n * sizeof(double));
+      double* w = (double*)malloc((size_t)n * sizeof(double));
+      for (int64_t j = 0; j < n; ++j) {
+        const double dx = new_locs[2 * i] - locs[2 * j];
+        const double dy = new_locs[2 * i + 1] - locs[2 * j + 1];
+        c[j] = oracle_matern(theta, sqrt(dx * dx + dy * dy));
+      }
+      double mu = 0.0;
+      for (int64_t j = 0; j < n; ++j) mu += c[j] * a[j];
+      oracle_forward_solve(n, A, c, w);
+      double ww = 0.0;
+      for (int64_t j = 0; j < n; ++j) ww += w[j] * w[j];
+      mean[i] = mu;
+      var[i] = theta[0] - ww;
+      free(c);
+      free(w);
+    }
+  }
+  free(A);
+  free(y);
+  free(a);
+  return info;
+}
