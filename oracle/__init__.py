@@ -65,6 +65,7 @@ def _load():
                 "oracle_simulate": (_I64, [_I64, _PD, _PD, _PD, _PD]),
                 "oracle_factor": (_I64, [_I64, _PD, _PD, _PD]),
                 "oracle_predict": (_I64, [_I64, _PD, _PD, _PD, _I64, _PD, _PD, _PD]),
+                "oracle_fisher": (_I64, [_I64, _PD, _PD, _PD]),
                 "oracle_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -202,3 +203,14 @@ def predict(locs, Z, theta, new_locs) -> tuple[np.ndarray, np.ndarray]:
     if info != 0:
         raise ValueError("Sigma(theta) is not positive definite (pivot %d)" % (info - 1))
     return mean, var
+
+
+def fisher(locs, theta) -> np.ndarray:
+    """Fisher information I_kl = 1/2 tr(Sigma^-1 D_k Sigma^-1 D_l), 3 x 3 (exact_fisher)."""
+    locs = _f64(locs).reshape(-1, 2)
+    th = _f64(theta)
+    out = np.empty(9)
+    info = int(_load().oracle_fisher(locs.shape[0], _p(locs), _p(th), _p(out)))
+    if info != 0:
+        raise ValueError("Sigma(theta) is not positive definite (pivot %d)" % (info - 1))
+    return out.reshape(3, 3)

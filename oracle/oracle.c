@@ -438,3 +438,80 @@ int64_t oracle_predict(int64_t n, const double* locs, const double* Z, const dou
   free(a);
   return info;
 }
+
+/* Fisher information of theta = (sigma^2, beta, nu) for the zero-mean Gaussian
+ * model (the paper's exact_fisher, listed with the package's functions in its
+ * Appendix):  I_kl = 1/2 tr(Sigma^-1 D_k Sigma^-1 D_l),  D_k = dSigma/dtheta_k.
+ * Sigma^-1 = X^T X with X = L^-1; M_k = Sigma^-1 D_k; I_kl = 1/2 sum_ij (M_k)_ij (M_l)_ji.
+ * out: 3 x 3 row-major.  Returns 0, or the not-positive-definite pivot + 1 (NaN). */
+int64_t oracle_fisher(int64_t n, const double* locs, const double theta[3], double out[9]) {
+  const size_t nn = (size_t)n * (size_t)n;
+  double* A = (double*)malloc(nn * sizeof(double));
+  double* X = (double*)calloc(nn, sizeof(double));
+  double* Si = (double*)calloc(nn, sizeof(double));
+  double* D = (double*)malloc(3 * nn * sizeof(double));
+  double* M = (double*)malloc(3 * nn * sizeof(double));
+  int64_t info = -1;
+  for (int c = 0; c < 9; ++c) out[c] = NAN;
+  if (!A || !X || !Si || !D || !M) goto done;
+  oracle_covariance(n, locs, theta, A);
+  info = oracle_cholesky(n, A);
+  if (info != 0) goto done;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = c; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = c; k < i; ++k) t -= A[i * n + k] * X[k * n + c];
+      X[i * n + c] = t / A[i * n + i];
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j <= i; ++j) {
+      double t = 0.0;
+      for (int64_t k = i; k < n; ++k) t += X[k * n + i] * X[k * n + j];
+      Si[i * n + j] = t;
+      Si[j * n + i] = t;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j <= i; ++j) {
+      double g[3];
+      oracle_matern_grad(theta, oracle_dist(locs, i, j), g);
+      for (int c = 0; c < 3; ++c) {
+        D[c * nn + i * n + j] = g[c];
+        D[c * nn + j * n + i] = g[c];
+      }
+    }
+  }
+  /* M_k = Sigma^-1 D_k */
+  for (int c = 0; c < 3; ++c) {
+    const double* Dc = D + c * nn;
+    double* Mc = M + c * nn;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = 0; j < n; ++j) {
+        double t = 0.0;
+        for (int64_t k = 0; k < n; ++k) t += Si[i * n + k] * Dc[k * n + j];
+        Mc[i * n + j] = t;
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      const double* Mk = M + k * nn;
+      const double* Ml = M + l * nn;
+      double t = 0.0;
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) t += Mk[i * n + j] * Ml[j * n + i];
+      out[k * 3 + l] = 0.5 * t;
+    }
+done:
+  free(A);
+  free(X);
+  free(Si);
+  free(D);
+  free(M);
+  return info;
+}
