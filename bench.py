@@ -252,6 +252,71 @@ def batched_leg(args, ctx) -> dict:
     return leg
 
 
+def configs_leg(args, ctx) -> dict:
+    """The smaller configurations: n = 1,600 (40x40 grid, theta0 = (1, 0.1, 0.5) and 10 seeded
+    perturbations; FP64 and mixed evaluations/s with the phase split, the oracle timed on the host
+    and checked at theta0) and n = 22,500 (150x150 grid, theta = (1.5, 0.2, 1.5): log-likelihood +
+    gradient evaluations/s in FP64)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+
+    out = {}
+    th0 = (1.0, 0.1, 0.5)
+    locs = synth.jittered_grid(40, 0)
+    eps = synth.normals(1600, 0)
+    z = oracle.simulate(locs, th0, eps)
+    dl, dz = torch.as_tensor(locs, device="cuda"), torch.as_tensor(z, device="cuda")
+    thetas = [th0] + [tuple(t) for t in synth.theta_perturbations(th0, 10, seed=2)]
+    for name, prec in (("fp64", exa.EXA_FP64), ("mixed", exa.EXA_MIXED_TF32X3)):
+        for t in thetas[:3]:
+            ctx.loglik_ex(dl, dz, t, prec)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = [ctx.loglik_ex(dl, dz, t, prec) for t in thetas]
+        dt = time.perf_counter() - t0
+        out["n1600_" + name] = {"evals_per_s": len(thetas) / dt,
+                                "ms_gen": float(np.mean([r["ms_gen"] for r in res])),
+                                "ms_chol": float(np.mean([r["ms_chol"] for r in res])),
+                                "ms_solve": float(np.mean([r["ms_solve"] for r in res])),
+                                "loglik_theta0": res[0]["loglik"]}
+    t0 = time.perf_counter()
+    ref = oracle.loglik(locs, z, th0)["l"]
+    out["n1600_oracle"] = {"seconds_per_eval": time.perf_counter() - t0, "threads": os.cpu_count()}
+    for name in ("fp64", "mixed"):
+        out["n1600_" + name]["rel_dl_vs_oracle"] = abs(out["n1600_" + name]["loglik_theta0"] - ref) / abs(ref)
+    thg = (1.5, 0.2, 1.5)
+    locs = synth.jittered_grid(150, 4)
+    dl = torch.as_tensor(locs, device="cuda")
+    dz = ctx.simulate(dl, torch.as_tensor(synth.normals(22500, 4), device="cuda"), thg, exa.EXA_FP64)
+    ctx.loglik_grad(dl, dz, thg)  # warm-up (allocates the second n^2 buffer)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l, g = ctx.loglik_grad(dl, dz, thg)
+    dt = time.perf_counter() - t0
+    out["n22500_gradient_fp64"] = {"evals_per_s": 1.0 / dt, "seconds": dt, "loglik": l, "grad": list(map(float, g))}
+    # kriging at 2,048 new locations from the same 22,500 observations (means and variances)
+    new = torch.as_tensor(synth.uniform_square(2048, 5), device="cuda")
+    ctx.predict(dl, dz, thg, new)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mean, var = ctx.predict(dl, dz, thg, new)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["n22500_predict_2048"] = {"seconds": dt, "predictions_per_s": 2048 / dt,
+                                  "var_min": float(var.min().item()), "var_max": float(var.max().item())}
+    # Fisher information at the n = 1,600 configuration
+    locs = torch.as_tensor(synth.jittered_grid(40, 0), device="cuda")
+    ctx.fisher(locs, th0)
+    t0 = time.perf_counter()
+    F = ctx.fisher(locs, th0)
+    out["n1600_fisher"] = {"seconds": time.perf_counter() - t0, "fisher": F.tolist()}
+    return out
+
+
 def batched_mle_leg(args) -> dict:
     """theta-hat distribution of the 256 config-5 replicates: every replicate fitted by its
     own bounded Nelder-Mead in log(theta), all advanced in lockstep by one CUDA-graph replay
@@ -382,6 +447,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         pk = peaks()
         rl = roofline(stats, pk)
         batched = batched_leg(args, ctx) if args.batched_steps > 0 else None
+        configs = configs_leg(args, ctx) if args.configs else None
         batched_mle = batched_mle_leg(args) if args.batched_mle_evals > 0 else None
         # CPU oracle baseline on a bounded sample of the same field
         n_s = args.cpu_sample
@@ -403,6 +469,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "speedup_mixed_vs_fp64": (fp64["ms_per_eval"] / (ms_max / args.steps)) if fp64 else None,
             "roofline": rl,
             "batched": batched,
+            "configs": configs,
             "batched_mle": batched_mle,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()} for st in stats],
             "cpu_baseline": cpu_baseline_entry(n, n_s, cs["seconds"], cs["threads"]),
@@ -450,6 +517,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 evaluations at the same n (0 to skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="graph replays of the 256-replicate mixed batch (0 skips the batched leg)")
+    ap.add_argument("--configs", type=int, default=1, help="also time the n=1,600 and n=22,500 configurations (0 skips)")
     ap.add_argument("--batched-mle-evals", type=int, default=0,
                     help="fit theta for the 256 batched replicates with this many evaluations each (0 skips)")
     ap.add_argument("--batched-fp64-steps", type=int, default=1, help="timed FP64 runs of the same batch")

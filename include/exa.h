@@ -183,6 +183,32 @@ exa_status exa_loglik_batched(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, co
                               const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
                               int32_t* d_status);
 
+/* Spatial prediction (kriging) at m new locations from n observations, FP64:
+ * the conditional mean and variance of the zero-mean field (the prediction of
+ * the sea-surface-temperature tutorial, Section IV):
+ *   mean_i = c_i^T Sigma^-1 z,  var_i = sigma^2 - c_i^T Sigma^-1 c_i,
+ *   c_i = (Sigma(new_i, obs_j))_j from Eq. 3.
+ *   d_locs      DEVICE n x 2 observed locations; d_z DEVICE n observations.
+ *   d_new_locs  DEVICE m x 2 new locations (m >= 0).
+ *   d_mean      DEVICE output, m values.
+ *   d_var       DEVICE output, m values, or NULL to skip the variances (they cost
+ *               n^2 m FP64 flops; the means cost n m covariance evaluations).
+ * Uses the context's factor workspace (like exa_loglik) and synchronises the
+ * context stream.  EXA_ERR_NOT_SPD if Sigma(theta) of the observations is not
+ * positive definite.                                                          */
+exa_status exa_predict(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
+                       const double* d_new_locs, int64_t m, double* d_mean, double* d_var);
+
+/* Fisher information of theta = (sigma^2, beta, nu) at the observed locations, FP64
+ * (the package's exact_fisher):  I_kl = 1/2 tr(Sigma^-1 D_k Sigma^-1 D_l),
+ * D_k = dSigma/dtheta_k (Eq. 3 differentiated as for exa_loglik_grad).
+ *   fisher   HOST output, 3 x 3 row-major (symmetric).
+ * Holds five n_pad^2 FP64 buffers (the matrix, Sigma^-1 and the three products
+ * Sigma^-1 D_k, n_pad = n rounded up to 128) and costs ~7 n^3 FP64 flops.
+ * Synchronises the context stream; EXA_ERR_NOT_SPD if Sigma(theta) is not
+ * positive definite.                                                          */
+exa_status exa_fisher(exa_ctx* ctx, const double* d_locs, const double theta[3], int64_t n, double fisher[9]);
+
 /* Products of step a2 on their own (component check of the tensor-core
  * contractions used by the mixed-precision factorisation):
  *   C = A B^T (store != 0)  or  C -= A B^T (store == 0)

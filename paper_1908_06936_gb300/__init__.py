@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_predict", "exa_fisher",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
                 "exa_ctx_set_batched_mixed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
                 "exa_ctx_set_tc_pairs": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_predict": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _P, _I64, _P, _P]),
+                "exa_fisher": (ctypes.c_int, [_P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_far_tile_margin": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_batched_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                                         ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P,
@@ -188,6 +190,22 @@ class Context:
         l = ctypes.c_double()
         self.check(exa_loglik_grad(self.handle, locs, z, theta, locs.shape[0], prec, l, g))
         return l.value, np.array(g[:])
+
+    def predict(self, locs, z, theta, new_locs, variance=True):
+        """Kriging at new locations: (mean, variance or None) as device tensors."""
+        import torch
+
+        m = new_locs.shape[0]
+        mean = torch.empty(m, dtype=torch.float64, device=new_locs.device)
+        var = torch.empty(m, dtype=torch.float64, device=new_locs.device) if variance else None
+        self.check(exa_predict(self.handle, locs, z, theta, locs.shape[0], new_locs, m, mean, var))
+        return mean, var
+
+    def fisher(self, locs, theta) -> np.ndarray:
+        """Fisher information of (sigma^2, beta, nu), 3 x 3."""
+        out = (ctypes.c_double * 9)()
+        self.check(exa_fisher(self.handle, locs, theta, locs.shape[0], out))
+        return np.array(out[:]).reshape(3, 3)
 
     def simulate(self, locs, eps, theta, prec=EXA_FP64):
         import torch
@@ -319,6 +337,17 @@ def exa_ctx_set_tc_pairs(ctx: int, on: int) -> int:
 
 def exa_ctx_set_far_tile_margin(ctx: int, bits: int) -> int:
     return lib().exa_ctx_set_far_tile_margin(_P(ctx), int(bits))
+
+
+def exa_predict(ctx: int, locs, z, theta, n: int, new_locs, m: int, mean, var=None) -> int:
+    return lib().exa_predict(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _P(_dev_ptr(z, "z", n)), _theta(theta), n,
+                             _P(_dev_ptr(new_locs, "new_locs", 2 * m) if m else None),
+                             int(m), _P(_dev_ptr(mean, "mean", m) if m else None),
+                             _P(_dev_ptr(var, "var", m) if var is not None else None))
+
+
+def exa_fisher(ctx: int, locs, theta, n: int, out) -> int:
+    return lib().exa_fisher(_P(ctx), _P(_dev_ptr(locs, "locs", 2 * n)), _theta(theta), n, out)
 
 
 def exa_loglik_noalloc(cuda_stream: int, locs, z, theta, n: int, loglik: ctypes.c_double) -> int:

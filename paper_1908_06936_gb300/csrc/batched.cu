@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) batched_gen_kernel(int nrep, const BMeta*
       v = Pr.sigma2;
     } else {
       const double dx = xi - m.locs[2 * j], dy = yi - m.locs[2 * j + 1];
-      v = matern_value_tab(Pr, tab, sqrt(dx * dx + dy * dy));
+      v = matern_value_tab(Pr, tab, dx * dx + dy * dy);
     }
     a[i + j * m.npad] = v;
     if (mat2) mat2[m.mo + i + j * m.npad] = v;
@@ -977,7 +977,7 @@ static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const do
     ProfScope ps(c, PK_OTHER, 0.0, 0.0, 3);
     batched_params_kernel<<<(nrep + 63) / 64, 64, 0, s>>>(nrep, d_theta, dP, d_status);
     batched_table_nodes_kernel<<<dim3((unsigned)((kNodes + 127) / 128), (unsigned)nrep), 128, 0, s>>>(dP, dNodes);
-    batched_table_coef_kernel<<<dim3(1, (unsigned)nrep), 128, 0, s>>>(dNodes, dTab);
+    batched_table_coef_kernel<<<dim3((kTabSeg + 127) / 128, (unsigned)nrep), 128, 0, s>>>(dNodes, dTab);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

@@ -35,6 +35,7 @@ __host__ __device__ inline void matern_params_hd(const double theta[3], MaternPa
   const double nu = theta[2];
   p->sigma2 = theta[0];
   p->beta = theta[1];
+  p->ib2 = 1.0 / (theta[1] * theta[1]);
   p->nu = nu;
   p->logc = (1.0 - nu) * 0.69314718055994530942 - lgamma(nu);
   const int N = (int)floor(nu + 0.5);
@@ -157,6 +158,15 @@ __device__ __forceinline__ bool bessel_k_nu(const MaternParams& P, double x, dou
   return scaled;
 }
 
+// Sigma / sigma^2 at x = r / beta > 0 (Eq. 3 without the variance).
+__device__ __forceinline__ double matern_ratio(const MaternParams& P, double x) {
+  if (x > 800.0) return 0.0;
+  const double lnx = log(x);
+  double knu, knum1;
+  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
+  return exp(P.logc + P.nu * lnx - (scaled ? x : 0.0)) * knu;
+}
+
 // Eq. 3 at distance r.
 __device__ __forceinline__ double matern_value(const MaternParams& P, double r) {
   if (r == 0.0) return P.sigma2;
@@ -170,17 +180,17 @@ __device__ __forceinline__ double matern_value(const MaternParams& P, double r) 
   return P.sigma2 * exp(e) * knu;
 }
 
-// Segment of x for the table (x finite, 2^kTabE0 <= x < 2^(kTabE0 + kTabOct)):
+// Segment of s for the table (s finite, 2^kTabE0 <= s < 2^(kTabE0 + kTabOct)):
 // integer work on the bit pattern only.
-__device__ __forceinline__ int table_segment(double x) {
-  const long long b = __double_as_longlong(x);
+__device__ __forceinline__ int table_segment(double s) {
+  const long long b = __double_as_longlong(s);
   const int e = (int)((b >> 52) & 0x7FF) - 1023;
-  const int sub = (int)((b >> (52 - 3)) & (kTabSub - 1));
+  const int sub = (int)((b >> (52 - kTabSubBits)) & (kTabSub - 1));
   return (e - kTabE0) * kTabSub + sub;
 }
 
-// Table construction.  Segment sgi covers [lo, lo + w) with lo = 2^e (1 + sub / kTabSub),
-// w = 2^e / kTabSub.  Node id = sgi (kTabDeg + 1) + k is q at the k-th Chebyshev point.
+// Table construction.  Segment sgi covers [lo, lo + w) of s with lo = 2^e (1 + sub / kTabSub),
+// w = 2^e / kTabSub.  Node id = sgi (kTabDeg + 1) + k is f at the k-th Chebyshev point.
 __device__ __forceinline__ void segment_geometry(int sgi, double& centre, double& half) {
   const int e = kTabE0 + sgi / kTabSub, sub = sgi % kTabSub;
   const double lo = ldexp(1.0 + (double)sub / kTabSub, e);
@@ -194,11 +204,7 @@ __device__ __forceinline__ double table_node_value(const MaternParams& P, int id
   double centre, half;
   segment_geometry(sgi, centre, half);
   const double tk = cos(3.14159265358979323846 * (k + 0.5) / (kTabDeg + 1));
-  const double x = centre + half * tk;
-  const double lnx = log(x);
-  double knu, knum1;
-  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
-  return P.logc + P.nu * lnx + log(knu) + (scaled ? 0.0 : x);
+  return matern_ratio(P, sqrt(centre + half * tk));  // f at the k-th Chebyshev point of s
 }
 
 // Chebyshev coefficients of segment sgi from its nodes, then their monomial form in t.
@@ -234,20 +240,20 @@ __device__ __forceinline__ void table_segment_coefs(const double* __restrict__ n
   for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
 }
 
-// Sigma at distance r from the table (exact routine below 2^kTabE0).
-__device__ __forceinline__ double matern_value_tab(const MaternParams& P, const MaternTable* __restrict__ T, double r) {
-  if (r == 0.0) return P.sigma2;
-  const double x = r / P.beta;
-  if (!(x > 0.0)) return x;
-  if (x > 800.0) return 0.0;
-  if (x < 0.0625) return matern_value(P, r);
-  const int sgi = table_segment(x);
-  const double t = fma(x, __ldg(&T->ih[sgi]), __ldg(&T->mc[sgi]));
+// Sigma at squared distance r2 = r^2 from the table (exact routine outside its range).
+__device__ __forceinline__ double matern_value_tab(const MaternParams& P, const MaternTable* __restrict__ T,
+                                                   double r2) {
+  if (r2 == 0.0) return P.sigma2;
+  const double s = r2 * P.ib2;
+  static_assert(kTabE0 == -8 && kTabE0 + kTabOct == 12, "table range below");
+  if (!(s >= 0x1p-8) || !(s < 0x1p12)) return matern_value(P, sqrt(r2));  // also NaN
+  const int sgi = table_segment(s);
+  const double t = fma(s, __ldg(&T->ih[sgi]), __ldg(&T->mc[sgi]));
   const double* c = T->a[sgi];
-  double q = __ldg(&c[kTabDeg]);
+  double f = __ldg(&c[kTabDeg]);
 #pragma unroll
-  for (int k = kTabDeg - 1; k >= 0; --k) q = fma(q, t, __ldg(&c[k]));
-  return P.sigma2 * exp(q - x);
+  for (int k = kTabDeg - 1; k >= 0; --k) f = fma(f, t, __ldg(&c[k]));
+  return P.sigma2 * f;
 }
 
 }  // namespace exa

@@ -55,6 +55,8 @@ struct exa_ctx {
   // gradient
   exa::DevBuf gr_part;      // second n x n buffer: Sigma^-1 for the gradient trace term
   exa::DevBuf gr_blocks;    // per-block gradient partial sums
+  exa::DevBuf pr_c, pr_y;   // prediction: cross-covariance block and its solve block
+  exa::DevBuf fs_m;         // Fisher information: Sigma^-1 D_k for k = 0, 1, 2
   // batched
   exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work, bt_mat2;
   exa::BatchPlan* bplan = nullptr;  // cached work list of the last shape set

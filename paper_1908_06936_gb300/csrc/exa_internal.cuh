@@ -31,6 +31,7 @@ constexpr int kMillerMax = 96;    // deepest backward recurrence (x just above 2
 
 struct MaternParams {
   double sigma2, beta, nu;
+  double ib2;        // 1 / beta^2
   double logc;       // (1 - nu) ln 2 - lgamma(nu)
   double mu;         // nu - N, in [-1/2, 1/2]
   int N;             // round(nu)
@@ -52,14 +53,17 @@ struct MaternParams {
 // Host: fill the parameter block for theta (defined in matern.cu).
 void matern_params(const double theta[3], MaternParams* p);
 
-// Per-theta interpolation table of q(x) = ln(2^(1-nu)/Gamma(nu) x^nu e^x K_nu(x)), so that
-// Sigma = sigma^2 exp(q(x) - x).  Segments follow the binary exponent of x: octave
-// [2^e, 2^(e+1)), e in [kTabE0, kTabE0 + kTabOct), split into kTabSub equal pieces; on
-// each, q is a degree-kTabDeg polynomial in t = (x - centre) / half-width.  Below
-// 2^kTabE0 and above 800 the exact routine / zero apply.
-constexpr int kTabE0 = -4;
-constexpr int kTabOct = 14;
-constexpr int kTabSub = 8;
+// Per-theta interpolation table of f(s) = Sigma / sigma^2 as a function of s = (r / beta)^2,
+// so that an entry costs no square root, division or exponential.  Segments follow the
+// binary exponent of s: octave [2^e, 2^(e+1)), e in [kTabE0, kTabE0 + kTabOct), split into
+// kTabSub equal pieces; on each, f is a degree-kTabDeg polynomial in t = (s - centre) /
+// half-width (Chebyshev interpolation, relative error far below 1e-15 at this width:
+// the pieces are 1/64 of an octave wide).  Below 2^kTabE0 (x < 1/16) and from
+// 2^(kTabE0 + kTabOct) on (x >= 64) the exact routine applies.
+constexpr int kTabE0 = -8;
+constexpr int kTabOct = 20;
+constexpr int kTabSubBits = 6;
+constexpr int kTabSub = 1 << kTabSubBits;
 constexpr int kTabSeg = kTabOct * kTabSub;
 constexpr int kTabDeg = 10;
 struct MaternTable {

@@ -208,6 +208,31 @@ struct GradParams {
   double psi_nu;  // digamma(nu)
 };
 
+// D_sigma2, D_beta, D_nu at distance r (the formulas of the header; the diagonal r = 0
+// gives (1, 0, 0)).
+__device__ __forceinline__ void matern_derivs(const GradParams& G, double r, double& d0, double& d1, double& d2) {
+  const MaternParams& P = G.m;
+  if (r == 0.0) {
+    d0 = 1.0;
+    d1 = d2 = 0.0;
+    return;
+  }
+  const double x = r / P.beta;
+  if (x > 800.0) {
+    d0 = d1 = d2 = 0.0;
+    return;
+  }
+  const double lnx = log(x);
+  double knu, knum1;
+  const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
+  const double base = P.logc + P.nu * lnx;
+  const double pre = P.sigma2 * exp(base - (scaled ? x : 0.0));  // sigma^2 c x^nu (e^-x if scaled)
+  const double sig = pre * knu;
+  d0 = sig / P.sigma2;
+  d1 = pre * knum1 * x / P.beta;
+  d2 = sig * (lnx - 0.69314718055994530942 - G.psi_nu) + P.sigma2 * exp(base - x) * dknu_dnu_scaled(P.nu, x);
+}
+
 // One 64 x 64 lower tile per block (as the generator), 256 threads; per-block partial
 // sums of w (a_i a_j - S_ij) D_k for k = sigma^2, beta, nu in a fixed order.
 __global__ void __launch_bounds__(256) grad_reduce_kernel(const double* __restrict__ locs, int64_t n,
@@ -218,7 +243,6 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const double* __restri
   __shared__ double red[3][256];
   int ti, tj;
   tri_dec(blockIdx.x, ti, tj);
-  const MaternParams& P = G.m;
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   if (i < n) {
@@ -230,27 +254,7 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const double* __restri
       const double cij = w * (ai * alpha[j] - sinv[i + j * lds]);
       double d0, d1, d2;
       const double dx = xi - locs[2 * j], dy = yi - locs[2 * j + 1];
-      const double r = sqrt(dx * dx + dy * dy);
-      if (r == 0.0) {
-        d0 = 1.0;
-        d1 = d2 = 0.0;
-      } else {
-        const double x = r / P.beta;
-        if (x > 800.0) {
-          d0 = d1 = d2 = 0.0;
-        } else {
-          const double lnx = log(x);
-          double knu, knum1;
-          const bool scaled = bessel_k_nu(P, x, lnx, knu, knum1);
-          const double base = P.logc + P.nu * lnx;
-          const double pre = P.sigma2 * exp(base - (scaled ? x : 0.0));  // sigma^2 c x^nu (e^-x if scaled)
-          const double sig = pre * knu;
-          d0 = sig / P.sigma2;
-          d1 = pre * knum1 * x / P.beta;
-          d2 = sig * (lnx - 0.69314718055994530942 - G.psi_nu) +
-               P.sigma2 * exp(base - x) * dknu_dnu_scaled(P.nu, x);
-        }
-      }
+      matern_derivs(G, sqrt(dx * dx + dy * dy), d0, d1, d2);
       acc0 = fma(cij, d0, acc0);
       acc1 = fma(cij, d1, acc1);
       acc2 = fma(cij, d2, acc2);
@@ -310,6 +314,41 @@ static cudaError_t launch_gradient(exa_ctx* c, const double* locs, int64_t n, in
   return cudaGetLastError();
 }
 
+// Sigma^-1 from the FP64 factor in c->mat: X = L^-1 in place (block columns right to
+// left: T = X22 L_panel, X_panel = -T W_j, X_jj = W_j), then the lower tiles of
+// S = X^T X.  Stream-ordered; the factor is consumed.
+static cudaError_t sigma_inverse_fp64(exa_ctx* c, int64_t npad, int nb, double* S) {
+  const int T = (int)(npad / nb);
+  double* A = (double*)c->mat.p;
+  double* W = (double*)c->w_all.p;
+  double* Tbuf = (double*)c->panel.p;  // npad x nb
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  for (int j = T - 1; j >= 0 && e == cudaSuccess; --j) {
+    const int64_t j0 = (int64_t)j * nb, l0 = j0 + nb, m = npad - l0;
+    if (m > 0) {
+      ProfScope ps(c, PK_GRAD, (double)m * m * nb + 2.0 * m * nb * nb, 8.0 * ((double)m * m / 2 + 3.0 * m * nb), 2);
+      dim3 grid(nb / 64, (unsigned)(m / 64));
+      trmm_lower_panel_kernel<<<grid, 128, 0, s>>>(A, npad, l0, j0, nb, Tbuf, c->d_status);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = launch_dgemm_nt_small(s, (int)m, nb, nb, -1.0, Tbuf, nb, 1, W + (int64_t)j * nb * nb, 1, nb, 0.0,
+                                  A + l0 + j0 * npad, 1, npad, c->d_status);
+    }
+    if (e == cudaSuccess) {
+      put_diag_inverse_kernel<<<32, 256, 0, s>>>(A, npad, j0, nb, W + (int64_t)j * nb * nb);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) {
+    const long long t64 = npad / 64;
+    ProfScope ps(c, PK_GRAD, (double)npad * npad * npad / 3.0, 8.0 * (double)npad * npad);
+    lauum_tiles_kernel<<<(unsigned)(t64 * (t64 + 1) / 2), 128, 0, s>>>(A, npad, npad, S, npad, c->d_status);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 }  // namespace exa
 
 using namespace exa;
@@ -341,7 +380,6 @@ extern "C" exa_status exa_loglik_grad(exa_ctx* c, const double* d_locs, const do
   double* W = (double*)c->w_all.p;
   double* S = (double*)c->gr_part.p;
   double* part = (double*)c->partial.p;
-  double* Tbuf = (double*)c->panel.p;  // npad x nb
   cudaStream_t s = c->stream;
   cudaError_t e = cudaSuccess;
   // a = L^-T y (in place in y)
@@ -350,30 +388,7 @@ extern "C" exa_status exa_loglik_grad(exa_ctx* c, const double* d_locs, const do
     ProfScope ps(c, PK_TRSV, 2.0 * rows * nb, 8.0 * rows * nb, 2);
     e = launch_trsv_bwd_step(s, A, npad, npad, nb, k, W, y, part + 2 * kRedPartials, c->d_status);
   }
-  // X = L^-1 in place, block columns right to left
-  for (int j = T - 1; j >= 0 && e == cudaSuccess; --j) {
-    const int64_t j0 = (int64_t)j * nb, l0 = j0 + nb, m = npad - l0;
-    if (m > 0) {
-      ProfScope ps(c, PK_GRAD, (double)m * m * nb + 2.0 * m * nb * nb, 8.0 * ((double)m * m / 2 + 3.0 * m * nb), 2);
-      dim3 grid(nb / 64, (unsigned)(m / 64));
-      trmm_lower_panel_kernel<<<grid, 128, 0, s>>>(A, npad, l0, j0, nb, Tbuf, c->d_status);
-      e = cudaGetLastError();
-      if (e == cudaSuccess)
-        e = launch_dgemm_nt_small(s, (int)m, nb, nb, -1.0, Tbuf, nb, 1, W + (int64_t)j * nb * nb, 1, nb, 0.0,
-                                  A + l0 + j0 * npad, 1, npad, c->d_status);
-    }
-    if (e == cudaSuccess) {
-      put_diag_inverse_kernel<<<32, 256, 0, s>>>(A, npad, j0, nb, W + (int64_t)j * nb * nb);
-      e = cudaGetLastError();
-    }
-  }
-  // Sigma^-1 = X^T X (lower tiles) into S
-  if (e == cudaSuccess) {
-    const long long t64 = npad / 64;
-    ProfScope ps(c, PK_GRAD, (double)npad * npad * npad / 3.0, 8.0 * (double)npad * npad);
-    lauum_tiles_kernel<<<(unsigned)(t64 * (t64 + 1) / 2), 128, 0, s>>>(A, npad, npad, S, npad, c->d_status);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = sigma_inverse_fp64(c, npad, nb, S);
   // fused regeneration of dSigma/dtheta and reduction
   if ((st = ensure(c, c->vec, (size_t)3 * npad * sizeof(double), "vectors")) != EXA_OK) return st;
   const long long t64n = (n + 63) / 64;
@@ -390,5 +405,161 @@ extern "C" exa_status exa_loglik_grad(exa_ctx* c, const double* d_locs, const do
   grad[0] = c->h_scalars[8];
   grad[1] = c->h_scalars[9];
   grad[2] = c->h_scalars[10];
+  return EXA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fisher information (exact_fisher): I_kl = 1/2 tr(Sigma^-1 D_k Sigma^-1 D_l).
+//   S = Sigma^-1 (lower tiles, as for the gradient), mirrored to a full matrix;
+//   D_k written as a full symmetric matrix into the factor's buffer (zero in the
+//   padding); M_k = S D_k on FP64 DMMA; tr(M_k M_l) = sum_ij M_k(i, j) M_l(j, i)
+//   from 32 x 32 tile pairs (I, J) / (J, I), per-tile partials summed in a fixed order.
+// ---------------------------------------------------------------------------
+namespace exa {
+
+__global__ void __launch_bounds__(256) mirror_lower_kernel(double* __restrict__ s, int64_t ld, int64_t npad) {
+  const int64_t j = blockIdx.y;  // column
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < j; i += (int64_t)gridDim.x * blockDim.x)
+    s[i + j * ld] = s[j + i * ld];  // upper (i < j) from lower (j, i)
+}
+
+__global__ void __launch_bounds__(256) deriv_matrix_kernel(const double* __restrict__ locs, int64_t n, int64_t npad,
+                                                           const __grid_constant__ GradParams G, int k,
+                                                           double* __restrict__ D) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (i < n && j < n) {
+      const double dx = locs[2 * i] - locs[2 * j], dy = locs[2 * i + 1] - locs[2 * j + 1];
+      double d[3];
+      matern_derivs(G, sqrt(dx * dx + dy * dy), d[0], d[1], d[2]);
+      v = d[k];
+    }
+    D[i + j * npad] = v;
+  }
+}
+
+// partial[tile][p] for the 6 pairs p = (0,0),(0,1),(0,2),(1,1),(1,2),(2,2)
+__global__ void __launch_bounds__(256) trace_pairs_kernel(const double* __restrict__ M, int64_t npad,
+                                                          double* __restrict__ partial) {
+  __shared__ double a[3][32][33], b[3][32][33];
+  __shared__ double red[6][8];
+  const int64_t I = (int64_t)blockIdx.y * 32, J = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t nn = npad * npad;
+  for (int k = 0; k < 3; ++k)
+    for (int r = ty; r < 32; r += 8) {
+      a[k][r][tx] = M[k * nn + (I + tx) + (J + r) * npad];  // a[k][c][r] = M_k(I + r, J + c): stored by column c
+      b[k][r][tx] = M[k * nn + (J + tx) + (I + r) * npad];  // b[k][c][r] = M_k(J + r, I + c)
+    }
+  __syncthreads();
+  // tr contribution: sum_{r, c} M_k(I + r, J + c) M_l(J + c, I + r) = sum a[k][c][r] b[l][r][c]
+  const int pk[6] = {0, 0, 0, 1, 1, 2}, pl[6] = {0, 1, 2, 1, 2, 2};
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = ty; c < 32; c += 8) {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) s[p] = fma(a[pk[p]][c][tx], b[pl[p]][tx][c], s[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    double v = s[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tx == 0) red[p][ty] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[threadIdx.x][w];
+    partial[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) trace_finish_kernel(const double* __restrict__ partial, int64_t ntiles,
+                                                           double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int p = blockIdx.x, tid = threadIdx.x;
+  double v = 0.0;
+  for (int64_t t = tid; t < ntiles; t += 256) v += partial[t * 6 + p];
+  sh[tid] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) out[p] = 0.5 * sh[0];
+}
+
+}  // namespace exa
+
+extern "C" exa_status exa_fisher(exa_ctx* c, const double* d_locs, const double theta[3], int64_t n,
+                                 double fisher[9]) {
+  if (!c) return EXA_ERR_ARG;
+  c->err[0] = 0;
+  c->last_pivot = -1;
+  if (n < 1 || !d_locs || !fisher) return set_err(c, EXA_ERR_ARG, "bad n or NULL pointer");
+  for (int i = 0; i < 9; ++i) fisher[i] = NAN;
+  exa_status st = check_theta(c, theta);
+  if (st != EXA_OK) return st;
+  const int nb = c->tile_nb;
+  const int64_t npad = round_up(n, 128);  // 32- and 64-tile kernels below; multiple of nb
+  const size_t nn = (size_t)npad * npad;
+  if ((st = ensure(c, c->gr_part, nn * sizeof(double), "inverse covariance")) != EXA_OK) return st;
+  if ((st = ensure(c, c->fs_m, 3 * nn * sizeof(double), "Fisher products")) != EXA_OK) return st;
+  if ((st = ensure(c, c->mat, nn * sizeof(double), "matrix")) != EXA_OK) return st;
+  const int64_t t32 = npad / 32;
+  if ((st = ensure(c, c->gr_blocks, (size_t)t32 * t32 * 6 * sizeof(double), "Fisher partials")) != EXA_OK) return st;
+  if ((st = reset_status(c)) != EXA_OK) return st;
+  double* A = (double*)c->mat.p;
+  double* S = (double*)c->gr_part.p;
+  double* M = (double*)c->fs_m.p;
+  cudaStream_t s = c->stream;
+  MaternParams P;
+  matern_params(theta, &P);
+  const MaternTable* tab = nullptr;
+  if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
+  cudaError_t e;
+  {
+    ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
+    e = launch_matern_gen(s, d_locs, n, npad, P, A, npad, nullptr, tab);
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "generation launch");
+  if ((st = factor_fp64(c, A, npad, npad, nb)) != EXA_OK) return st;
+  if ((st = read_status(c)) != EXA_OK) return st;
+  e = sigma_inverse_fp64(c, npad, nb, S);
+  if (e == cudaSuccess) {
+    mirror_lower_kernel<<<dim3((unsigned)((npad + 255) / 256 < 32 ? (npad + 255) / 256 : 32), (unsigned)npad), 256, 0,
+                          s>>>(S, npad, npad);
+    e = cudaGetLastError();
+  }
+  GradParams G;
+  G.m = P;
+  G.psi_nu = host_digamma(theta[2]);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    {
+      ProfScope ps(c, PK_GRAD, 0.0, 8.0 * (double)nn);
+      deriv_matrix_kernel<<<dim3((unsigned)((npad + 255) / 256 < 32 ? (npad + 255) / 256 : 32), (unsigned)npad), 256,
+                            0, s>>>(d_locs, n, npad, G, k, A);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(c, PK_DGEMM_SMALL, 2.0 * (double)npad * npad * npad, 24.0 * (double)nn);
+      e = launch_dgemm_nt_small(s, (int)npad, (int)npad, (int)npad, 1.0, S, 1, npad, A, 1, npad, 0.0, M + k * nn, 1,
+                                npad, c->d_status);
+    }
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_GRAD, 0.0, 48.0 * (double)nn, 2);
+    trace_pairs_kernel<<<dim3((unsigned)t32, (unsigned)t32), 256, 0, s>>>(M, npad, (double*)c->gr_blocks.p);
+    trace_finish_kernel<<<6, 256, 0, s>>>((double*)c->gr_blocks.p, t32 * t32, c->d_scalars + 16);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_scalars + 16, c->d_scalars + 16, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "Fisher launch");
+  if ((st = read_status(c)) != EXA_OK) return st;
+  const double* v = c->h_scalars + 16;
+  const int pk[6] = {0, 0, 0, 1, 1, 2}, pl[6] = {0, 1, 2, 1, 2, 2};
+  for (int p = 0; p < 6; ++p) fisher[pk[p] * 3 + pl[p]] = fisher[pl[p] * 3 + pk[p]] = v[p];
   return EXA_OK;
 }

@@ -2,8 +2,10 @@
 // modified Bessel function K_nu of fractional order.
 //
 // Per theta the host precomputes every quantity that depends only on nu
-// (Gamma values, Temme's Gamma_1/Gamma_2, reciprocal tables), so the per-entry
-// work is one log, one exp (+ one sqrt for x > 2) and division-free loops.
+// (Gamma values, Temme's Gamma_1/Gamma_2, reciprocal tables) for the exact
+// routine, and the device builds from it an interpolation table of
+// Sigma / sigma^2 in s = (r / beta)^2, so that most entries cost a squared
+// distance, a segment lookup on the bit pattern and a degree-10 polynomial.
 #include <math.h>
 
 #include "bessel.cuh"
@@ -58,8 +60,8 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
     } else {
       const double dx = xi - __ldg(locs + 2 * j);
       const double dy = yi - __ldg(locs + 2 * j + 1);
-      const double r = sqrt(dx * dx + dy * dy);
-      v = tab ? matern_value_tab(P, tab, r) : matern_value(P, r);
+      const double r2 = dx * dx + dy * dy;
+      v = tab ? matern_value_tab(P, tab, r2) : matern_value(P, sqrt(r2));
       vmax = fmax(vmax, fabs(v));
     }
     a[i + j * ld] = v;
@@ -106,7 +108,7 @@ __global__ void matern_table_coef_kernel(const double* __restrict__ nodes, Mater
 cudaError_t launch_matern_table(cudaStream_t s, const MaternParams& p, MaternTable* tab, double* nodes) {
   const int total = kTabSeg * (kTabDeg + 1);
   matern_table_nodes_kernel<<<(total + 127) / 128, 128, 0, s>>>(p, nodes);
-  matern_table_coef_kernel<<<1, 128, 0, s>>>(nodes, tab);
+  matern_table_coef_kernel<<<(kTabSeg + 127) / 128, 128, 0, s>>>(nodes, tab);
   return cudaGetLastError();
 }
 
