@@ -66,6 +66,7 @@ def _load():
                 "oracle_factor": (_I64, [_I64, _PD, _PD, _PD]),
                 "oracle_predict": (_I64, [_I64, _PD, _PD, _PD, _I64, _PD, _PD, _PD]),
                 "oracle_fisher": (_I64, [_I64, _PD, _PD, _PD]),
+                "oracle_set_model": (None, [_D, ctypes.c_int, _D]),
                 "oracle_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -214,3 +215,9 @@ def fisher(locs, theta) -> np.ndarray:
     if info != 0:
         raise ValueError("Sigma(theta) is not positive definite (pivot %d)" % (info - 1))
     return out.reshape(3, 3)
+
+
+def set_model(nugget: float = 0.0, metric: int = 0, radius: float = 6371.0) -> None:
+    """Model options for every later call: nugget tau^2 on the diagonal; metric 0 Euclidean,
+    1 great circle between (longitude, latitude) in degrees on a sphere of this radius."""
+    _load().oracle_set_model(float(nugget), int(metric), float(radius))

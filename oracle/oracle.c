@@ -171,10 +171,37 @@ void oracle_matern_grad(const double theta[3], double r, double out[3]) {
   out[2] = s * (-ORACLE_LN2 - oracle_digamma(nu) + log(x)) + pref * oracle_dbesselk_dnu_scaled(nu, x);
 }
 
-static double oracle_dist(const double* locs, int64_t i, int64_t j) {
-  const double dx = locs[2 * i] - locs[2 * j];
-  const double dy = locs[2 * i + 1] - locs[2 * j + 1];
+/* Model options (the paper's dmetric and nugget):
+ *   metric 0: Euclidean distance between (x, y) pairs;
+ *   metric 1: great-circle distance (haversine form, the reference the paper cites
+ *             for dmetric = great_circle) between (longitude, latitude) pairs in
+ *             degrees on a sphere of the given radius;
+ *   nugget:   tau^2 added to every diagonal entry (Sigma + tau^2 I).           */
+static double g_nugget = 0.0;
+static int g_metric = 0;
+static double g_radius = 6371.0;
+
+void oracle_set_model(double nugget, int metric, double radius) {
+  g_nugget = nugget;
+  g_metric = metric;
+  g_radius = radius;
+}
+
+static double oracle_dist_xy(double x1, double y1, double x2, double y2) {
+  if (g_metric == 1) {
+    const double rad = 3.14159265358979323846 / 180.0;
+    const double p1 = y1 * rad, p2 = y2 * rad;
+    const double sp = sin(0.5 * (p2 - p1)), sl = sin(0.5 * (x2 - x1) * rad);
+    double a = sp * sp + cos(p1) * cos(p2) * sl * sl;
+    if (a > 1.0) a = 1.0;
+    return 2.0 * g_radius * asin(sqrt(a));
+  }
+  const double dx = x1 - x2, dy = y1 - y2;
   return sqrt(dx * dx + dy * dy);
+}
+
+static double oracle_dist(const double* locs, int64_t i, int64_t j) {
+  return oracle_dist_xy(locs[2 * i], locs[2 * i + 1], locs[2 * j], locs[2 * j + 1]);
 }
 
 /* Full symmetric covariance matrix, row-major n x n.                       */
@@ -182,7 +209,7 @@ void oracle_covariance(int64_t n, const double* locs, const double theta[3], dou
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < n; ++i) {
     for (int64_t j = 0; j <= i; ++j) {
-      const double v = oracle_matern(theta, oracle_dist(locs, i, j));
+      const double v = oracle_matern(theta, oracle_dist(locs, i, j)) + (i == j ? g_nugget : 0.0);
       S[i * n + j] = v;
       S[j * n + i] = v;
     }
@@ -194,7 +221,8 @@ void oracle_covariance(int64_t n, const double* locs, const double theta[3], dou
 void oracle_covariance_entries(int64_t m, const int64_t* rows, const int64_t* cols, const double* locs,
                                const double theta[3], double* out) {
 #pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t k = 0; k < m; ++k) out[k] = oracle_matern(theta, oracle_dist(locs, rows[k], cols[k]));
+  for (int64_t k = 0; k < m; ++k)
+    out[k] = oracle_matern(theta, oracle_dist(locs, rows[k], cols[k])) + (rows[k] == cols[k] ? g_nugget : 0.0);
 }
 
 /* Unblocked Cholesky (Cholesky-Crout, lower), in place on a row-major n x n
@@ -417,11 +445,8 @@ int64_t oracle_predict(int64_t n, const double* locs, const double* Z, const dou
     for (int64_t i = 0; i < m; ++i) {
       double* c = (double*)malloc((size_t)n * sizeof(double));
       double* w = (double*)malloc((size_t)n * sizeof(double));
-      for (int64_t j = 0; j < n; ++j) {
-        const double dx = new_locs[2 * i] - locs[2 * j];
-        const double dy = new_locs[2 * i + 1] - locs[2 * j + 1];
-        c[j] = oracle_matern(theta, sqrt(dx * dx + dy * dy));
-      }
+      for (int64_t j = 0; j < n; ++j)
+        c[j] = oracle_matern(theta, oracle_dist_xy(new_locs[2 * i], new_locs[2 * i + 1], locs[2 * j], locs[2 * j + 1]));
       double mu = 0.0;
       for (int64_t j = 0; j < n; ++j) mu += c[j] * a[j];
       oracle_forward_solve(n, A, c, w);
