@@ -225,6 +225,18 @@ typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1, EXA_GEMM_T3_PAIR = 2 } exa_gemm
 exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
                            const double* d_b, double* d_c, int64_t ldc, int store);
 
+/* Model options (the paper's dmetric and a nugget), applied by every later call
+ * on the context except exa_loglik_noalloc (always Euclidean, no nugget):
+ *   nugget  tau^2 >= 0 added to every diagonal entry: Sigma + tau^2 I (a fixed
+ *           value, not estimated; the gradient and Fisher information are those of
+ *           theta with tau^2 held fixed; predictions are of the noise-free field);
+ *   metric  0: Euclidean distance between (x, y); 1: great-circle distance
+ *           between (longitude, latitude) in degrees, haversine form, on a sphere
+ *           of the given radius (beta is then in the radius's units);
+ *   radius  > 0, or 0 for 6371 (the Earth's mean radius in km).
+ * EXA_ERR_ARG for a negative or non-finite nugget/radius or another metric.   */
+exa_status exa_ctx_set_model(exa_ctx* ctx, double nugget, int metric, double radius);
+
 /* Off-band trailing updates of the mixed factorisation on pairs of SMs
  * (256 x 256 tiles, tcgen05 .cta_group::2; default on) or on single SMs
  * (128 x 128 tiles).  Both compute the same products.                       */

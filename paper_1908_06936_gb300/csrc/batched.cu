@@ -68,7 +68,7 @@ struct BCtl {
 __device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
 
 __global__ void batched_params_kernel(int nrep, const double* __restrict__ theta, MaternParams* __restrict__ P,
-                                      int32_t* __restrict__ status) {
+                                      int32_t* __restrict__ status, double nugget, int metric, double radius) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrep) return;
   double th[3] = {theta[3 * r], theta[3 * r + 1], theta[3 * r + 2]};
@@ -77,6 +77,9 @@ __global__ void batched_params_kernel(int nrep, const double* __restrict__ theta
   status[r] = ok ? EXA_OK : EXA_ERR_ARG;
   if (!ok) th[0] = th[1] = th[2] = 1.0;  // keep the arithmetic finite; the result is discarded
   matern_params_hd(th, &P[r]);
+  P[r].nugget = nugget;
+  P[r].metric = metric;
+  P[r].radius = radius;
 }
 
 // Per-replicate interpolation tables (blockIdx.y = replicate).
@@ -130,10 +133,9 @@ __global__ void __launch_bounds__(256) batched_gen_kernel(int nrep, const BMeta*
     if (i >= m.n || j >= m.n) {
       v = (i == j) ? 1.0 : 0.0;
     } else if (i == j) {
-      v = Pr.sigma2;
+      v = Pr.sigma2 + Pr.nugget;
     } else {
-      const double dx = xi - m.locs[2 * j], dy = yi - m.locs[2 * j + 1];
-      v = matern_value_tab(Pr, tab, dx * dx + dy * dy);
+      v = matern_value_tab(Pr, tab, model_dist2(Pr, xi, yi, m.locs[2 * j], m.locs[2 * j + 1]));
     }
     a[i + j * m.npad] = v;
     if (mat2) mat2[m.mo + i + j * m.npad] = v;
@@ -975,7 +977,8 @@ static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const do
   if (e != cudaSuccess) return cuda_err(c, e, "batched setup");
   {
     ProfScope ps(c, PK_OTHER, 0.0, 0.0, 3);
-    batched_params_kernel<<<(nrep + 63) / 64, 64, 0, s>>>(nrep, d_theta, dP, d_status);
+    batched_params_kernel<<<(nrep + 63) / 64, 64, 0, s>>>(nrep, d_theta, dP, d_status, c->nugget, c->metric,
+                                                          c->radius);
     batched_table_nodes_kernel<<<dim3((unsigned)((kNodes + 127) / 128), (unsigned)nrep), 128, 0, s>>>(dP, dNodes);
     batched_table_coef_kernel<<<dim3((kTabSeg + 127) / 128, (unsigned)nrep), 128, 0, s>>>(dNodes, dTab);
     e = cudaGetLastError();

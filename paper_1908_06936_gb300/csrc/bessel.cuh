@@ -36,6 +36,10 @@ __host__ __device__ inline void matern_params_hd(const double theta[3], MaternPa
   p->sigma2 = theta[0];
   p->beta = theta[1];
   p->ib2 = 1.0 / (theta[1] * theta[1]);
+  p->nugget = 0.0;
+  p->radius = 6371.0;
+  p->metric = 0;
+  p->pad2_ = 0;
   p->nu = nu;
   p->logc = (1.0 - nu) * 0.69314718055994530942 - lgamma(nu);
   const int N = (int)floor(nu + 0.5);
@@ -156,6 +160,22 @@ __device__ __forceinline__ bool bessel_k_nu(const MaternParams& P, double x, dou
     knum1 = a;
   }
   return scaled;
+}
+
+// Squared distance between two locations: Euclidean, or the great-circle distance
+// (haversine form) between (longitude, latitude) pairs in degrees on a sphere of
+// radius P.radius (the paper's dmetric = great_circle).
+__device__ __forceinline__ double model_dist2(const MaternParams& P, double x1, double y1, double x2, double y2) {
+  if (P.metric == 1) {
+    const double rad = 3.14159265358979323846 / 180.0;
+    const double p1 = y1 * rad, p2 = y2 * rad;
+    const double sp = sin(0.5 * (p2 - p1)), sl = sin(0.5 * (x2 - x1) * rad);
+    const double a = fmin(fma(cos(p1) * cos(p2), sl * sl, sp * sp), 1.0);
+    const double d = 2.0 * P.radius * asin(sqrt(a));
+    return d * d;
+  }
+  const double dx = x1 - x2, dy = y1 - y2;
+  return dx * dx + dy * dy;
 }
 
 // Sigma / sigma^2 at x = r / beta > 0 (Eq. 3 without the variance).

@@ -114,6 +114,13 @@ exa_status factor_fp64(exa_ctx* c, double* a, int64_t ld, int64_t npad, int nb) 
   return EXA_OK;
 }
 
+void model_params(const exa_ctx* c, const double theta[3], MaternParams* P) {
+  matern_params(theta, P);
+  P->nugget = c->nugget;
+  P->metric = c->metric;
+  P->radius = c->radius;
+}
+
 exa_status matern_table(exa_ctx* c, const MaternParams& P, const MaternTable** tab) {
   const size_t bytes = sizeof(MaternTable) + (size_t)kTabSeg * (kTabDeg + 1) * sizeof(double) + 256;
   exa_status st = ensure(c, c->table, bytes, "interpolation table");
@@ -152,6 +159,16 @@ exa_status read_status(exa_ctx* c) {
 // exported entry points
 // ---------------------------------------------------------------------------
 extern "C" {
+
+exa_status exa_ctx_set_model(exa_ctx* c, double nugget, int metric, double radius) {
+  if (!c) return EXA_ERR_ARG;
+  if (!(nugget >= 0.0) || !isfinite(nugget) || (metric != 0 && metric != 1) || !(radius >= 0.0) || !isfinite(radius))
+    return set_err(c, EXA_ERR_ARG, "bad model options (nugget %g, metric %d, radius %g)", nugget, metric, radius);
+  c->nugget = nugget;
+  c->metric = metric;
+  c->radius = radius > 0.0 ? radius : 6371.0;
+  return EXA_OK;
+}
 
 exa_status exa_ctx_create(exa_ctx** out, void* cuda_stream, size_t workspace_bytes, int tile_nb) {
   if (!out) return EXA_ERR_ARG;
@@ -236,7 +253,7 @@ exa_status exa_covariance(exa_ctx* c, const double* d_locs, int64_t n, const dou
   exa_status st = check_theta(c, theta);
   if (st != EXA_OK) return st;
   MaternParams P;
-  matern_params(theta, &P);
+  model_params(c, theta, &P);
   const MaternTable* tab = nullptr;
   if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
   cudaError_t e = launch_matern_gen(c->stream, d_locs, n, n, P, d_sigma, ld, nullptr, tab);
@@ -315,7 +332,7 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
   double* tmp = y + npad;
   double* part = (double*)c->partial.p;
   MaternParams P;
-  matern_params(theta, &P);
+  model_params(c, theta, &P);
   cudaEventRecord(c->ev[0], c->stream);
   const MaternTable* tab = nullptr;
   if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
@@ -381,7 +398,7 @@ extern "C" exa_status exa_simulate(exa_ctx* c, const double* d_locs, const doubl
   cudaError_t e = cudaSuccess;
   if (prec == EXA_FP64) {
     MaternParams P;
-    matern_params(theta, &P);
+    model_params(c, theta, &P);
     const MaternTable* tab = nullptr;
     if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
     e = launch_matern_gen(c->stream, d_locs, n, npad, P, A, npad, nullptr, tab);

@@ -67,6 +67,9 @@ struct exa_ctx {
   long long batched_spin = 2000000000LL;  // bound of one dependency wait (SM cycles)
   int batched_stall = 0;            // test hook: add a task whose dependency is never met
   int tc_pairs = 1;                 // mixed trailing update on CTA pairs (tcgen05 .cta_group::2)
+  double nugget = 0.0;              // tau^2 on the diagonal
+  int metric = 0;                   // 0 Euclidean, 1 great circle (longitude, latitude in degrees)
+  double radius = 6371.0;           // sphere radius of the great-circle metric
   int far_tile_margin = 16;         // single-product far tiles below sigma^2 by this many binades (0: off)
   int batched_band = 0;             // mixed: tile updates within this many tile diagonals stay FP64
   int batched_max_iter = 10;        // mixed: refinement steps per replicate at most
@@ -101,6 +104,8 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
 void release_extra(exa_ctx* c);
 // Build the interpolation table for theta on the context stream; returns its device address.
 exa_status matern_table(exa_ctx* c, const MaternParams& P, const MaternTable** tab);
+// matern_params plus the context's model options (nugget, metric, radius).
+void model_params(const exa_ctx* c, const double theta[3], MaternParams* P);
 void release_batched(exa_ctx* c);
 // Lay out a split operand of `rows` x K in `buf` (T3 planes and/or OZ digits) and build its TMA maps.
 exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz);

@@ -32,6 +32,10 @@ constexpr int kMillerMax = 96;    // deepest backward recurrence (x just above 2
 struct MaternParams {
   double sigma2, beta, nu;
   double ib2;        // 1 / beta^2
+  double nugget;     // tau^2 added to the diagonal (0: none)
+  double radius;     // sphere radius of the great-circle metric
+  int metric;        // 0: Euclidean (x, y); 1: great circle between (longitude, latitude) in degrees
+  int pad2_;
   double logc;       // (1 - nu) ln 2 - lgamma(nu)
   double mu;         // nu - N, in [-1/2, 1/2]
   int N;             // round(nu)

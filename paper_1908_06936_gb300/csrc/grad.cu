@@ -253,8 +253,7 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const double* __restri
       const double w = (i == j) ? 1.0 : 2.0;
       const double cij = w * (ai * alpha[j] - sinv[i + j * lds]);
       double d0, d1, d2;
-      const double dx = xi - locs[2 * j], dy = yi - locs[2 * j + 1];
-      matern_derivs(G, sqrt(dx * dx + dy * dy), d0, d1, d2);
+      matern_derivs(G, sqrt(model_dist2(G.m, xi, yi, locs[2 * j], locs[2 * j + 1])), d0, d1, d2);
       acc0 = fma(cij, d0, acc0);
       acc1 = fma(cij, d1, acc1);
       acc2 = fma(cij, d2, acc2);
@@ -305,7 +304,7 @@ static double host_digamma(double x) {
 static cudaError_t launch_gradient(exa_ctx* c, const double* locs, int64_t n, int64_t npad, const double theta[3],
                                    const double* alpha, const double* sinv, double* partial, double* out) {
   GradParams G;
-  matern_params(theta, &G.m);
+  model_params(c, theta, &G.m);
   G.psi_nu = host_digamma(theta[2]);
   const long long t = (n + 63) / 64;
   const long long blocks = t * (t + 1) / 2;
@@ -430,9 +429,9 @@ __global__ void __launch_bounds__(256) deriv_matrix_kernel(const double* __restr
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     if (i < n && j < n) {
-      const double dx = locs[2 * i] - locs[2 * j], dy = locs[2 * i + 1] - locs[2 * j + 1];
       double d[3];
-      matern_derivs(G, sqrt(dx * dx + dy * dy), d[0], d[1], d[2]);
+      matern_derivs(G, sqrt(model_dist2(G.m, locs[2 * i], locs[2 * i + 1], locs[2 * j], locs[2 * j + 1])), d[0], d[1],
+                    d[2]);
       v = d[k];
     }
     D[i + j * npad] = v;
@@ -515,7 +514,7 @@ extern "C" exa_status exa_fisher(exa_ctx* c, const double* d_locs, const double 
   double* M = (double*)c->fs_m.p;
   cudaStream_t s = c->stream;
   MaternParams P;
-  matern_params(theta, &P);
+  model_params(c, theta, &P);
   const MaternTable* tab = nullptr;
   if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
   cudaError_t e;

@@ -56,11 +56,9 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
     if (i >= n || j >= n) {
       v = (i == j) ? 1.0 : 0.0;  // identity padding
     } else if (i == j) {
-      v = P.sigma2;
+      v = P.sigma2 + P.nugget;
     } else {
-      const double dx = xi - __ldg(locs + 2 * j);
-      const double dy = yi - __ldg(locs + 2 * j + 1);
-      const double r2 = dx * dx + dy * dy;
+      const double r2 = model_dist2(P, xi, yi, __ldg(locs + 2 * j), __ldg(locs + 2 * j + 1));
       v = tab ? matern_value_tab(P, tab, r2) : matern_value(P, sqrt(r2));
       vmax = fmax(vmax, fabs(v));
     }

@@ -342,7 +342,7 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   double* G = sigma_keep ? sigma_keep : A;
   unsigned long long* offmax = (unsigned long long*)c->mx_offmax.p;
   MaternParams Pm;
-  matern_params(theta, &Pm);
+  model_params(c, theta, &Pm);
   cudaStream_t s = c->stream;
   const MaternTable* tab = nullptr;
   if ((st = matern_table(c, Pm, &tab)) != EXA_OK) return st;

@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(256) krige_mean_kernel(const double* __restric
     __syncthreads();
     const int cnt = (int)((n - j0) < 256 ? (n - j0) : 256);
     for (int t = q; t < cnt; t += 4) {
-      const double dx = xi - sx[t], dy = yi - sy[t];
-      acc = fma(matern_value_tab(P, tab, dx * dx + dy * dy), sa[t], acc);
+      acc = fma(matern_value_tab(P, tab, model_dist2(P, xi, yi, sx[t], sy[t])), sa[t], acc);
     }
     __syncthreads();
   }
@@ -69,8 +68,7 @@ __global__ void __launch_bounds__(256) cross_cov_kernel(const double* __restrict
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     if (live && j < n) {
-      const double dx = obs[2 * j] - xi, dy = obs[2 * j + 1] - yi;
-      v = matern_value_tab(P, tab, dx * dx + dy * dy);
+      v = matern_value_tab(P, tab, model_dist2(P, obs[2 * j], obs[2 * j + 1], xi, yi));
     }
     C[j + c * npad] = v;
   }
@@ -129,7 +127,7 @@ extern "C" exa_status exa_predict(exa_ctx* c, const double* d_locs, const double
   }
   if (e != cudaSuccess) return cuda_err(c, e, "prediction solve");
   MaternParams P;
-  matern_params(theta, &P);
+  model_params(c, theta, &P);
   const MaternTable* tab = nullptr;
   if ((st = matern_table(c, P, &tab)) != EXA_OK) return st;
   {
