@@ -317,6 +317,48 @@ def configs_leg(args, ctx) -> dict:
     return out
 
 
+def mle_leg(args, ctx) -> dict:
+    """Maximum-likelihood fit of one field at n = 40,000 (200x200 jittered grid, theta0 = (1, 0.1, 0.5),
+    Z = L eps from the mixed-precision factor): bounded Nelder-Mead in log(theta) from the lower bounds
+    (the paper's start, Section III Example 2), every evaluation a mixed-precision log-likelihood; the
+    optimum is evaluated once more in FP64 for |dl|/|l| there."""
+    import math
+
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+    from paper_1908_06936_gb300.mle import fit_replicates_with
+
+    th0 = (1.0, 0.1, 0.5)
+    dl = torch.as_tensor(synth.jittered_grid(200, 6), device="cuda")
+    dz = ctx.simulate(dl, torch.as_tensor(synth.normals(40000, 6), device="cuda"), th0, exa.EXA_MIXED_TF32X3)
+    fails = [0]
+
+    def f(_r, t):
+        try:
+            return ctx.loglik(dl, dz, list(map(float, t)), exa.EXA_MIXED_TF32X3)
+        except exa.ExaError as e:
+            if e.status in (2, 6):  # not SPD / refinement stalled: -inf, the search steps away
+                fails[0] += 1
+                return -math.inf
+            raise
+
+    f(0, th0)  # warm-up (allocates)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = fit_replicates_with(f, 1, ftol=1e-5, xtol=1e-4, max_evals=args.mle_evals)
+    dt = time.perf_counter() - t0
+    th = [float(v) for v in res["theta"][0]]
+    lm = float(res["loglik"][0])
+    l64 = ctx.loglik(dl, dz, th, exa.EXA_FP64)
+    return {"workload": "n=40000 (200x200 jittered grid), Z = L eps at theta0 = (1, 0.1, 0.5); Nelder-Mead in "
+                        "log(theta) from the lower bounds; mixed-precision evaluations",
+            "evals": int(res["evals"][0]), "seconds": dt, "evals_per_s": int(res["evals"][0]) / dt,
+            "not_spd_or_stalled": fails[0], "theta_hat": th, "loglik_mixed": lm, "loglik_fp64_at_theta_hat": l64,
+            "rel_dl_at_theta_hat": abs(lm - l64) / abs(l64)}
+
+
 def batched_mle_leg(args) -> dict:
     """theta-hat distribution of the 256 config-5 replicates: every replicate fitted by its
     own bounded Nelder-Mead in log(theta), all advanced in lockstep by one CUDA-graph replay
@@ -449,6 +491,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         batched = batched_leg(args, ctx) if args.batched_steps > 0 else None
         configs = configs_leg(args, ctx) if args.configs else None
         batched_mle = batched_mle_leg(args) if args.batched_mle_evals > 0 else None
+        mle = mle_leg(args, ctx) if args.mle_evals > 0 else None
         # CPU oracle baseline on a bounded sample of the same field
         n_s = args.cpu_sample
         cs = oracle_sample(locs, z_host, n_s)
@@ -471,6 +514,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "batched": batched,
             "configs": configs,
             "batched_mle": batched_mle,
+            "mle_n40000": mle,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()} for st in stats],
             "cpu_baseline": cpu_baseline_entry(n, n_s, cs["seconds"], cs["threads"]),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -518,6 +562,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="graph replays of the 256-replicate mixed batch (0 skips the batched leg)")
     ap.add_argument("--configs", type=int, default=1, help="also time the n=1,600 and n=22,500 configurations (0 skips)")
+    ap.add_argument("--mle-evals", type=int, default=0,
+                    help="maximum-likelihood fit at n=40,000 with this many mixed evaluations at most (0 skips)")
     ap.add_argument("--batched-mle-evals", type=int, default=0,
                     help="fit theta for the 256 batched replicates with this many evaluations each (0 skips)")
     ap.add_argument("--batched-fp64-steps", type=int, default=1, help="timed FP64 runs of the same batch")

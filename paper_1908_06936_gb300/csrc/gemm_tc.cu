@@ -538,7 +538,6 @@ constexpr int A_BYTES = TM * KC * 2;   // 16 KB per slice
 constexpr int B_BYTES = TN * KC * 2;   // 4 KB per slice
 constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t IDESC = idesc(kFmtBF16, TM, TN);
 constexpr int GROUP_COLS = TN;          // one accumulator per slice-sum group
 constexpr int BUF_COLS = S * GROUP_COLS;
 constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a power of two
@@ -646,15 +645,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
 #pragma unroll
         for (int kk = 0; kk < KC / 16; ++kk) {  // K = 16 per instruction: advance 32 bytes
           const uint64_t o = (uint64_t)(kk * 2);
+          // The B slices lie one after another (slice t = rows [TN t, TN t + TN) of one
+          // SW128 tile) and group g = s + t sits at columns [TN g, TN g + TN), so one
+          // MMA of A slice s against B slices 0 .. S-1-s (N = TN (S - s)) adds every
+          // product of that slice to its group.  The first (s = 0, N = S TN) writes all
+          // groups; sums stay exact integers, so the order changes no bit.
+          const uint64_t bb = sdesc_sw128(sb + S * A_BYTES) + o;
 #pragma unroll
-          for (int gs = 0; gs < S; ++gs) {       // slice-sum group
-#pragma unroll
-            for (int s = 0; s <= gs; ++s) {
-              const int t2 = gs - s;
-              const uint64_t a = sdesc_sw128(sb + s * A_BYTES) + o;
-              const uint64_t bb = sdesc_sw128(sb + S * A_BYTES + t2 * B_BYTES) + o;
-              mma_bf16(d0 + gs * GROUP_COLS, a, bb, IDESC, (kc | kk | s) ? 1u : 0u);
-            }
+          for (int s = 0; s < S; ++s) {
+            const uint64_t a = sdesc_sw128(sb + s * A_BYTES) + o;
+            mma_bf16(d0 + s * GROUP_COLS, a, bb, idesc(kFmtBF16, TM, TN * (S - s)), (kc | kk | s) ? 1u : 0u);
           }
         }
         mma_commit(&empty[stage]);
