@@ -61,15 +61,16 @@ void matern_params(const double theta[3], MaternParams* p);
 // so that an entry costs no square root, division or exponential.  Segments follow the
 // binary exponent of s: octave [2^e, 2^(e+1)), e in [kTabE0, kTabE0 + kTabOct), split into
 // kTabSub equal pieces; on each, f is a degree-kTabDeg polynomial in t = (s - centre) /
-// half-width (Chebyshev interpolation, relative error far below 1e-15 at this width:
-// the pieces are 1/64 of an octave wide).  Below 2^kTabE0 (x < 1/16) and from
+// half-width (Chebyshev interpolation on pieces 1/64 of an octave wide: the truncation
+// error is below 1e-15 relative for x < 32 and about 1e-14 relative in the last octave,
+// 45 <= x < 64, where f < 1e-18).  Below 2^kTabE0 (x < 1/16) and from
 // 2^(kTabE0 + kTabOct) on (x >= 64) the exact routine applies.
 constexpr int kTabE0 = -8;
 constexpr int kTabOct = 20;
 constexpr int kTabSubBits = 6;
 constexpr int kTabSub = 1 << kTabSubBits;
 constexpr int kTabSeg = kTabOct * kTabSub;
-constexpr int kTabDeg = 10;
+constexpr int kTabDeg = 8;
 struct MaternTable {
   double mc[kTabSeg];                  // -centre / half-width
   double ih[kTabSeg];                  // 1 / half-width
@@ -96,10 +97,11 @@ struct DevStatus {
 // that a padded matrix factors as diag(L, I).
 // If offmax is non-null, offmax[d] receives (as the bits of a non-negative double)
 // the largest off-diagonal |Sigma_ij| over `panel`-wide tile pairs (I, J) with I - J = d.
-// With tab != nullptr the entries with x >= 2^kTabE0 come from the table.
+// With tab != nullptr the entries with x >= 2^kTabE0 come from the table.  With a2 != nullptr
+// every entry is stored at the same place in a2 as well (two copies for one evaluation).
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
                               double* a, int64_t ld, unsigned long long* offmax = nullptr,
-                              const MaternTable* tab = nullptr, int panel = 256);
+                              const MaternTable* tab = nullptr, int panel = 256, double* a2 = nullptr);
 // W (sub*nb square, row-major) <- block diagonal of `sub` inverted nb x nb tiles, zero elsewhere.
 cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w);
 

@@ -5,7 +5,7 @@
 // (Gamma values, Temme's Gamma_1/Gamma_2, reciprocal tables) for the exact
 // routine, and the device builds from it an interpolation table of
 // Sigma / sigma^2 in s = (r / beta)^2, so that most entries cost a squared
-// distance, a segment lookup on the bit pattern and a degree-10 polynomial.
+// distance, a segment lookup on the bit pattern and a degree-8 polynomial.
 #include <math.h>
 
 #include "bessel.cuh"
@@ -38,7 +38,8 @@ __device__ __forceinline__ void tri_decode(long long b, int& ti, int& tj) {
 __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restrict__ locs, int64_t n, int64_t npad,
                                                          const __grid_constant__ MaternParams P, double* __restrict__ a,
                                                          int64_t ld, unsigned long long* __restrict__ offmax,
-                                                         const MaternTable* __restrict__ tab, int oshift) {
+                                                         const MaternTable* __restrict__ tab, int oshift,
+                                                         double* __restrict__ a2) {
   int ti, tj;
   tri_decode(blockIdx.x, ti, tj);
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
       vmax = fmax(vmax, fabs(v));
     }
     a[i + j * ld] = v;
+    if (a2) a2[i + j * ld] = v;
   }
   }
   if (offmax) {
@@ -78,12 +80,13 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
 }
 
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
-                              double* a, int64_t ld, unsigned long long* offmax, const MaternTable* tab, int panel) {
+                              double* a, int64_t ld, unsigned long long* offmax, const MaternTable* tab, int panel,
+                              double* a2) {
   const int oshift = panel == 512 ? 3 : 2;  // 64-row generator tiles per panel tile: 2^oshift
   const long long t = (npad + 63) / 64;
   const long long blocks = t * (t + 1) / 2;
   if (blocks <= 0) return cudaSuccess;
-  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax, tab, oshift);
+  matern_gen_kernel<<<(unsigned)blocks, 256, 0, s>>>(locs, n, npad, p, a, ld, offmax, tab, oshift, a2);
   return cudaGetLastError();
 }
 

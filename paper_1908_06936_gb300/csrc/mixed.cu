@@ -349,10 +349,8 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
   cudaError_t e = cudaMemsetAsync(offmax, 0, (size_t)(T + 1) * sizeof(unsigned long long), s);
   if (e == cudaSuccess) {
     ProfScope ps(c, PK_GEN, 0.0, 4.0 * (double)npad * (double)(npad + 1));
-    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax, tab, kMixNB);
+    e = launch_matern_gen(s, d_locs, n, npad, Pm, G, npad, offmax, tab, kMixNB, sigma_keep ? A : nullptr);
   }
-  if (e == cudaSuccess && sigma_keep)
-    e = cudaMemcpyAsync(A, G, (size_t)npad * npad * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_err(c, e, "generation");
   cudaEventRecord(c->ev[1], s);
   int band = c->mixed_band;
