@@ -115,6 +115,15 @@ exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
  * runs on the others.  0 restores the default (16).                        */
 exa_status exa_ctx_set_lookahead(exa_ctx* ctx, int sms);
 
+/* Mixed precision: while the trailing matrix still has at least min_rows rows,
+ * panels are applied in pairs (the off-band TF32x3 update of the two panels
+ * accumulates in one pass, K = 1024, so each FP64 tile is read and written once
+ * per pair; band tiles keep one exact pass per panel) while the look-ahead
+ * stream factors the next two panels.  Needs CTA pairs (exa_ctx_set_tc_pairs)
+ * and at least four panels.  0 turns it off; a negative value restores the
+ * default (61440).  Results differ from the one-panel order only by rounding. */
+exa_status exa_ctx_set_panel_fusion(exa_ctx* ctx, int64_t min_rows);
+
 /* Message describing the last error on this context ("" if none).  The
  * string is owned by the context and valid until its next call.           */
 const char* exa_last_error(const exa_ctx* ctx);
@@ -220,7 +229,9 @@ exa_status exa_fisher(exa_ctx* ctx, const double* d_locs, const double theta[3],
  * with 256 x 256 tiles, tcgen05 .cta_group::2).  Shapes: m % 128 == 0 (256 for
  * T3_PAIR), k % 64 == 0, n % 128 == 0 (T3), n % 32 == 0 (OZ) or n % 256 == 0
  * (T3_PAIR), and k <= 512 (the digit sums of OZ stay below 2^24 up to
- * k = 512, so its accumulation is exact).                                    */
+ * k = 512, so its accumulation is exact); T3_PAIR takes k <= 1024, reducing
+ * columns 512.. as a second operand pair into the same accumulator (the
+ * two-panel pass of the factorisation).                                      */
 typedef enum { EXA_GEMM_T3 = 0, EXA_GEMM_OZ = 1, EXA_GEMM_T3_PAIR = 2 } exa_gemm_kind;
 exa_status exa_gemm_update(exa_ctx* ctx, exa_gemm_kind kind, int64_t m, int64_t n, int64_t k, const double* d_a,
                            const double* d_b, double* d_c, int64_t ldc, int store);

@@ -239,6 +239,12 @@ exa_status exa_ctx_set_lookahead(exa_ctx* c, int sms) {
   return EXA_OK;
 }
 
+exa_status exa_ctx_set_panel_fusion(exa_ctx* c, int64_t min_rows) {
+  if (!c) return EXA_ERR_ARG;
+  c->fuse_min_rows = min_rows < 0 ? -1 : min_rows;
+  return EXA_OK;
+}
+
 const char* exa_last_error(const exa_ctx* c) { return c ? c->err : "null context"; }
 
 int64_t exa_last_pivot(const exa_ctx* c) { return c ? c->last_pivot : -1; }

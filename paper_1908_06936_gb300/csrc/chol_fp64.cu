@@ -2,7 +2,8 @@
 // the tile decomposition of Section II-A, Fig. 1(a)).
 //
 // For tile column k (k0 = k nb):
-//   potrf_diag  : L_kk = chol(A_kk) and W_k = L_kk^-1, in shared memory (one CTA).
+//   potrf_diag  : L_kk = chol(A_kk) in shared memory (one CTA), then W_k = L_kk^-1
+//                 by independent row substitutions spread over several CTAs.
 //   trsm_panel  : L_ik = A_ik L_kk^-T = A_ik W_k^T for all rows below (DMMA GEMM),
 //                 written in place and to a row-major panel copy P.
 //   syrk_update : A_ij -= L_ik L_jk^T over the trailing lower triangle (DMMA GEMM).
@@ -113,25 +114,23 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
   }
 }
 
-// Blocked variant for nb = 64 / 128 (same outputs as potrf_diag_kernel).  On this
-// part FP64 instructions issue at ~1.6 per clock per SM, so the aim is to keep the
-// FP64 pipe busy with few block-wide barriers:
-//   factorisation: 16-wide panels factored by warp 0 (warp-level syncs only), then a
-//     rank-16 update of the trailing triangle by all warps (one barrier per panel);
-//   inverse: block columns J from the right, in place (the order of LAPACK's blocked
-//     trtri): W_JJ = L_JJ^-1 by warp 0, then W(J+1:, J) = -W(J+1:, J+1:) L(J+1:, J) W_JJ
-//     from the already inverted trailing block and the still original panel.
+// Blocked variant for nb = 64 / 128 (the factor and log-determinant part of
+// potrf_diag_kernel; the inverse follows in trtri_rows_kernel).  On this part FP64
+// instructions issue at ~1.6 per clock per SM, so one SM needs ~0.2 ms for the
+// nb^3/3 multiply-adds of a 128 tile: the aim is to keep its FP64 pipe busy with few
+// block-wide barriers.  16-wide panels are factored by warp 0 (warp-level syncs
+// only), then a rank-16 update of the trailing triangle by all warps (one barrier per
+// panel).
 constexpr int kPotrfPW = 16;
 
 template <int NB>
 __global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restrict__ a, int64_t ld, int64_t k0,
                                                                  double* __restrict__ w_out,
                                                                  double* __restrict__ logdet_part, DevStatus* st) {
-  constexpr int PW = kPotrfPW, sd = NB + 1, NP = NB / PW;
+  constexpr int PW = kPotrfPW, sd = NB + 1;
   extern __shared__ double sm[];
   double* S = sm;                // NB x sd, element (i, j) at S[i * sd + j]
-  double* Y = sm + NB * sd;      // (NB - PW) x PW scratch of the inverse
-  double* lg = Y + (NB - PW) * PW;  // NB logs
+  double* lg = sm + NB * sd;     // NB logs
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int k = (int)(k0 / NB);
@@ -213,66 +212,82 @@ __global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restr
     for (int i = 0; i < NB; ++i) s += lg[i];
     logdet_part[k] = s;
   }
-  // ---- inverse, block columns from the right ----
-  for (int J = NP - 1; J >= 0; --J) {
-    const int j0 = J * PW, r0 = j0 + PW, m = NB - r0;
-    // W_JJ = L_JJ^-1 in place (16 x 16, column by column from the right), warp 0
-    if (warp == 0) {
-      for (int j = j0 + PW - 1; j >= j0; --j) {
-        const double wjj = 1.0 / S[j * sd + j];
-        double t = 0.0;
-        const int i = j + 1 + lane;  // rows of this 16-block below j
-        if (i < j0 + PW)
-          for (int l = j + 1; l <= i; ++l) t = fma(S[i * sd + l], S[l * sd + j], t);
-        __syncwarp();
-        if (i < j0 + PW) S[i * sd + j] = -t * wjj;
-        if (lane == 0) S[j * sd + j] = wjj;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (m == 0) continue;
-    // Y = W(r0:, r0:) L(r0:, j0:j0+PW)   (W lower triangular, already inverted)
-    for (int e = tid; e < m * PW; e += 256) {
-      const int i = r0 + e / PW, c = e % PW;
-      double s0 = 0.0, s1 = 0.0;
-      int t = r0;
-      for (; t + 1 <= i; t += 2) {
-        s0 = fma(S[i * sd + t], S[t * sd + j0 + c], s0);
-        s1 = fma(S[i * sd + t + 1], S[(t + 1) * sd + j0 + c], s1);
-      }
-      if (t <= i) s0 = fma(S[i * sd + t], S[t * sd + j0 + c], s0);
-      Y[(i - r0) * PW + c] = s0 + s1;
-    }
-    __syncthreads();
-    // W(r0:, J) = -Y W_JJ  (W_JJ lower triangular: column c takes rows u >= c)
-    for (int e = tid; e < m * PW; e += 256) {
-      const int ir = e / PW, c = e % PW;
-      double s = 0.0;
-      for (int u = c; u < PW; ++u) s = fma(Y[ir * PW + u], S[(j0 + u) * sd + j0 + c], s);
-      S[(r0 + ir) * sd + j0 + c] = -s;
-    }
-    __syncthreads();
+}
+
+// W_k = L_kk^-1 (row-major, zeros above the diagonal) for the NB x NB diagonal tile that
+// potrf_diag_blocked_kernel has just factored in place.  Row i of W solves x L = e_i
+// (the left-inverse equations W L = I that LAPACK's trtri satisfies) by substitution
+// from the right: x_i = 1 / L_ii, then for l = i-1 .. 0,
+// x_l = -(sum_{m > l} x_m L_ml) / L_ll.  Rows are independent, so warp w of CTA c takes
+// row c + gridDim.x w (short and long rows mix within every CTA).  The lane holding
+// column l broadcasts x_l, then every column j < l accumulates x_l L_lj (columns at
+// or above l read the zeros stored above the diagonal, or L_ll once x_l is final).
+// The sums are compensated (each product split exactly with an FMA, each addition
+// with Knuth's TwoSum, the errors carried in a second word: the Dot2 scheme of Ogita,
+// Rump and Oishi, SIAM J. Sci. Comput. 26, 2005), so W is as accurate as if the sums
+// were formed in twice the precision: its rounding errors, which the condition number
+// of an ill-conditioned tile would magnify, stay out of the panel solve A W^T.
+template <int NB>
+__global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restrict__ a, int64_t ld, int64_t k0,
+                                                         double* __restrict__ w_out, const DevStatus* st) {
+  constexpr int sd = NB + 1, Q = NB / 32;
+  extern __shared__ double sm[];
+  double* S = sm;  // S[l * sd + j] = L(l, j) for l >= j, 0 above
+  if (failed(st)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* A = a + k0 + k0 * ld;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int l = idx % NB, j = idx / NB;
+    S[l * sd + j] = (l >= j) ? A[l + (int64_t)j * ld] : 0.0;
   }
-  double* W = w_out + (int64_t)k * NB * NB;
-  for (int idx = tid; idx < NB * NB; idx += 256) {
-    const int r = idx / NB, c = idx % NB;
-    W[idx] = (c <= r) ? S[r * sd + c] : 0.0;
+  __syncthreads();
+  double* W = w_out + (k0 / NB) * (int64_t)NB * NB;
+  const int nw = blockDim.x >> 5;
+  for (int i = blockIdx.x + gridDim.x * warp; i < NB; i += gridDim.x * nw) {
+    // hi[q] + lo[q] = sum_{m > l} x_m L_mj for column j = lane + 32 q
+    double hi[Q], lo[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) hi[q] = lo[q] = 0.0;
+    for (int j = i + 1 + lane; j < NB; j += 32) W[(int64_t)i * NB + j] = 0.0;
+    for (int l = i; l >= 0; --l) {
+      const int ql = l >> 5;
+      double h = hi[0], e = lo[0];
+#pragma unroll
+      for (int q = 1; q < Q; ++q)
+        if (q == ql) h = hi[q], e = lo[q];
+      const double sum = __shfl_sync(0xffffffffu, h + e, l & 31);
+      const double xl = (l == i) ? 1.0 / S[l * sd + l] : -sum / S[l * sd + l];
+      if (lane == (l & 31)) W[(int64_t)i * NB + l] = xl;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q <= ql) {
+          const double lv = S[l * sd + lane + 32 * q];
+          const double p = xl * lv, pe = fma(xl, lv, -p);  // p + pe = xl lv exactly
+          const double t = hi[q] + p, bv = t - hi[q];      // TwoSum(hi, p)
+          const double te = (hi[q] - (t - bv)) + (p - bv);
+          hi[q] = t;
+          lo[q] += te + pe;
+        }
+    }
   }
 }
 
 template <int NB>
 static cudaError_t launch_potrf_blocked(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_out,
                                         double* logdet_part, DevStatus* st) {
-  const size_t smem = (size_t)(NB * (NB + 1) + (NB - kPotrfPW) * kPotrfPW + NB) * sizeof(double);
+  const size_t smem = (size_t)(NB * (NB + 1) + NB) * sizeof(double);  // potrf: S and the logs; trtri: S
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(potrf_diag_blocked_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(trtri_rows_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   potrf_diag_blocked_kernel<NB><<<1, 256, smem, s>>>(a, ld, k0, w_out, logdet_part, st);
+  // one row per warp: NB / 8 CTAs of 8 warps
+  trtri_rows_kernel<NB><<<NB / 8, 256, smem, s>>>(a, ld, k0, w_out, st);
   return cudaGetLastError();
 }
 

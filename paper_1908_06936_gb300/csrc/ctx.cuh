@@ -31,6 +31,7 @@ struct exa_ctx {
   size_t held_bytes = 0;
   int tile_nb = 128;     // FP64 tile
   int lookahead_sms = 0;  // SMs reserved for the look-ahead stream (0: default)
+  int64_t fuse_min_rows = -1;  // two-panel trailing passes down to this many rows (0: off, < 0: default)
   int mixed_band = 0;    // exact-product band (256-wide tiles); 0: from Sigma; < 0: all tiles
   int64_t last_pivot = -1;
   char err[512];
@@ -44,10 +45,12 @@ struct exa_ctx {
   exa::DevBuf table;        // per-theta Matérn interpolation table + its node values
   // mixed precision
   exa::DevBuf mx_sigma;     // FP64 copy of Sigma for the refinement residual
-  exa::DevBuf mx_split;     // split-precision panel operands (A role), two buffers by step parity
+  exa::DevBuf mx_split;     // split-precision panel operands (A role), four buffers by panel index mod 4
   exa::DevBuf mx_split2;
+  exa::DevBuf mx_split3;
+  exa::DevBuf mx_split4;
   exa::DevBuf mx_split_b;   // split-precision operands (B role: inverse diagonal block / test B)
-  exa::SplitOperand sp_a, sp_a2, sp_b;
+  exa::SplitOperand sp_a, sp_a2, sp_a3, sp_a4, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
   exa::DevBuf mx_w2;        // inverse of the panel-wide diagonal block (row-major)
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)

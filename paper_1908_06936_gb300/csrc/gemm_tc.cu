@@ -330,15 +330,21 @@ __device__ __forceinline__ bool decode_pair_tile(const GemmArgs& g, long long t,
 // with eA + eB <= far_thr, the single product hi * hi (relative error ~2^-10 per term) has
 // an absolute error no larger than the three-product form makes on blocks of size 1; the
 // caller sets far_thr from the scale of Sigma.  Producer and MMA issuer decide alike.
-__device__ __forceinline__ bool far_tile(const GemmArgs& g, int bi, int bj) {
-  if (g.far_thr == INT_MIN || !g.ea_blk || !g.eb_blk) return false;
-  const int ea = g.ea_blk[g.a_row0 / t3p::TILE + bi], eb = g.eb_blk[g.b_row0 / t3p::TILE + bj];
+// src 1 asks about the second operand pair (g.K2 > 0), whose rows start at a2_row0 / b2_row0.
+__device__ __forceinline__ bool far_tile(const GemmArgs& g, int bi, int bj, int src) {
+  const int* eab = src ? g.ea2_blk : g.ea_blk;
+  const int* ebb = src ? g.eb2_blk : g.eb_blk;
+  if (g.far_thr == INT_MIN || !eab || !ebb) return false;
+  const int ea = eab[(src ? g.a2_row0 : g.a_row0) / t3p::TILE + bi];
+  const int eb = ebb[(src ? g.b2_row0 : g.b_row0) / t3p::TILE + bj];
   return (long long)ea + (long long)eb <= (long long)g.far_thr;
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     gemm_t3_pair_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                         const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                        const __grid_constant__ CUtensorMap tA2_hi, const __grid_constant__ CUtensorMap tA2_lo,
+                        const __grid_constant__ CUtensorMap tB2_hi, const __grid_constant__ CUtensorMap tB2_lo,
                         const __grid_constant__ GemmArgs g) {
   using namespace t3p;
   extern __shared__ uint8_t smem_raw[];
@@ -374,7 +380,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
   cluster_sync();  // both CTAs' barriers are initialised before any remote arrival or copy
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int kchunks = g.K / KC;
+  // chunks [0, kc1) reduce over the first operand pair, [kc1, kchunks) over the second
+  const int kc1 = g.K / KC;
+  const int kchunks = kc1 + g.K2 / KC;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
@@ -382,6 +390,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     prefetch_tmap(&tA_lo);
     prefetch_tmap(&tB_hi);
     prefetch_tmap(&tB_lo);
+    if (g.K2 > 0) {
+      prefetch_tmap(&tA2_hi);
+      prefetch_tmap(&tA2_lo);
+      prefetch_tmap(&tB2_hi);
+      prefetch_tmap(&tB2_lo);
+    }
     int stage = 0;
     uint32_t phase = 0;
     int last_par[STAGES];
@@ -389,22 +403,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     for (long long t = pair; t < g.ntiles && !*abort; t += npairs) {
       int bi, bj;
       if (!decode_pair_tile(g, t, bi, bj)) continue;
-      const int ya = g.a_row0 + bi * TILE + (int)rank * HALF_ROWS;
-      const int yb = g.b_row0 + bj * TILE + (int)rank * HALF_ROWS;
-      const bool one = far_tile(g, bi, bj);
+      const int ya1 = g.a_row0 + bi * TILE + (int)rank * HALF_ROWS;
+      const int yb1 = g.b_row0 + bj * TILE + (int)rank * HALF_ROWS;
+      const int ya2 = g.a2_row0 + bi * TILE + (int)rank * HALF_ROWS;
+      const int yb2 = g.b2_row0 + bj * TILE + (int)rank * HALF_ROWS;
+      const bool one1 = far_tile(g, bi, bj, 0);
+      const bool one2 = g.K2 > 0 && far_tile(g, bi, bj, 1);
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
           *abort = 1;
           record_timeout(g.st, 51);
           break;
         }
+        const bool second = kc >= kc1;
+        const bool one = second ? one2 : one1;
+        const int kx = (second ? kc - kc1 : kc) * KC;
+        const int ya = second ? ya2 : ya1, yb = second ? yb2 : yb1;
         uint8_t* sb = smem + stage * STAGE_BYTES;
         if (leader) mbar_expect_tx(&full[stage], (one ? 1 : 2) * STAGE_BYTES);
         const uint32_t fl = map_to_rank(smem_u32(&full[stage]), 0);
-        tma_load_2d_pair(sb, &tA_hi, fl, kc * KC, ya);
-        if (!one) tma_load_2d_pair(sb + OP_BYTES, &tA_lo, fl, kc * KC, ya);
-        tma_load_2d_pair(sb + 2 * OP_BYTES, &tB_hi, fl, kc * KC, yb);
-        if (!one) tma_load_2d_pair(sb + 3 * OP_BYTES, &tB_lo, fl, kc * KC, yb);
+        tma_load_2d_pair(sb, second ? &tA2_hi : &tA_hi, fl, kx, ya);
+        if (!one) tma_load_2d_pair(sb + OP_BYTES, second ? &tA2_lo : &tA_lo, fl, kx, ya);
+        tma_load_2d_pair(sb + 2 * OP_BYTES, second ? &tB2_hi : &tB_hi, fl, kx, yb);
+        if (!one) tma_load_2d_pair(sb + 3 * OP_BYTES, second ? &tB2_lo : &tB_lo, fl, kx, yb);
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -436,7 +457,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       }
       fence_after();
       const uint32_t d = tmem + b * TILE;
-      const bool one = far_tile(g, bi, bj);
+      const bool one1 = far_tile(g, bi, bj, 0);
+      const bool one2 = g.K2 > 0 && far_tile(g, bi, bj, 1);
       bool ok = true;
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&full[stage], phase, abort)) {
@@ -446,6 +468,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
           break;
         }
         fence_after();
+        const bool one = kc >= kc1 ? one2 : one1;
         const uint32_t sb = smem_u32(smem + stage * STAGE_BYTES);
         const uint64_t ahi = sdesc_sw128(sb), alo = sdesc_sw128(sb + OP_BYTES);
         const uint64_t bhi = sdesc_sw128(sb + 2 * OP_BYTES), blo = sdesc_sw128(sb + 3 * OP_BYTES);
@@ -964,7 +987,9 @@ cudaError_t launch_row_exp_blockmax(cudaStream_t s, SplitOperand& op, int64_t ro
 }
 
 cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
-                                int max_ctas) {
+                                int max_ctas, const SplitOperand* A2, const SplitOperand* B2) {
+  if (g.K2 > 0 && (!A2 || !B2)) return cudaErrorInvalidValue;
+  if (g.K2 <= 0) A2 = &A, B2 = &B;
   if (g.ntiles <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -977,7 +1002,8 @@ cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const Spl
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
   const long long pairs = g.ntiles < cap / 2 ? g.ntiles : cap / 2;
   if (pairs < 1) return cudaErrorInvalidValue;
-  gemm_t3_pair_kernel<<<(unsigned)(2 * pairs), kGemmThreads, t3p::SMEM_BYTES, s>>>(A.t_hi, A.t_lo, B.t_hi, B.t_lo, g);
+  gemm_t3_pair_kernel<<<(unsigned)(2 * pairs), kGemmThreads, t3p::SMEM_BYTES, s>>>(
+      A.t_hi, A.t_lo, B.t_hi, B.t_lo, A2->t_hi, A2->t_lo, B2->t_hi, B2->t_lo, g);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,13 @@ struct GemmArgs {
   const int* ea_blk;          // per 256-row block maximum exponent of A
   const int* eb_blk;          // per 256-row block maximum exponent of B
   int far_thr;
+  // T3 on CTA pairs only: a second operand pair (A2, B2) reduced into the same tile after
+  // the first, K2 more columns (0: none), rows from a2_row0 / b2_row0, with its own
+  // block exponents for the far-tile test.
+  int K2;
+  int a2_row0, b2_row0;
+  const int* ea2_blk;
+  const int* eb2_blk;
   DevStatus* st;
 };
 
@@ -73,8 +80,10 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
                            int max_ctas = 0);
 // T3 on CTA pairs, 256 x 256 tiles (kEnumFull with g.nt = n / 256, or kEnumLowerOffBand with
 // g.nt = tile rows of 256); no lower_mask.  Uses pairs of SMs (max_ctas rounded down to even).
+// With g.K2 > 0 each tile also takes -= A2 B2^T (K2 columns) in the same accumulator.
 cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
-                                int max_ctas = 0);
+                                int max_ctas = 0, const SplitOperand* A2 = nullptr,
+                                const SplitOperand* B2 = nullptr);
 int tc_num_sms();
 
 }  // namespace exa

@@ -17,6 +17,7 @@ constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
 constexpr double kIrQuadTol = 1e-10;  // refinement stops once |z^T d| <= kIrQuadTol |z^T x|
 constexpr int kLookaheadSMs = 16;         // SMs left to the look-ahead stream during a trailing update
+constexpr int64_t kFuseMinRows = 61440;   // two panels per trailing pass down to this many rows
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 
@@ -165,16 +166,68 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
   return EXA_OK;
 }
 
-// Trailing update by panel k restricted to block columns [j_lo, j_hi) (in panel
-// units relative to the trailing region r0 = (k+1) NB): band tiles exact, the
-// rest TF32x3.  `ctas` caps the persistent grids.
-static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const SplitOperand& sp, bool next_column,
-                                  int ctas) {
+// Block column j (> p) from panel p, whose split `sp` holds rows from (p + 1) NB: the
+// first band+1 tile rows from the diagonal exact (OZ), the rest TF32x3.  `ctas` caps
+// the persistent grids.
+static exa_status column_update(const MixStep& M, cudaStream_t s, int p, int j, const SplitOperand& sp, int ctas) {
+  exa_ctx* c = M.c;
+  const int NB = kMixNB;
+  const int64_t cj = (int64_t)j * NB;
+  const int off = (int)(cj - (int64_t)(p + 1) * NB);  // operand row of global row cj
+  const int64_t m = M.npad - cj;
+  if (m <= 0) return EXA_OK;
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.C = M.a;
+  g.ldc = M.ld;
+  g.K = NB;
+  g.panel = NB;
+  g.st = c->d_status;
+  g.store = 0;
+  g.band = M.band;
+  g.enum_mode = kEnumFull;
+  const int64_t rb = m < (int64_t)(M.band + 1) * NB ? m : (int64_t)(M.band + 1) * NB;
+  g.lower_mask = 1;
+  g.c_row0 = cj;
+  g.c_col0 = cj;
+  g.a_row0 = off;
+  g.b_row0 = off;
+  g.nt = NB / 32;
+  g.ntiles = (rb / 128) * g.nt;
+  cudaError_t e;
+  {
+    ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 16.0 * (double)rb * NB, 1, s, true);
+    e = launch_gemm_oz(s, sp, sp, g, ctas);
+  }
+  if (e == cudaSuccess && m > rb) {
+    g.lower_mask = 0;
+    g.c_row0 = cj + rb;
+    g.a_row0 = off + (int)rb;
+    g.nt = NB / 128;
+    g.ntiles = ((m - rb) / 128) * g.nt;
+    ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 16.0 * (double)(m - rb) * NB, 1, s, true);
+    e = launch_gemm_t3(s, sp, sp, g, ctas);
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "column update launch");
+  return EXA_OK;
+}
+
+// The trailing lower triangle from row/column j0 NB on, from panel p (split `sp`, rows
+// from (p + 1) NB) and, when sp2 is given, panel p + 1 as well (rows from (p + 2) NB).
+// Band tiles (I - J <= band) take the exact OZ products, one pass per panel (its digit
+// sums stay exact only up to K = 512); the others take TF32x3 on CTA pairs with both
+// panels reduced into one accumulator (K = 2 NB), so every such tile of the FP64
+// matrix is read and written once for the two panels.
+static exa_status region_update(const MixStep& M, cudaStream_t s, int p, int j0, const SplitOperand& sp,
+                                const SplitOperand* sp2, int ctas) {
   exa_ctx* c = M.c;
   const int NB = kMixNB, SUB = kMixNB / kMixSub;
-  const int64_t r0 = (int64_t)(k + 1) * NB;
-  const int64_t m = M.npad - r0;
+  const int64_t cs = (int64_t)j0 * NB;
+  const int64_t m2 = M.npad - cs;
+  if (m2 <= 0) return EXA_OK;
+  const int off1 = (int)(cs - (int64_t)(p + 1) * NB), off2 = (int)(cs - (int64_t)(p + 2) * NB);
   const int band = M.band;
+  const double npan = sp2 ? 2.0 : 1.0;
   GemmArgs g;
   memset(&g, 0, sizeof(g));
   g.C = M.a;
@@ -184,91 +237,82 @@ static exa_status trailing_update(const MixStep& M, cudaStream_t s, int k, const
   g.st = c->d_status;
   g.store = 0;
   g.band = band;
+  g.lower_mask = 1;
+  g.c_row0 = g.c_col0 = cs;
+  g.a_row0 = g.b_row0 = off1;
+  const long long t128 = m2 / 128;
+  g.enum_mode = kEnumLowerOffBand;
   cudaError_t e = cudaSuccess;
-  if (next_column) {
-    // block column k+1: rows of its first band+1 tile rows exact, the rest TF32x3
-    const int64_t rb = m < (int64_t)(band + 1) * NB ? m : (int64_t)(band + 1) * NB;
-    g.enum_mode = kEnumFull;
-    g.lower_mask = 1;
-    g.c_row0 = r0;
-    g.c_col0 = r0;
-    g.nt = NB / 32;
-    g.ntiles = (rb / 128) * g.nt;
-    {
-      ProfScope ps(c, PK_GEMM_OZ, 2.0 * (double)rb * NB * NB, 16.0 * (double)rb * NB, 1, s, true);
-      e = launch_gemm_oz(s, sp, sp, g, ctas);
-    }
-    if (e == cudaSuccess && m > rb) {
-      g.lower_mask = 0;
-      g.c_row0 = r0 + rb;
-      g.a_row0 = (int)rb;
-      g.nt = NB / 128;
-      g.ntiles = ((m - rb) / 128) * g.nt;
-      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 16.0 * (double)(m - rb) * NB, 1, s, true);
-      e = launch_gemm_t3(s, sp, sp, g, ctas);
-    }
-  } else {
-    // block columns >= k+2: the trailing matrix from r0 + NB, operand rows offset by NB
-    const int64_t m2 = m - NB;
-    if (m2 <= 0) return EXA_OK;
-    g.lower_mask = 1;
-    g.c_row0 = g.c_col0 = r0 + NB;
-    g.a_row0 = g.b_row0 = NB;
-    const long long t128 = m2 / 128;
-    g.enum_mode = kEnumLowerOffBand;
+  long long t3_tiles = 0;
+  for (long long bi = 0; bi < t128; ++bi) {
+    const long long lim = (long long)SUB * (bi / SUB - band);
+    if (lim > 0) t3_tiles += lim;
+  }
+  if (t3_tiles > 0) {
+    ProfScope ps(c, PK_GEMM_T3, npan * 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
+                 16.0 * 128.0 * 128.0 * (double)t3_tiles + npan * 8.0 * (double)m2 * NB, 1, s, true);
     if (c->tc_pairs) {  // 256-tiles on CTA pairs (m2 is a multiple of the 512 panel)
-      const long long t256 = m2 / 256, sp2 = kRasterSuper / 2;
-      const long long ts = (t256 + sp2 - 1) / sp2;
+      const long long t256 = m2 / 256, sp2s = kRasterSuper / 2;
+      const long long ts = (t256 + sp2s - 1) / sp2s;
       g.nt = (int)t256;
-      g.ntiles = ts * (ts + 1) / 2 * sp2 * sp2;
+      g.ntiles = ts * (ts + 1) / 2 * sp2s * sp2s;
+      g.ea_blk = g.eb_blk = sp.exb;
+      g.far_thr = M.far_thr;
+      if (sp2) {
+        g.K2 = NB;
+        g.a2_row0 = g.b2_row0 = off2;
+        g.ea2_blk = g.eb2_blk = sp2->exb;
+      }
+      e = launch_gemm_t3_pair(s, sp, sp, g, ctas, sp2, sp2);
+      g.K2 = 0;
+      g.ea_blk = g.eb_blk = g.ea2_blk = g.eb2_blk = nullptr;
+      g.far_thr = INT_MIN;
     } else {
       const long long ts = (t128 + kRasterSuper - 1) / kRasterSuper;  // supertile rows
       g.nt = (int)t128;
       g.ntiles = ts * (ts + 1) / 2 * kRasterSuper * kRasterSuper;
-    }
-    long long t3_tiles = 0;
-    for (long long bi = 0; bi < t128; ++bi) {
-      const long long lim = (long long)SUB * (bi / SUB - band);
-      if (lim > 0) t3_tiles += lim;
-    }
-    if (t3_tiles > 0) {
-      ProfScope ps(c, PK_GEMM_T3, 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
-                   16.0 * 128.0 * 128.0 * (double)t3_tiles + 8.0 * (double)m2 * NB, 1, s, true);
-      if (c->tc_pairs) {
-        g.ea_blk = g.eb_blk = sp.exb;
-        g.far_thr = M.far_thr;
-        e = launch_gemm_t3_pair(s, sp, sp, g, ctas);
-        g.ea_blk = g.eb_blk = nullptr;
-        g.far_thr = INT_MIN;
-      } else {
-        e = launch_gemm_t3(s, sp, sp, g, ctas);
+      e = launch_gemm_t3(s, sp, sp, g, ctas);
+      if (e == cudaSuccess && sp2) {
+        g.a_row0 = g.b_row0 = off2;
+        e = launch_gemm_t3(s, *sp2, *sp2, g, ctas);
       }
     }
-    if (e == cudaSuccess) {
-      const long long tr = m2 / NB;
-      long long pairs = 0;
-      for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
-      const long long per_pair = (long long)(NB / 128) * (NB / 32);
-      g.enum_mode = kEnumBand;
-      g.ntiles = pairs * per_pair;
-      long long skipped = 0;
-      for (int h = 0; h < NB / 128; ++h)
-        for (int q = 0; q < NB / 32; ++q)
-          if ((long long)q * 32 > (long long)h * 128 + 127) ++skipped;
-      const double oz_tiles = (double)pairs * per_pair - (double)skipped * (double)tr;
-      ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles, 1, s, true);
-      e = launch_gemm_oz(s, sp, sp, g, ctas);
-    }
+  }
+  // band tiles, one exact pass per panel
+  const long long tr = m2 / NB;
+  long long pairs = 0;
+  for (long long I = 0; I < tr; ++I) pairs += (I < band ? I : band) + 1;
+  const long long per_pair = (long long)(NB / 128) * (NB / 32);
+  long long skipped = 0;
+  for (int h = 0; h < NB / 128; ++h)
+    for (int q = 0; q < NB / 32; ++q)
+      if ((long long)q * 32 > (long long)h * 128 + 127) ++skipped;
+  const double oz_tiles = (double)pairs * per_pair - (double)skipped * (double)tr;
+  g.enum_mode = kEnumBand;
+  g.ntiles = pairs * per_pair;
+  for (int q = 0; q < (sp2 ? 2 : 1) && e == cudaSuccess; ++q) {
+    g.a_row0 = g.b_row0 = q ? off2 : off1;
+    ProfScope ps(c, PK_GEMM_OZ, 2.0 * 128.0 * 32.0 * NB * oz_tiles, 16.0 * 128.0 * 32.0 * oz_tiles, 1, s, true);
+    e = launch_gemm_oz(s, q ? *sp2 : sp, q ? *sp2 : sp, g, ctas);
   }
   if (e != cudaSuccess) return cuda_err(c, e, "trailing update launch");
   return EXA_OK;
 }
 
-// Mixed-precision tiled Cholesky with one step of look-ahead: while the main
-// stream applies panel k to block columns >= k+2 (on all but kLookaheadSMs
-// SMs), the side stream factors diagonal block k+1, inverts it and runs the
-// TRSM of panel k+1 on the reserved SMs.  Panel splits alternate between two
-// buffers so the side stream never overwrites operands still in use.
+// Mixed-precision tiled Cholesky with look-ahead on a side stream (kLookaheadSMs SMs
+// reserved for it during the big trailing updates).  Panel splits rotate through four
+// buffers (panel k in buffer k mod 4), so the side stream never overwrites operands
+// still in use.
+//
+// While the trailing matrix is large (at least c->fuse_min_rows rows), panels go in
+// pairs: with panels k and k+1 factored and every column >= k+2 holding the updates
+// of the panels before k, the main stream brings columns k+2 and k+3 up to date
+// (what the side stream needs next), the side stream factors panel k+2, applies it
+// to column k+3 and factors panel k+3, and meanwhile the main stream applies panels
+// k and k+1 together to every column >= k+4 (one read and write of each FP64 tile for
+// the two panels).  Then, and for every panel when fusion is off, one panel at a
+// time: column k+1 first, the side stream factors panel k+1 while the main stream
+// applies panel k to the columns >= k+2.
 exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_prec prec, int band, int far_thr) {
   const int NB = kMixNB, nb = kMixSub;
   const int T = (int)(npad / NB);
@@ -280,8 +324,14 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
     return st;
   if ((st = ensure(c, c->panel, (size_t)(NB * nb + nb * nb) * sizeof(double), "panel")) != EXA_OK) return st;
   if ((st = ensure(c, c->logdet_part, (size_t)T128 * sizeof(double), "log-det partials")) != EXA_OK) return st;
-  if ((st = ensure_split(c, c->sp_a, c->mx_split, npad, NB, true, true)) != EXA_OK) return st;
-  if ((st = ensure_split(c, c->sp_a2, c->mx_split2, npad, NB, true, true)) != EXA_OK) return st;
+  const int64_t fuse_rows = c->fuse_min_rows < 0 ? kFuseMinRows : c->fuse_min_rows;
+  // the fused phase runs while rows (k + 4) NB .. npad number at least fuse_rows, from k = 0
+  const bool fuse = fuse_rows > 0 && c->tc_pairs && T >= 4 && npad - 4 * (int64_t)NB >= fuse_rows;
+  SplitOperand* buf[4] = {&c->sp_a, &c->sp_a2, &c->sp_a3, &c->sp_a4};
+  DevBuf* mem[4] = {&c->mx_split, &c->mx_split2, &c->mx_split3, &c->mx_split4};
+  for (int i = 0; i < (fuse ? 4 : 2); ++i)
+    if ((st = ensure_split(c, *buf[i], *mem[i], npad, NB, true, true)) != EXA_OK) return st;
+  const int nbuf = fuse ? 4 : 2;
   if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure(c, c->mx_w2, (size_t)NB * NB * sizeof(double), "diagonal block inverse")) != EXA_OK) return st;
   if (!c->side) {
@@ -297,22 +347,43 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   const int sms = tc_num_sms();
   const int side_ctas = c->lookahead_sms > 0 ? c->lookahead_sms : kLookaheadSMs;
   const int main_ctas = sms - side_ctas;
-  SplitOperand* buf[2] = {&c->sp_a, &c->sp_a2};
+  auto B = [&](int p) -> SplitOperand& { return *buf[p % nbuf]; };
   // panel 0 on the main stream
-  if ((st = panel_factor(M, ms, 0, *buf[0], 0)) != EXA_OK) return st;
-  for (int k = 0; k + 1 < T; ++k) {
-    SplitOperand& cur = *buf[k & 1];
+  if ((st = panel_factor(M, ms, 0, B(0), 0)) != EXA_OK) return st;
+  int k = 0;
+  if (fuse) {
+    // panel 1 on the main stream as well
+    if ((st = column_update(M, ms, 0, 1, B(0), 0)) != EXA_OK) return st;
+    if ((st = panel_factor(M, ms, 1, B(1), 0)) != EXA_OK) return st;
+    for (; k + 3 < T && npad - (int64_t)(k + 4) * NB >= fuse_rows; k += 2) {
+      for (int j = k + 2; j <= k + 3; ++j)
+        for (int p = k; p <= k + 1; ++p)
+          if ((st = column_update(M, ms, p, j, B(p), 0)) != EXA_OK) return st;
+      cudaEventRecord(c->la_ev[0], ms);
+      cudaStreamWaitEvent(ss, c->la_ev[0], 0);
+      if ((st = panel_factor(M, ss, k + 2, B(k + 2), side_ctas)) != EXA_OK) return st;
+      if ((st = column_update(M, ss, k + 2, k + 3, B(k + 2), side_ctas)) != EXA_OK) return st;
+      if ((st = panel_factor(M, ss, k + 3, B(k + 3), side_ctas)) != EXA_OK) return st;
+      cudaEventRecord(c->la_ev[1], ss);
+      if ((st = region_update(M, ms, k, k + 4, B(k), &B(k + 1), main_ctas)) != EXA_OK) return st;
+      cudaStreamWaitEvent(ms, c->la_ev[1], 0);
+    }
+    // hand over to the one-panel loop: panel k applied to every column >= k+2 leaves
+    // panel k+1 factored and the columns >= k+2 holding every panel before k+1
+    if ((st = region_update(M, ms, k, k + 2, B(k), nullptr, 0)) != EXA_OK) return st;
+    ++k;
+  }
+  for (; k + 1 < T; ++k) {
     // block column k+1 first (everything the side stream needs), on the whole GPU
-    if ((st = trailing_update(M, ms, k, cur, true, 0)) != EXA_OK) return st;
+    if ((st = column_update(M, ms, k, k + 1, B(k), 0)) != EXA_OK) return st;
     cudaEventRecord(c->la_ev[0], ms);
     cudaStreamWaitEvent(ss, c->la_ev[0], 0);
-    if ((st = panel_factor(M, ss, k + 1, *buf[(k + 1) & 1], side_ctas)) != EXA_OK) return st;
+    if ((st = panel_factor(M, ss, k + 1, B(k + 1), side_ctas)) != EXA_OK) return st;
     cudaEventRecord(c->la_ev[1], ss);
     // the rest of the trailing matrix on the remaining SMs
-    if ((st = trailing_update(M, ms, k, cur, false, main_ctas)) != EXA_OK) return st;
+    if ((st = region_update(M, ms, k, k + 2, B(k), nullptr, main_ctas)) != EXA_OK) return st;
     cudaStreamWaitEvent(ms, c->la_ev[1], 0);
   }
-  if (T == 1) return EXA_OK;
   return EXA_OK;
 }
 
@@ -521,21 +592,30 @@ extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m,
   const bool oz = (kind == EXA_GEMM_OZ);
   const bool pair = (kind == EXA_GEMM_T3_PAIR);
   if (kind != EXA_GEMM_T3 && kind != EXA_GEMM_OZ && !pair) return set_err(c, EXA_ERR_ARG, "unknown gemm kind");
-  if (m % (pair ? 256 : 128) || k % 64 || k > kSplitMaxK || (oz ? (n % 32) : (n % (pair ? 256 : 128))))
+  // T3 on pairs reduces up to two operand pairs per pass: k up to 2 kSplitMaxK
+  const int64_t kmax = pair ? 2 * (int64_t)kSplitMaxK : kSplitMaxK;
+  if (m % (pair ? 256 : 128) || k % 64 || k > kmax || (oz ? (n % 32) : (n % (pair ? 256 : 128))))
     return set_err(c, EXA_ERR_ARG, "gemm shape m=%lld n=%lld k=%lld not supported", (long long)m, (long long)n,
                    (long long)k);
+  const int k1 = (int)(k < kSplitMaxK ? k : kSplitMaxK), k2 = (int)(k - k1);
   exa_status st;
-  if ((st = ensure_split(c, c->sp_a, c->mx_split, m, (int)k, !oz, oz)) != EXA_OK) return st;
-  if ((st = ensure_split(c, c->sp_b, c->mx_split_b, n, (int)k, !oz, oz)) != EXA_OK) return st;
+  if ((st = ensure_split(c, c->sp_a, c->mx_split, m, k1, !oz, oz)) != EXA_OK) return st;
+  if ((st = ensure_split(c, c->sp_b, c->mx_split_b, n, k1, !oz, oz)) != EXA_OK) return st;
+  if (k2 > 0) {
+    if ((st = ensure_split(c, c->sp_a2, c->mx_split2, m, k2, true, false)) != EXA_OK) return st;
+    if ((st = ensure_split(c, c->sp_a3, c->mx_split3, n, k2, true, false)) != EXA_OK) return st;
+  }
   if ((st = reset_status(c)) != EXA_OK) return st;
-  cudaError_t e = launch_split_rows(c->stream, d_a, k, 1, (int)m, (int)k, c->sp_a, 0);
-  if (e == cudaSuccess) e = launch_split_rows(c->stream, d_b, k, 1, (int)n, (int)k, c->sp_b, 0);
+  cudaError_t e = launch_split_rows(c->stream, d_a, k, 1, (int)m, k1, c->sp_a, 0);
+  if (e == cudaSuccess) e = launch_split_rows(c->stream, d_b, k, 1, (int)n, k1, c->sp_b, 0);
+  if (e == cudaSuccess && k2 > 0) e = launch_split_rows(c->stream, d_a + k1, k, 1, (int)m, k2, c->sp_a2, 0);
+  if (e == cudaSuccess && k2 > 0) e = launch_split_rows(c->stream, d_b + k1, k, 1, (int)n, k2, c->sp_a3, 0);
   if (e != cudaSuccess) return cuda_err(c, e, "split launch");
   GemmArgs g;
   memset(&g, 0, sizeof(g));
   g.C = d_c;
   g.ldc = ldc;
-  g.K = (int)k;
+  g.K = k1;
   g.enum_mode = kEnumFull;
   g.store = store ? 1 : 0;
   g.st = c->d_status;
@@ -546,7 +626,9 @@ extern "C" exa_status exa_gemm_update(exa_ctx* c, exa_gemm_kind kind, int64_t m,
   } else if (pair) {
     g.nt = (int)(n / 256);
     g.ntiles = (m / 256) * (n / 256);
-    e = launch_gemm_t3_pair(c->stream, c->sp_a, c->sp_b, g);
+    g.K2 = k2;
+    e = launch_gemm_t3_pair(c->stream, c->sp_a, c->sp_b, g, 0, k2 > 0 ? &c->sp_a2 : nullptr,
+                            k2 > 0 ? &c->sp_a3 : nullptr);
   } else {
     g.nt = (int)(n / 128);
     g.ntiles = (m / 128) * (n / 128);

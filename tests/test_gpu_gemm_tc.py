@@ -108,3 +108,36 @@ def test_t3_pair_product(ctx, m, n, k, store):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
     single = run(ctx, exa.EXA_GEMM_T3, A, B, C0, store)
     assert np.all(np.abs(got - single) <= 2.0 ** -22 * (np.abs(A) @ np.abs(B).T) + 1e-300)
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 576), (512, 768, 1024), (768, 512, 768)])
+@pytest.mark.parametrize("store", [0, 1])
+def test_t3_pair_two_operand_pairs(ctx, m, n, k, store):
+    # k > 512 on CTA pairs: columns 512.. are a second operand pair reduced into the same
+    # accumulator (the two-panel pass of the factorisation); same three-product bound, and
+    # within the sum of two such bounds of two separate passes (the FP32 partial sums
+    # round differently when 1024 terms share one accumulator)
+    import paper_1908_06936_gb300 as exa
+
+    A, B = operands(m, n, k, seed=7 * m + n + k, spread=2)
+    C0 = np.random.default_rng(5).standard_normal((m, n))
+    got = run(ctx, exa.EXA_GEMM_T3_PAIR, A, B, C0, store)
+    ref = A @ B.T if store else C0 - A @ B.T
+    bound = 2.0 ** -19 * (np.abs(A) @ np.abs(B).T) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+    first = run(ctx, exa.EXA_GEMM_T3_PAIR, np.ascontiguousarray(A[:, :512]), np.ascontiguousarray(B[:, :512]), C0,
+                store)
+    two = run(ctx, exa.EXA_GEMM_T3_PAIR, np.ascontiguousarray(A[:, 512:]), np.ascontiguousarray(B[:, 512:]),
+              first if not store else np.zeros_like(C0), 0 if not store else 1)
+    two = two if not store else first + two
+    assert np.all(np.abs(got - two) <= 2.0 ** -18 * (np.abs(A) @ np.abs(B).T) + 1e-300)
+
+
+def test_t3_pair_k_limit(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    c = torch.zeros(256 * 256, dtype=torch.float64, device="cuda")
+    for kind, k in ((exa.EXA_GEMM_T3_PAIR, 1088), (exa.EXA_GEMM_T3, 576), (exa.EXA_GEMM_OZ, 576)):
+        a = torch.zeros(256 * k, dtype=torch.float64, device="cuda")
+        assert exa.exa_gemm_update(ctx.handle, kind, 256, 256, k, a, a, c, 256, 0) == exa.EXA_ERR_ARG

@@ -192,3 +192,37 @@ def test_far_tiles_single_product_keeps_accuracy(ctx):
     print("far %.3e three %.3e" % (abs(far - l64) / abs(l64), abs(three - l64) / abs(l64)))
     assert abs(far - l64) <= 1e-6 * abs(l64)
     assert abs(far - three) <= 1e-7 * abs(l64)
+
+
+@pytest.mark.parametrize("m,theta,min_rows", [(50, (1.0, 0.1, 0.5), 1), (72, (1.0, 0.05, 1.0), 1),
+                                              (100, (1.0, 0.03, 1.0), 1), (100, (1.0, 0.03, 1.0), 4096),
+                                              (64, (1.5, 0.2, 1.5), 1)])
+def test_two_panel_passes_match_one_panel_order(ctx, m, theta, min_rows):
+    # panels applied in pairs (one K = 1024 TF32x3 pass per pair off the band, the side
+    # stream factoring two panels ahead) and one at a time differ only in the rounding of
+    # the FP32 partial sums.  n = 2,500 has five panels (one pair, then the hand-over);
+    # min_rows = 4096 at n = 10,000 switches to the one-panel order midway.
+    import paper_1908_06936_gb300 as exa
+
+    locs = synth.jittered_grid(m, m + 1)
+    dl, dz = to_dev(locs), to_dev(synth.normals(m * m, m + 1))
+    exa.exa_ctx_set_panel_fusion(ctx.handle, min_rows)
+    try:
+        fused = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+        exa.exa_ctx_set_panel_fusion(ctx.handle, 0)
+        single = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+    finally:
+        exa.exa_ctx_set_panel_fusion(ctx.handle, -1)
+    l64 = ctx.loglik(dl, dz, theta, exa.EXA_FP64)
+    print("fused %.3e one-panel %.3e" % (abs(fused["loglik"] - l64) / abs(l64), abs(single["loglik"] - l64) / abs(l64)))
+    assert abs(fused["loglik"] - l64) <= 1e-6 * abs(l64)
+    assert abs(fused["loglik"] - single["loglik"]) <= 1e-7 * abs(l64)
+    assert fused["exact_band"] == single["exact_band"]
+
+
+def test_panel_fusion_setting(ctx):
+    import paper_1908_06936_gb300 as exa
+
+    assert exa.exa_ctx_set_panel_fusion(ctx.handle, 12345) == exa.EXA_OK
+    assert exa.exa_ctx_set_panel_fusion(ctx.handle, -7) == exa.EXA_OK
+    assert exa.exa_ctx_set_panel_fusion(0, 1) == exa.EXA_ERR_ARG
