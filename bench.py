@@ -405,6 +405,21 @@ def batched_mle_leg(args) -> dict:
                               "loglik_oracle": float(ref["loglik"][i])} for i, r in enumerate(small)]}
 
 
+def aggregate_over_ranks(ms_total: float, units_per_rank: float, world: int, device=None) -> tuple[float, float]:
+    """Whole-job timing of N independent replicas: the slowest rank's timed region (max over
+    ranks, an all-reduce on the default process group when world > 1) and the throughput of
+    all ranks' units over that time, units per second.  Returns (ms_max, value)."""
+    import torch
+
+    t = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
 def run_ours(args, rank: int, world: int) -> dict | None:
     import numpy as np
     import torch
@@ -446,11 +461,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     clk = clocks.stop()
     stats = exa.exa_profile_read(ctx.handle, reset=1)
     exa.exa_profile_enable(ctx.handle, 0)
-    t = torch.tensor([ms_total], device="cuda")
-    if dist:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max, value = aggregate_over_ranks(ms_total, args.steps, world, device="cuda")
     launches = int(sum(st["launches"] for st in stats))
 
     # end to end through the C ABI: pinned host inputs copied in every step, result read back
