@@ -392,6 +392,23 @@ __device__ __forceinline__ bool ptrsv_wait(const int* f, volatile int* abort, lo
   return true;
 }
 
+// Warm L2 with what the next step of a CTA reads first, while it waits for the step's
+// input block: the 128 x 128 tile at rows r0.. and columns c0.. (column-major, ld), and
+// with w != nullptr the 128 x 128 inverse w (row-major, contiguous).  prefetch.global.L2
+// takes one 128-byte line per instruction and never faults on these in-bounds lines.
+__device__ __forceinline__ void ptrsv_prefetch(const PTrsvArgs& g, int64_t r0, int64_t c0, const double* w) {
+  const double* tile = g.a + r0 + c0 * g.ld;
+  for (int li = threadIdx.x; li < kPNB * 8; li += blockDim.x) {  // 8 lines per 128-row column
+    const double* p = tile + (li & 7) * 16 + (int64_t)(li >> 3) * g.ld;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
+  if (w)
+    for (int li = threadIdx.x; li < kPNB * kPNB / 16; li += blockDim.x) {
+      const double* p = w + li * 16;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+}
+
 __device__ __forceinline__ void ptrsv_fail(const PTrsvArgs& g, int site) {
   if (atomicExch(g.abort, 1) == 0 && atomicExch(&g.st->timeout, 1) == 0) g.st->timeout_where = site;
 }
@@ -449,6 +466,7 @@ __global__ void __launch_bounds__(256) trsv_fwd_persistent_kernel(PTrsvArgs g) {
     // this CTA's first block below k (blocks b with b % G == me); none now means none later
     int b = k + 1 + ((me - (k + 1)) % G + G) % G;
     if (b >= g.T) break;
+    ptrsv_prefetch(g, (int64_t)b * kPNB, k0, b == k + 1 ? g.w + (int64_t)(k + 1) * kPNB * kPNB : nullptr);
     if (k % G != me) {
       if (tid == 0) {
         ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
@@ -533,6 +551,7 @@ __global__ void __launch_bounds__(256) trsv_bwd_persistent_kernel(PTrsvArgs g) {
     // this CTA's first block above k, nearest first; none now means none later
     int i = k - 1 - ((k - 1 - me) % G + G) % G;
     if (i < 0) break;
+    ptrsv_prefetch(g, (int64_t)i * kPNB, k0, i == k - 1 ? g.w + (int64_t)(k - 1) * kPNB * kPNB : nullptr);
     if (k % G != me) {
       if (tid == 0) {
         ok = ptrsv_wait(&g.flags[k], g.abort, g.spin);
