@@ -125,7 +125,6 @@ constexpr int kPotrfPW = 16;
 
 template <int NB>
 __global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restrict__ a, int64_t ld, int64_t k0,
-                                                                 double* __restrict__ w_out,
                                                                  double* __restrict__ logdet_part, DevStatus* st) {
   constexpr int PW = kPotrfPW, sd = NB + 1;
   extern __shared__ double sm[];
@@ -285,7 +284,7 @@ static cudaError_t launch_potrf_blocked(cudaStream_t s, double* a, int64_t ld, i
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  potrf_diag_blocked_kernel<NB><<<1, 256, smem, s>>>(a, ld, k0, w_out, logdet_part, st);
+  potrf_diag_blocked_kernel<NB><<<1, 256, smem, s>>>(a, ld, k0, logdet_part, st);
   // one row per warp: NB / 8 CTAs of 8 warps
   trtri_rows_kernel<NB><<<NB / 8, 256, smem, s>>>(a, ld, k0, w_out, st);
   return cudaGetLastError();
