@@ -50,15 +50,17 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision tiled Cholesky (panel width 256).  For tile column k:
-//   1. FP64 factorisation of the 256 x 256 diagonal block as two 128 sub-tiles
-//      (POTRF, TRSM, SYRK, POTRF on DMMA), then its inverse
-//      W = [W00 0; -W11 L10 W00  W11] (two small DMMA products).
+// Mixed-precision tiled Cholesky (panel width kMixNB = 512).  For tile column k:
+//   1. FP64 factorisation of the 512 x 512 diagonal block as four 128 sub-tiles
+//      (POTRF with the sub-tile inverse, TRSM and SYRK within the block on DMMA),
+//      then its inverse W, block row by block row from the sub-tile inverses:
+//      W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj (small DMMA products).
 //   2. Panel TRSM  L_ik = A_ik W^T on the tensor cores: the first `band` tile
 //      rows with the exact OZ products, the rest with T3.
 //   3. Trailing update A_ij -= L_ik L_jk^T: tiles with I - J <= band (the
 //      diagonal tile and its neighbours, where the Schur complement cancels
-//      most) with OZ, all others with T3.  Storage stays FP64 throughout.
+//      most) with OZ, all others with T3 (far tiles with one product).  Storage
+//      stays FP64 throughout.
 // ---------------------------------------------------------------------------
 struct MixStep {
   exa_ctx* c;
