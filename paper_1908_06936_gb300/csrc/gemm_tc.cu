@@ -10,10 +10,11 @@
 //    accumulated in FP32 in TMEM (~22 significant bits per product).
 //  * OZ (band tiles, where the Schur complement cancels most): each row is scaled
 //    by a power of two 2^e_r so that |a| <= 1 and cut into S = 5 signed 7-bit
-//    integer digits held exactly in BF16, a = 2^e_r sum_s d_s 2^{-7(s+1)}.  Digit
-//    products are integers of at most 14 bits; with K <= 256 every partial sum
-//    of one slice-sum group g = s + t stays below 2^24, so FP32 accumulation in
-//    TMEM is exact.  The 15 products with g <= 4 go to five accumulators that
+//    integer digits held exactly in BF16, a = 2^e_r sum_s d_s 2^{-7(s+1)}
+//    (|d_0| <= 128, |d_s| <= 64 after it).  A group g = s + t sums at most two
+//    products with a leading digit (<= 2^13, or 2^14 for g = 0) and g - 1 others
+//    (<= 2^12), at most 7 * 2^12 per k; with K <= 512 every partial sum stays
+//    below 2^24, so FP32 accumulation in TMEM is exact.  The 15 products with g <= 4 go to five accumulators that
 //    the epilogue combines in FP64 (error ~2^-35 of the row maxima).
 //
 // Both kernels are persistent and warp-specialised: warp 0 issues TMA loads,

@@ -27,7 +27,7 @@ struct GemmArgs {
   int64_t ldc;
   int64_t c_row0, c_col0;     // output origin
   int a_row0, b_row0;         // operand row origins
-  int K;                      // reduction length (T3: % 32, OZ: % 64, <= 256 for OZ)
+  int K;                      // reduction length (T3: % 32, OZ: % 64 and <= 512, its exact-sum limit)
   int enum_mode;              // kEnum*
   int nt;                     // tiles along N (kEnumFull); tile rows (kEnumLowerOffBand)
   int band;                   // band width in panel tiles (kEnumLowerOffBand / kEnumBand)
