@@ -171,7 +171,7 @@ void oracle_matern_grad(const double theta[3], double r, double out[3]) {
   out[2] = s * (-ORACLE_LN2 - oracle_digamma(nu) + log(x)) + pref * oracle_dbesselk_dnu_scaled(nu, x);
 }
 
-/* Model options (the paper's dmetric and nugget):
+/* Model options (the paper's dmetric of Section III, Example 1, and the nugget of Section V):
  *   metric 0: Euclidean distance between (x, y) pairs;
  *   metric 1: great-circle distance (haversine form, the reference the paper cites
  *             for dmetric = great_circle) between (longitude, latitude) pairs in
