@@ -36,3 +36,20 @@ def test_binding_wraps_every_declared_symbol():
 
     missing = [n for n in declared_functions() if not callable(getattr(exa, n, None))]
     assert not missing, missing
+
+
+def test_setters_reject_a_null_context():
+    # host-side argument checks: every option setter returns EXA_ERR_ARG for a NULL context
+    # without touching the device
+    import paper_1908_06936_gb300 as exa
+
+    calls = [
+        lambda: exa.exa_ctx_set_mixed_band(0, 1),
+        lambda: exa.exa_ctx_set_lookahead(0, 16),
+        lambda: exa.exa_ctx_set_panel_fusion(0, 1),
+        lambda: exa.exa_ctx_set_tc_pairs(0, 1),
+        lambda: exa.exa_ctx_set_far_tile_margin(0, 16),
+        lambda: exa.exa_ctx_set_model(0, 0.0, 0, 0.0),
+    ]
+    for call in calls:
+        assert call() == exa.EXA_ERR_ARG
