@@ -150,31 +150,51 @@ def make_inputs(m: int, seed: int):
     return locs, dl, dz, np.ascontiguousarray(dz.cpu().numpy())
 
 
+# DRAM traffic of the dominant kernel relative to its algorithmic bytes, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launch's algorithmic bytes) of the same
+# kernel on a C larger than L2; the per-launch traffic of the bench is this ratio times the
+# average algorithmic bytes of its timed launches.  Keyed by kernel class; the capture and its
+# command are summarised in profiles/gemm_t3_pair_c16384.md.
+TRAFFIC_RATIO = {}
+
+
 def roofline(stats: list, pk: dict) -> dict:
+    """Roofline of the dominant kernel class (largest event-timed device time): algorithmic
+    flops (or bytes) of the timed launch groups over their event-timed duration."""
     dom = max(stats, key=lambda s: s["ms"]) if stats else None
     if not dom or dom["timed_launches"] == 0 or dom["ms"] <= 0:
         return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
-    avg_ms = dom["ms"] / dom["timed_launches"]
+    nt = dom["timed_launches"]
+    avg_ms = dom["ms"] / nt
     name = dom["name"]
-    if name in ("gemm_tf32x3_tc",):
-        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+    extra = {}
+    if name in ("gemm_tf32x3_tc", "gemm_tf32x3_pair"):
+        ach = dom["timed_flops"] / (dom["ms"] * 1e-3) / 1e12
         peak = pk["tf32"]
-        bound, unit, note = "tensor", "TFLOP/s", "useful flops vs tf32 peak (3 tf32 MMAs per useful product)"
+        bound, unit, note = "tensor", "TFLOP/s", ("useful flops (n^3/3 accounting) vs the tf32 dense peak; three tf32 "
+                                                  "MMAs per useful product (far tiles one), so the ceiling is ~1/3")
+        extra["frac_of_three_product_ceiling"] = 3.0 * ach / peak
     elif name in ("gemm_ozaki_tc",):
-        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+        ach = dom["timed_flops"] / (dom["ms"] * 1e-3) / 1e12
         peak = pk["bf16"]
         bound, unit, note = "tensor", "TFLOP/s", "useful flops vs bf16 peak (15 bf16 MMAs per useful product)"
     elif name in ("syrk_update_fp64", "trsm_panel_fp64", "potrf_diag_fp64", "dgemm_small_fp64"):
-        ach = dom["flops"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e12
+        ach = dom["timed_flops"] / (dom["ms"] * 1e-3) / 1e12
         peak = pk["fp64"]
         bound, unit, note = "tensor", "TFLOP/s", "FP64 DMMA"
     else:
-        ach = dom["bytes"] / dom["timed_launches"] / (avg_ms * 1e-3) / 1e9
+        ach = dom["timed_bytes"] / (dom["ms"] * 1e-3) / 1e9
         peak = pk["hbm_gbs"]
         bound, unit, note = "hbm", "GB/s", "algorithmic bytes vs measured copy bandwidth"
-    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": None, "avg_launch_ms": avg_ms, "launches": dom["timed_launches"],
-            "peak_source": pk["source"], "note": note}
+    traffic = None
+    if name in TRAFFIC_RATIO:
+        traffic = TRAFFIC_RATIO[name] * dom["timed_bytes"] / nt
+        extra["algorithmic_bytes_per_launch"] = dom["timed_bytes"] / nt
+    out = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+           "traffic": traffic, "avg_launch_ms": avg_ms, "launches": nt,
+           "flops_per_launch": dom["timed_flops"] / nt, "peak_source": pk["source"], "note": note}
+    out.update(extra)
+    return out
 
 
 def batched_leg(args, ctx) -> dict:

@@ -63,9 +63,11 @@ typedef enum {
  * and the triangular solves are FP64.                                      */
 typedef enum {
   EXA_FP64 = 0,          /* all tiles FP64 (the exact variant, Fig. 1(a)) */
-  EXA_MIXED_TF32X3 = 1,  /* off-diagonal TRSM/GEMM/SYRK products as 3 TF32 tensor-core products, FP32 accumulate */
-  EXA_MIXED_BF16X3 = 2,  /* off-diagonal TRSM/GEMM/SYRK products as 3 BF16 tensor-core products, FP32 accumulate */
-  EXA_MIXED_FP32 = 3     /* batched form only: off-diagonal tile products in FP32 (FFMA), FP32 accumulate per tile */
+  EXA_MIXED_FP32 = 1,    /* batched form only: off-diagonal tile products in FP32 (FFMA), FP32 accumulate per
+                            tile; exa_loglik refuses it (EXA_ERR_ARG): on one large field FP32 FFMA runs at a
+                            third of the TF32x3 tensor-core rate with fewer significant bits */
+  EXA_MIXED_BF16X3 = 2,  /* refused (EXA_ERR_ARG): 3 BF16 products keep 16 significant bits, |dl|/|l| ~ 3e-4 */
+  EXA_MIXED_TF32X3 = 3   /* off-diagonal TRSM/GEMM/SYRK products as 3 TF32 tensor-core products, FP32 accumulate */
 } exa_prec;
 
 typedef struct exa_ctx exa_ctx;
@@ -266,14 +268,18 @@ exa_status exa_ctx_set_far_tile_margin(exa_ctx* ctx, int bits);
 
 /* Kernel accounting.  Launch counts and the algorithmic flops / bytes of every
  * kernel class are always accumulated; with profiling enabled each launch is
- * also bracketed by CUDA events on the context stream (adds ~2 us per launch). */
+ * also bracketed by CUDA events on the stream it runs on (adds ~2 us per
+ * launch).  The rate of a class is timed_flops / ms (or timed_bytes / ms):
+ * both count the same timed launch groups.                                  */
 typedef struct {
   char name[32];          /* kernel class */
   int64_t launches;       /* kernels launched */
   int64_t timed_launches; /* launch groups timed with events */
-  double ms;              /* summed device time of the timed launches */
-  double flops;           /* algorithmic flops (useful multiply-adds x 2) */
-  double bytes;           /* algorithmic DRAM bytes (compulsory reads + writes) */
+  double ms;              /* summed device time of the timed launch groups */
+  double flops;           /* algorithmic flops of every launch (useful multiply-adds x 2) */
+  double bytes;           /* algorithmic DRAM bytes of every launch (compulsory reads + writes) */
+  double timed_flops;     /* algorithmic flops of the timed launch groups only */
+  double timed_bytes;     /* algorithmic bytes of the timed launch groups only */
 } exa_kernel_stat;
 exa_status exa_profile_enable(exa_ctx* ctx, int on);
 /* Copy up to max per-class records into out (host); returns how many.  Waits

@@ -63,7 +63,6 @@ def _load():
                 "oracle_loglik": (_I64, [_I64, _PD, _PD, _PD, _PD]),
                 "oracle_loglik_grad": (_I64, [_I64, _PD, _PD, _PD, _PD, _PD]),
                 "oracle_simulate": (_I64, [_I64, _PD, _PD, _PD, _PD]),
-                "oracle_factor": (_I64, [_I64, _PD, _PD, _PD]),
                 "oracle_predict": (_I64, [_I64, _PD, _PD, _PD, _I64, _PD, _PD, _PD]),
                 "oracle_fisher": (_I64, [_I64, _PD, _PD, _PD]),
                 "oracle_set_model": (None, [_D, ctypes.c_int, _D]),

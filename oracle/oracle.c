@@ -405,16 +405,6 @@ int64_t oracle_simulate(int64_t n, const double* locs, const double theta[3], co
   return info;
 }
 
-/* Cholesky factor of Sigma(theta) returned to the caller (row-major, lower
- * triangle; the strict upper triangle is zeroed).                          */
-int64_t oracle_factor(int64_t n, const double* locs, const double theta[3], double* L) {
-  oracle_covariance(n, locs, theta, L);
-  const int64_t info = oracle_cholesky(n, L);
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = i + 1; j < n; ++j) L[i * n + j] = 0.0;
-  return info;
-}
-
 /* Spatial prediction (kriging, the conditional expectation the paper's
  * exact_predict computes for the sea-surface-temperature tutorial of Section IV)
  * at m new locations from n observed ones, zero mean:

@@ -24,7 +24,7 @@ __all__ = [
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
-EXA_FP64, EXA_MIXED_TF32X3, EXA_MIXED_BF16X3, EXA_MIXED_FP32 = 0, 1, 2, 3
+EXA_FP64, EXA_MIXED_FP32, EXA_MIXED_BF16X3, EXA_MIXED_TF32X3 = 0, 1, 2, 3
 EXA_GEMM_T3, EXA_GEMM_OZ, EXA_GEMM_T3_PAIR = 0, 1, 2
 PREC = {"fp64": EXA_FP64, "tf32x3": EXA_MIXED_TF32X3, "bf16x3": EXA_MIXED_BF16X3, "fp32": EXA_MIXED_FP32}
 _STATUS = {0: "EXA_OK", 1: "EXA_ERR_ARG", 2: "EXA_ERR_NOT_SPD", 3: "EXA_ERR_NOMEM", 4: "EXA_ERR_CUDA",
@@ -43,7 +43,8 @@ class ExaError(RuntimeError):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
-                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("timed_flops", ctypes.c_double), ("timed_bytes", ctypes.c_double)]
 
 
 class ExaResult(ctypes.Structure):
@@ -325,7 +326,8 @@ def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
     buf = (KernelStat * 32)()
     k = lib().exa_profile_read(_P(ctx), buf, 32, int(reset))
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "timed_launches": buf[i].timed_launches,
-             "ms": buf[i].ms, "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(k)]
+             "ms": buf[i].ms, "flops": buf[i].flops, "bytes": buf[i].bytes, "timed_flops": buf[i].timed_flops,
+             "timed_bytes": buf[i].timed_bytes} for i in range(k)]
 
 
 def exa_ctx_set_batched(ctx: int, tile_nb: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,

@@ -1,8 +1,10 @@
 """torch.autograd.Function over the library's log-likelihood and its hand-written adjoint.
 
-forward  : exa_loglik (no gradient needed) or exa_loglik_grad (theta requires grad),
-           which returns l and dl/dtheta from one factorisation (the FP64 adjoint:
-           1/2 a^T dSigma a - 1/2 tr(Sigma^-1 dSigma), a = Sigma^-1 z).
+forward  : exa_loglik (no gradient needed) or exa_loglik_grad (a gradient of theta is
+           needed), which returns l and dl/dtheta from one factorisation (the adjoint
+           1/2 a^T dSigma a - 1/2 tr(Sigma^-1 dSigma), a = Sigma^-1 z), both in the
+           caller's precision `prec`; a precision the library's gradient does not offer
+           raises instead of being replaced by another.
 backward : grad_output * dl/dtheta.
 Only the three covariance parameters are differentiable; locations and data are
 treated as constants.
@@ -18,8 +20,8 @@ class MaternLogLik(torch.autograd.Function):
     @staticmethod
     def forward(fctx, theta, locs, z, exa_ctx, prec):
         th = [float(v) for v in theta.detach().cpu().tolist()]
-        if theta.requires_grad:
-            l, g = exa_ctx.loglik_grad(locs, z, th, EXA_FP64)
+        if fctx.needs_input_grad[0]:
+            l, g = exa_ctx.loglik_grad(locs, z, th, prec)
             fctx.save_for_backward(torch.tensor(g, dtype=theta.dtype, device=theta.device))
         else:
             l = exa_ctx.loglik(locs, z, th, prec)

@@ -845,11 +845,11 @@ struct CholArgs {
 template <int NB, int MODE>
 static exa_status launch_chol(exa_ctx* c, cudaStream_t s, const CholArgs& a) {
   const size_t smem = Tile<NB>::smem(MODE);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(batched_chol_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  static PerDeviceOnce attr_once;
+  const cudaError_t ea = attr_once([&] {
+    return cudaFuncSetAttribute(batched_chol_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (ea != cudaSuccess) return cuda_err(c, ea, "batched kernel attribute");
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

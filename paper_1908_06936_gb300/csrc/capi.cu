@@ -301,8 +301,17 @@ exa_status exa_loglik_ex(exa_ctx* c, const double* d_locs, const double* d_z, co
   if (n < 1 || !d_locs || !d_z) return set_err(c, EXA_ERR_ARG, "bad n or NULL device pointer");
   exa_status st = check_theta(c, theta);
   if (st != EXA_OK) return st;
-  if (prec == EXA_FP64) return loglik_fp64(c, d_locs, d_z, theta, n, out, nullptr);
-  if (prec == EXA_MIXED_TF32X3 || prec == EXA_MIXED_BF16X3) return loglik_mixed(c, d_locs, d_z, theta, n, prec, out);
+  if (prec == EXA_FP64 || prec == EXA_MIXED_TF32X3 || prec == EXA_MIXED_BF16X3) {
+    st = prec == EXA_FP64 ? loglik_fp64(c, d_locs, d_z, theta, n, out, nullptr)
+                          : loglik_mixed(c, d_locs, d_z, theta, n, prec, out);
+    prof_fold(c);  // the evaluation ended with a synchronise: recycle its timing events
+    return st;
+  }
+  if (prec == EXA_MIXED_FP32)
+    return set_err(c, EXA_ERR_ARG,
+                   "EXA_MIXED_FP32 is offered by exa_loglik_batched only: on one field its FP32 FFMA tile "
+                   "products run at a third of the TF32x3 tensor-core rate with fewer significant bits; use "
+                   "EXA_MIXED_TF32X3");
   return set_err(c, EXA_ERR_ARG, "unknown precision %d", (int)prec);
 }
 

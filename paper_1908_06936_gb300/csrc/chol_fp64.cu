@@ -275,15 +275,15 @@ template <int NB>
 static cudaError_t launch_potrf_blocked(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_out,
                                         double* logdet_part, DevStatus* st) {
   const size_t smem = (size_t)(NB * (NB + 1) + NB) * sizeof(double);  // potrf: S and the logs; trtri: S
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(potrf_diag_blocked_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([&] {
+    cudaError_t r = cudaFuncSetAttribute(potrf_diag_blocked_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(trtri_rows_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(trtri_rows_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   potrf_diag_blocked_kernel<NB><<<1, 256, smem, s>>>(a, ld, k0, logdet_part, st);
   // one row per warp: NB / 8 CTAs of 8 warps
   trtri_rows_kernel<NB><<<NB / 8, 256, smem, s>>>(a, ld, k0, w_out, st);
@@ -295,13 +295,12 @@ cudaError_t launch_potrf_diag(cudaStream_t s, double* a, int64_t ld, int64_t k0,
   if (nb == 128) return launch_potrf_blocked<128>(s, a, ld, k0, w_out, logdet_part, st);
   if (nb == 64) return launch_potrf_blocked<64>(s, a, ld, k0, w_out, logdet_part, st);
   const size_t smem = (size_t)(nb * (nb + 1) + nb) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((128 * 129 + 128) * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([] {
+    return cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((128 * 129 + 128) * sizeof(double)));
+  });
+  if (e != cudaSuccess) return e;
   potrf_diag_kernel<<<1, 256, smem, s>>>(a, ld, k0, nb, w_out, logdet_part, st);
   return cudaGetLastError();
 }

@@ -4,12 +4,53 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "../../include/exa.h"
 
 namespace exa {
+
+// One-time set-up per device (function attributes such as the dynamic shared-memory
+// limit, and cached device properties, hold for the current device only): runs f()
+// once per device id 0..63 with that device current, thread-safe; a failed f() is
+// retried on the next call.  Ids beyond 63 run f() every time.
+class PerDeviceOnce {
+ public:
+  template <class F>
+  cudaError_t operator()(F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return f();
+    const uint64_t bit = 1ull << dev;
+    if (done_.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu_);
+    if (done_.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess) done_.fetch_or(bit, std::memory_order_release);
+    return e;
+  }
+
+ private:
+  std::atomic<uint64_t> done_{0};
+  std::mutex mu_;
+};
+
+// A device property cached per device (ids 0..63; beyond that, queried every call).
+template <class F>
+int per_device_int(std::atomic<int> (&cache)[64], F&& query) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return query();
+  if (dev < 0 || dev >= 64) return query();
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  v = query();
+  if (v > 0) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // Matérn generation parameters (one per theta), computed on the host.

@@ -938,13 +938,12 @@ cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int
   if (rows <= 0) return cudaSuccess;
   if (K > kSplitMaxK) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kSplitRows * (K + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(split_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSplitRows * (kSplitMaxK + 1) * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([] {
+    return cudaFuncSetAttribute(split_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSplitRows * (kSplitMaxK + 1) * (int)sizeof(double));
+  });
+  if (e != cudaSuccess) return e;
   split_rows_kernel<<<(rows + kSplitRows - 1) / kSplitRows, 256, smem, s>>>(src, rs, cs, rows, K, op.hi, op.lo,
                                                         (__nv_bfloat16_raw*)op.dig, (int64_t)op.rows * op.K, op.ex,
                                                         out_row0);
@@ -952,14 +951,14 @@ cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int
 }
 
 static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static std::atomic<int> cache[64];
+  const int n = per_device_int(cache, [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
+  });
+  return n > 0 ? n : 148;
 }
 
 int tc_num_sms() { return num_sms(); }
@@ -967,12 +966,11 @@ int tc_num_sms() { return num_sms(); }
 cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
                            int max_ctas) {
   if (g.ntiles <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gemm_t3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3::SMEM_BYTES);
+  static PerDeviceOnce attr_once;
+  {
+    const cudaError_t e =
+        attr_once([] { return cudaFuncSetAttribute(gemm_t3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3::SMEM_BYTES); });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int cap = num_sms();
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
@@ -992,12 +990,11 @@ cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const Spl
   if (g.K2 > 0 && (!A2 || !B2)) return cudaErrorInvalidValue;
   if (g.K2 <= 0) A2 = &A, B2 = &B;
   if (g.ntiles <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gemm_t3_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3p::SMEM_BYTES);
+  static PerDeviceOnce attr_once;
+  {
+    const cudaError_t e =
+        attr_once([] { return cudaFuncSetAttribute(gemm_t3_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t3p::SMEM_BYTES); });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int cap = num_sms();
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
@@ -1011,12 +1008,11 @@ cudaError_t launch_gemm_t3_pair(cudaStream_t s, const SplitOperand& A, const Spl
 cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
                            int max_ctas) {
   if (g.ntiles <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+  static PerDeviceOnce attr_once;
+  {
+    const cudaError_t e =
+        attr_once([] { return cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES); });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int cap = num_sms();
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;

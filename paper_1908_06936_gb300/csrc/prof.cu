@@ -7,7 +7,8 @@
 namespace exa {
 
 static const char* kNames[PK_COUNT] = {"matern_gen", "potrf_diag_fp64", "trsm_panel_fp64", "syrk_update_fp64",
-                                       "dgemm_small_fp64", "split_rows", "gemm_tf32x3_tc", "gemm_ozaki_tc",
+                                       "dgemm_small_fp64", "split_rows", "gemm_tf32x3_tc", "gemm_tf32x3_pair",
+                                       "gemm_ozaki_tc",
                                        "trsv", "symv_residual", "gradient", "batched_chol", "other"};
 
 const char* prof_name(int kind) { return (kind >= 0 && kind < PK_COUNT) ? kNames[kind] : "?"; }
@@ -57,10 +58,16 @@ void prof_collect(exa_ctx* c) {
     if (cudaEventElapsedTime(&ms, p.pool[r.ev0], p.pool[r.ev1]) == cudaSuccess) {
       p.ms[r.kind] += ms;
       p.timed[r.kind] += 1;
+      p.timed_flops[r.kind] += r.flops;
+      p.timed_bytes[r.kind] += r.bytes;
     }
   }
   p.recs.clear();
   p.used = 0;
+}
+
+void prof_fold(exa_ctx* c) {
+  if (c->prof.on && !c->prof.recs.empty()) prof_collect(c);
 }
 
 void prof_release(exa_ctx* c) {
@@ -95,12 +102,14 @@ extern "C" int exa_profile_read(exa_ctx* c, exa_kernel_stat* out, int max, int r
     out[k].ms = p.ms[i];
     out[k].flops = p.flops[i];
     out[k].bytes = p.bytes[i];
+    out[k].timed_flops = p.timed_flops[i];
+    out[k].timed_bytes = p.timed_bytes[i];
     ++k;
   }
   if (reset) {
     for (int i = 0; i < PK_COUNT; ++i) {
       p.launches[i] = p.timed[i] = 0;
-      p.flops[i] = p.bytes[i] = p.ms[i] = 0.0;
+      p.flops[i] = p.bytes[i] = p.ms[i] = p.timed_flops[i] = p.timed_bytes[i] = 0.0;
     }
   }
   return k;

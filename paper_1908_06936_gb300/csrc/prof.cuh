@@ -17,7 +17,8 @@ enum ProfKind : int {
   PK_SYRK64,        // FP64 DMMA trailing update
   PK_DGEMM_SMALL,   // FP64 DMMA block-inverse products
   PK_SPLIT,         // split of FP64 rows into TF32 halves / BF16 digits
-  PK_GEMM_T3,       // tcgen05 TF32x3 products
+  PK_GEMM_T3,       // tcgen05 TF32x3 products, one CTA per 128 x 128 tile
+  PK_GEMM_T3_PAIR,  // tcgen05 TF32x3 products on CTA pairs (256 x 256 tiles): the trailing update
   PK_GEMM_OZ,       // tcgen05 exact digit-slice products
   PK_TRSV,          // triangular solves
   PK_SYMV,          // refinement residual
@@ -42,6 +43,8 @@ struct Prof {
   double bytes[PK_COUNT] = {};
   double ms[PK_COUNT] = {};
   int64_t timed[PK_COUNT] = {};
+  double timed_flops[PK_COUNT] = {};  // flops / bytes of the timed scopes only, so that
+  double timed_bytes[PK_COUNT] = {};  // timed work / timed milliseconds is a rate
   std::vector<cudaEvent_t> pool;
   std::vector<ProfRec> recs;
   size_t used = 0;
@@ -63,6 +66,9 @@ class ProfScope {
 };
 
 void prof_collect(exa_ctx* c);  // synchronises and folds pending event pairs into the totals
+// After an evaluation that ended with a synchronise: fold its event pairs so the
+// event pool is reused (no-op when profiling is off).
+void prof_fold(exa_ctx* c);
 void prof_release(exa_ctx* c);
 
 }  // namespace exa

@@ -1,4 +1,5 @@
-// Release of the buffers held by the mixed-precision, gradient and batched paths.
+// release_extra: frees the device buffers, the look-ahead stream and its events held by the
+// mixed-precision, gradient, prediction, Fisher and batched paths of a context.
 #include "ctx.cuh"
 
 namespace exa {

@@ -620,8 +620,8 @@ cudaError_t launch_transpose_lower_to_upper(cudaStream_t s, double* a, int64_t l
 }
 
 static int ptrsv_grid() {
-  static int grid = 0;
-  if (!grid) {
+  static std::atomic<int> cache[64];
+  return per_device_int(cache, [] {
     int dev = 0, sms = 0, per = 0, per2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -629,9 +629,8 @@ static int ptrsv_grid() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, trsv_bwd_persistent_kernel, 256, 0);
     if (per2 < per) per = per2;
     if (per > 2) per = 2;
-    grid = (per < 1 ? 1 : per) * sms;
-  }
-  return grid;
+    return (per < 1 ? 1 : per) * (sms > 0 ? sms : 1);
+  });
 }
 
 // Forward (x = L^-1 rhs, rhs overwritten) then backward (x = L^-T x) solve.  The

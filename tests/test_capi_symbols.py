@@ -53,3 +53,21 @@ def test_setters_reject_a_null_context():
     ]
     for call in calls:
         assert call() == exa.EXA_ERR_ARG
+
+
+def header_enum(name):
+    src = open(os.path.join(ROOT, "include", "exa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\}\s*" + name + ";", src).group(1)
+    return {k: int(v) for k, v in re.findall(r"(EXA_\w+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_enums_match_the_header():
+    # the precision and status codes the binding passes are the header's, and the precision
+    # codes are the boundary's: FP64 0, FP32 1, BF16x3 2, TF32x3 3
+    import paper_1908_06936_gb300 as exa
+
+    prec = header_enum("exa_prec")
+    assert prec == {"EXA_FP64": 0, "EXA_MIXED_FP32": 1, "EXA_MIXED_BF16X3": 2, "EXA_MIXED_TF32X3": 3}
+    for k, v in list(prec.items()) + list(header_enum("exa_status").items()) + list(header_enum("exa_gemm_kind").items()):
+        assert getattr(exa, k) == v, k

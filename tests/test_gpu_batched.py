@@ -148,7 +148,7 @@ def test_batched_full_config_sigma2_scaling(ctx):
 
 
 # ---- mixed precision (FP32 off-diagonal tiles, FP64 diagonal tiles, FP64 refinement) ----
-MIXED = 3  # EXA_MIXED_FP32
+MIXED = 1  # EXA_MIXED_FP32
 MIXED_TOL = 1e-6  # stated bound for a reduced-precision log-likelihood, |dl|/|l|
 
 

@@ -107,6 +107,18 @@ def test_bf16x3_is_refused_with_reason(ctx):
     assert ei.value.status == exa.EXA_ERR_ARG and "3e-4" in str(ei.value)
 
 
+def test_precision_enum_values_and_fp32_refusal(ctx):
+    """The precision codes are the boundary's (FP64 0, FP32 1, BF16x3 2, TF32x3 3); the single-field
+    path refuses EXA_MIXED_FP32 (batched form only) with its reason."""
+    import paper_1908_06936_gb300 as exa
+
+    assert (exa.EXA_FP64, exa.EXA_MIXED_FP32, exa.EXA_MIXED_BF16X3, exa.EXA_MIXED_TF32X3) == (0, 1, 2, 3)
+    locs, Z = workload(8, seed=1)
+    with pytest.raises(exa.ExaError) as ei:
+        ctx.loglik(to_dev(locs), to_dev(Z), (1.0, 0.1, 0.5), exa.EXA_MIXED_FP32)
+    assert ei.value.status == exa.EXA_ERR_ARG and "batched" in str(ei.value)
+
+
 def test_mixed_simulate_close_to_oracle(ctx):
     import paper_1908_06936_gb300 as exa
 
