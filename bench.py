@@ -318,6 +318,17 @@ def configs_leg(args, ctx) -> dict:
     l, g = ctx.loglik_grad(dl, dz, thg)
     dt = time.perf_counter() - t0
     out["n22500_gradient_fp64"] = {"evals_per_s": 1.0 / dt, "seconds": dt, "loglik": l, "grad": list(map(float, g))}
+    # mixed precision: mixed factor, FP64-refined Sigma^-1 z, Sigma^-1 on the tensor cores
+    ctx.loglik_grad(dl, dz, thg, exa.EXA_MIXED_TF32X3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lm, gm = ctx.loglik_grad(dl, dz, thg, exa.EXA_MIXED_TF32X3)
+    dtm = time.perf_counter() - t0
+    gsc = max(1.0, float(np.max(np.abs(g))))
+    out["n22500_gradient_mixed"] = {"evals_per_s": 1.0 / dtm, "seconds": dtm, "loglik": lm, "grad": list(map(float, gm)),
+                                    "rel_dl_vs_fp64": abs(lm - l) / abs(l),
+                                    "grad_err_vs_fp64_over_max": (np.abs(gm - g) / gsc).tolist(),
+                                    "speedup_vs_fp64": dt / dtm}
     # kriging at 2,048 new locations from the same 22,500 observations (means and variances)
     new = torch.as_tensor(synth.uniform_square(2048, 5), device="cuda")
     ctx.predict(dl, dz, thg, new)

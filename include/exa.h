@@ -160,11 +160,31 @@ exa_status exa_loglik(exa_ctx* ctx, const double* d_locs, const double* d_z, con
 exa_status exa_loglik_ex(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                          exa_prec prec, exa_result* out);
 
-/* Log-likelihood and its gradient dl/d(sigma^2, beta, nu), FP64:
+/* Log-likelihood and its gradient dl/d(sigma^2, beta, nu) (Eq. 2 differentiated
+ * through the Matern covariance of Eq. 3):
  *   dl/dtheta_k = 1/2 a^T (dSigma/dtheta_k) a - 1/2 tr(Sigma^-1 dSigma/dtheta_k),  a = Sigma^-1 z.
- * grad (host, 3 doubles).  Only EXA_FP64 is accepted for prec.              */
+ * grad (host, 3 doubles).  dSigma/dtheta_k is regenerated entry by entry (never stored).
+ *   EXA_FP64          FP64 factor, a, and Sigma^-1 = L^-T L^-1 on FP64 DMMA.  Holds two
+ *                     n_pad^2 FP64 buffers (n_pad = n rounded up to the tile) when the
+ *                     context can hold them; otherwise (workspace bound or cudaMalloc
+ *                     failure) it holds one: L^-1 overwrites the factor and each tile of
+ *                     L^-T L^-1 is reduced as it is formed.  Same result to rounding.
+ *   EXA_MIXED_TF32X3  l from the mixed evaluation (exa_loglik), a refined in FP64 to
+ *                     rounding level, Sigma^-1 of the mixed factor with every product on
+ *                     the tensor cores in exact 7-bit digit slices (35-bit operands), or on
+ *                     FP64 DMMA after exa_ctx_set_gradient_inverse(ctx, 1).  Holds two
+ *                     n_pad^2 FP64 buffers (n_pad = n rounded up to 512) plus about 5 n^2
+ *                     bytes of digit planes.  Stated accuracy against the FP64 oracle:
+ *                     each component within 5e-5 of max|grad| (2.4e-5 measured on the
+ *                     smoothest field tested, nu = 1.5, beta = 0.2; <= 2e-6 for nu <= 1).
+ * Other precisions return EXA_ERR_ARG.                                       */
 exa_status exa_loglik_grad(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                            exa_prec prec, double* loglik, double grad[3]);
+
+/* Mixed-precision gradient: compute Sigma^-1 of the mixed factor on FP64 DMMA
+ * (fp64 != 0: about 2 n^3 / 3 FP64 flops, for ill-conditioned fields) or on the
+ * tensor cores (0, the default).                                             */
+exa_status exa_ctx_set_gradient_inverse(exa_ctx* ctx, int fp64);
 
 /* Batched evaluation of nrep independent replicate fields of uneven sizes
  * (one persistent launch walks the tile tasks of every replicate; the

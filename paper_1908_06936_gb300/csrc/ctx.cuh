@@ -53,10 +53,17 @@ struct exa_ctx {
   exa::SplitOperand sp_a, sp_a2, sp_a3, sp_a4, sp_b;
   exa::DevBuf mx_vec;       // refinement vectors
   exa::DevBuf mx_w2;        // inverse of the panel-wide diagonal block (row-major)
+  exa::DevBuf mx_wall;      // every panel's diagonal-block inverse, T x 512 x 512 (kept for the gradient)
+  int keep_block_inverses = 0;  // mixed factorisation: write block k's inverse to mx_wall + k 512^2
+  int ir_tight = 0;         // mixed refinement: iterate to rounding level (the gradient needs Sigma^-1 z)
+  int grad_inverse_fp64 = 0;  // mixed gradient: Sigma^-1 of the mixed factor on FP64 DMMA instead of the tensor cores
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
   exa::DevBuf mx_symv;      // partial sums of the tiled symmetric product
   // gradient
   exa::DevBuf gr_part;      // second n x n buffer: Sigma^-1 for the gradient trace term
+  exa::DevBuf gr_xsplit;    // mixed gradient: digit planes of every 512-row block of X = L^-1
+  exa::DevBuf gr_lsplit;    // mixed gradient: digit planes of one 512-row block of L
+  exa::DevBuf gr_t;         // mixed gradient: 512 x n product of one row block
   exa::DevBuf gr_blocks;    // per-block gradient partial sums
   exa::DevBuf pr_c, pr_y;   // prediction: cross-covariance block and its solve block
   exa::DevBuf fs_m;         // Fisher information: Sigma^-1 D_k for k = 0, 1, 2
@@ -112,5 +119,9 @@ void model_params(const exa_ctx* c, const double theta[3], MaternParams* P);
 void release_batched(exa_ctx* c);
 // Lay out a split operand of `rows` x K in `buf` (T3 planes and/or OZ digits) and build its TMA maps.
 exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz);
+// Bytes of one split operand (a multiple of 1024), and its layout at `base` (1024-byte aligned)
+// with its TMA maps.
+size_t split_bytes(int64_t rows, int K, bool t3, bool oz);
+cudaError_t split_layout(SplitOperand& op, void* base, int64_t rows, int K, bool t3, bool oz);
 
 }  // namespace exa

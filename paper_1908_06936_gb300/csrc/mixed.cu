@@ -21,19 +21,19 @@ constexpr int64_t kFuseMinRows = 61440;   // two panels per trailing pass down t
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 
-exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz) {
+size_t split_bytes(int64_t rows, int K, bool t3, bool oz) {
   const size_t t3_bytes = t3 ? (size_t)rows * K * 4 : 0;
   const size_t dig_bytes = oz ? (size_t)kOzSlices * rows * K * 2 : 0;
   const size_t ex_bytes = oz ? (size_t)round_up(rows, 64) * 4 : 0;
   const size_t exb_bytes = oz ? (size_t)round_up((rows + 255) / 256, 64) * 4 : 0;
-  const size_t total = 2 * t3_bytes + dig_bytes + ex_bytes + exb_bytes + 1024;
-  void* old = buf.p;
-  exa_status st = ensure(c, buf, total, "split operands");
-  if (st != EXA_OK) return st;
-  const bool same = (old == buf.p) && op.rows == rows && op.K == K && ((op.hi != nullptr) == t3) &&
-                    ((op.dig != nullptr) == oz);
-  if (same) return EXA_OK;
-  uint8_t* base = (uint8_t*)buf.p;
+  return (2 * t3_bytes + dig_bytes + ex_bytes + exb_bytes + 1023) / 1024 * 1024;
+}
+
+cudaError_t split_layout(SplitOperand& op, void* base_p, int64_t rows, int K, bool t3, bool oz) {
+  const size_t t3_bytes = t3 ? (size_t)rows * K * 4 : 0;
+  const size_t dig_bytes = oz ? (size_t)kOzSlices * rows * K * 2 : 0;
+  const size_t ex_bytes = oz ? (size_t)round_up(rows, 64) * 4 : 0;
+  uint8_t* base = (uint8_t*)base_p;
   op.rows = rows;
   op.K = K;
   op.hi = t3 ? (float*)base : nullptr;
@@ -41,11 +41,20 @@ exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows,
   op.dig = oz ? (void*)(base + 2 * t3_bytes) : nullptr;
   op.ex = oz ? (int*)(base + 2 * t3_bytes + dig_bytes) : nullptr;
   op.exb = oz ? (int*)(base + 2 * t3_bytes + dig_bytes + ex_bytes) : nullptr;
-  cudaError_t e = make_split_maps(op);
-  if (e != cudaSuccess) {
-    op.rows = 0;
-    return cuda_err(c, e, "tensor map encode");
-  }
+  const cudaError_t e = make_split_maps(op);
+  if (e != cudaSuccess) op.rows = 0;
+  return e;
+}
+
+exa_status ensure_split(exa_ctx* c, SplitOperand& op, DevBuf& buf, int64_t rows, int K, bool t3, bool oz) {
+  void* old = buf.p;
+  exa_status st = ensure(c, buf, split_bytes(rows, K, t3, oz) + 1024, "split operands");
+  if (st != EXA_OK) return st;
+  const bool same = (old == buf.p) && op.rows == rows && op.K == K && ((op.hi != nullptr) == t3) &&
+                    ((op.dig != nullptr) == oz);
+  if (same) return EXA_OK;
+  const cudaError_t e = split_layout(op, buf.p, rows, K, t3, oz);
+  if (e != cudaSuccess) return cuda_err(c, e, "tensor map encode");
   return EXA_OK;
 }
 
@@ -82,7 +91,8 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
   double* P = (double*)c->panel.p;       // (NB - 128) x 128 FP64 panel of the in-block TRSM
   double* tmp = P + (size_t)NB * nb;     // 128 x 128 scratch
   double* LD = (double*)c->logdet_part.p;
-  double* W2 = (double*)c->mx_w2.p;      // NB x NB inverse of the diagonal block (row-major)
+  // NB x NB inverse of the diagonal block (row-major); every block's is kept when asked
+  double* W2 = c->keep_block_inverses ? (double*)c->mx_wall.p + (size_t)k * kMixNB * kMixNB : (double*)c->mx_w2.p;
   const double dnb = nb;
   const int64_t k0 = (int64_t)k * NB;
   cudaError_t e = cudaSuccess;
@@ -104,7 +114,7 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
     }
   }
   if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
-  if (k == M.T - 1) return EXA_OK;
+  if (k == M.T - 1 && !c->keep_block_inverses) return EXA_OK;
   // 2. W = L_kk^-1 by block rows: W_ii from the tiles, W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj
   {
     ProfScope ps(c, PK_DGEMM_SMALL, (double)NB * NB * NB / 3.0, 8.0 * 4.0 * NB * NB, 1 + SUB * (SUB - 1), s, true);
@@ -123,6 +133,7 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
     }
   }
   if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
+  if (k == M.T - 1) return EXA_OK;  // the last block has no panel below it
   const int64_t r0 = k0 + NB;
   const int64_t m = npad - r0;
   double* panel_src = a + r0 + k0 * ld;  // element (r, t) at panel_src[r + t*ld]
@@ -336,6 +347,9 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   const int nbuf = fuse ? 4 : 2;
   if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure(c, c->mx_w2, (size_t)NB * NB * sizeof(double), "diagonal block inverse")) != EXA_OK) return st;
+  if (c->keep_block_inverses &&
+      (st = ensure(c, c->mx_wall, (size_t)T * NB * NB * sizeof(double), "diagonal block inverses")) != EXA_OK)
+    return st;
   if (!c->side) {
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->la_ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -541,7 +555,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
       e = cudaMemcpyAsync(c->h_scalars + 4, c->d_scalars + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
     if ((st = read_status(c)) != EXA_OK) return st;
-    if (fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
+    if (!c->ir_tight && fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
       q_done = true;
       ++it;
       break;

@@ -1,0 +1,98 @@
+"""Single-kernel cases for profiling the library's hot kernels in isolation.
+
+Each case runs one C-ABI call twice (a warm-up, then the call to capture) on a
+problem larger than the 129 MB L2, so DRAM counters mean something, but a few GB
+on the device at most, and prints the device time of the second call (CUDA
+events on the context stream).  Under ncu, skip the warm-up's launches of the
+kernel (``-s``) and capture one launch (``-c 1``).
+
+  python -m paper_1908_06936_gb300.profile_cases gemm-pair --c 16384 --k 1024
+  python -m paper_1908_06936_gb300.profile_cases gemm-oz --c 16384
+  python -m paper_1908_06936_gb300.profile_cases potrf --n 16384
+  python -m paper_1908_06936_gb300.profile_cases matern --m 128
+
+gemm-pair / gemm-oz: exa_gemm_update, C -= A B^T with C (c x c, FP64) and A, B
+(c x k, FP64, standard normal); gemm-pair is the CTA-pair TF32x3 trailing-update
+kernel (k = 1024 reduces two operand pairs per pass, as the fused two-panel pass
+of the factorisation), gemm-oz the exact digit-slice band kernel (k <= 512).
+potrf: exa_potrf of the Matern covariance of an m x m jittered grid (FP64 tiled
+Cholesky: potrf_diag, trsm_panel, syrk_update).  matern: exa_covariance of an
+m x m jittered grid (the generation kernel, lower triangle, one copy).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def _timed(fn, stream):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def main(argv=None) -> dict:
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("case", choices=["gemm-pair", "gemm-oz", "potrf", "matern"])
+    ap.add_argument("--c", type=int, default=16384, help="rows and columns of C (gemm cases)")
+    ap.add_argument("--k", type=int, default=512, help="inner dimension (gemm cases)")
+    ap.add_argument("--m", type=int, default=128, help="grid side, n = m^2 (potrf, matern)")
+    ap.add_argument("--theta", type=float, nargs=3, default=(1.0, 0.03, 1.0))
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    out = {"case": args.case}
+    with exa.Context() as ctx:
+        if args.case in ("gemm-pair", "gemm-oz"):
+            kind = exa.EXA_GEMM_T3_PAIR if args.case == "gemm-pair" else exa.EXA_GEMM_OZ
+            c, k = args.c, args.k
+            g = torch.Generator(device="cuda").manual_seed(7)
+            A = torch.randn((c, k), dtype=torch.float64, device="cuda", generator=g)
+            B = torch.randn((c, k), dtype=torch.float64, device="cuda", generator=g)
+            C = torch.zeros((c, c), dtype=torch.float64, device="cuda")
+            call = lambda: ctx.check(exa.exa_gemm_update(ctx.handle, kind, c, c, k, A, B, C, c, 0))
+            call()
+            ms = _timed(call, s)
+            out.update({"c": c, "k": k, "ms": ms, "useful_tflops": 2.0 * c * c * k / (ms * 1e-3) / 1e12,
+                        "c_bytes_rw": 16.0 * c * c})
+        elif args.case == "potrf":
+            m = args.m
+            n = m * m
+            locs = torch.as_tensor(synth.jittered_grid(m, 3), device="cuda")
+            S = ctx.covariance(locs, args.theta)
+            work = torch.empty_like(S)
+
+            def call():
+                work.copy_(S)
+                ctx.check(exa.exa_potrf(ctx.handle, work, n, n))
+
+            call()
+            ms = _timed(call, s)
+            out.update({"n": n, "ms": ms, "tflops_n3_over_3": n ** 3 / 3.0 / (ms * 1e-3) / 1e12})
+        else:
+            m = args.m
+            n = m * m
+            locs = torch.as_tensor(synth.jittered_grid(m, 3), device="cuda")
+            S = torch.empty((n, n), dtype=torch.float64, device="cuda")
+            call = lambda: ctx.check(exa.exa_covariance(ctx.handle, locs, n, args.theta, S, n))
+            call()
+            ms = _timed(call, s)
+            lower = n * (n + 1) / 2.0
+            out.update({"n": n, "ms": ms, "entries_per_s": lower / (ms * 1e-3),
+                        "write_gbs": 8.0 * lower / (ms * 1e-3) / 1e9})
+    print(json.dumps(out), flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    main()
