@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kGemmThreads)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
+    const uint64_t pol = l2_evict_last_policy();
     prefetch_tmap(&tA_hi);
     prefetch_tmap(&tA_lo);
     prefetch_tmap(&tB_hi);
@@ -162,10 +163,10 @@ __global__ void __launch_bounds__(kGemmThreads)
         }
         uint8_t* sb = smem + stage * STAGE_BYTES;
         mbar_expect_tx(&full[stage], STAGE_BYTES);
-        tma_load_2d(sb, &tA_hi, &full[stage], kc * KC, ya);
-        tma_load_2d(sb + OP_BYTES, &tA_lo, &full[stage], kc * KC, ya);
-        tma_load_2d(sb + 2 * OP_BYTES, &tB_hi, &full[stage], kc * KC, yb);
-        tma_load_2d(sb + 3 * OP_BYTES, &tB_lo, &full[stage], kc * KC, yb);
+        tma_load_2d_hint(sb, &tA_hi, &full[stage], kc * KC, ya, pol);
+        tma_load_2d_hint(sb + OP_BYTES, &tA_lo, &full[stage], kc * KC, ya, pol);
+        tma_load_2d_hint(sb + 2 * OP_BYTES, &tB_hi, &full[stage], kc * KC, yb, pol);
+        tma_load_2d_hint(sb + 3 * OP_BYTES, &tB_lo, &full[stage], kc * KC, yb, pol);
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kGemmThreads)
         const int cb = half * 64 + h2 * 32;
         double cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(cb + j) * g.ldc];
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)(cb + j) * g.ldc);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           uint32_t acc[16];
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kGemmThreads)
             const int cc = cb + c * 16 + j;
             if (diag && cc > r) continue;
             const double v = f32_bits_to_f64(acc[j]);
-            cp[(int64_t)cc * g.ldc] = g.store ? v : cv[c * 16 + j] - v;
+            __stcs(cp + (int64_t)cc * g.ldc, g.store ? v : cv[c * 16 + j] - v);
           }
         }
       }
@@ -304,7 +305,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int TILE = 256;
 constexpr uint32_t IDESC = idesc(kFmtTF32, TILE, TILE);
 constexpr int TMEM_COLS = 512;                  // 2 accumulator buffers x 256 columns
-constexpr int kSuper = kRasterSuper / 2;        // supertile edge in 256-tiles
+constexpr int kSuper = kPairSuper;              // supertile edge in 256-tiles
 }  // namespace t3p
 
 // Pair tiles (units of 256): kEnumFull (bi = t / nt) or kEnumLowerOffBand (supertiles of the
@@ -387,6 +388,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
+    const uint64_t pol = l2_evict_last_policy();
     prefetch_tmap(&tA_hi);
     prefetch_tmap(&tA_lo);
     prefetch_tmap(&tB_hi);
@@ -423,10 +425,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
         uint8_t* sb = smem + stage * STAGE_BYTES;
         if (leader) mbar_expect_tx(&full[stage], (one ? 1 : 2) * STAGE_BYTES);
         const uint32_t fl = map_to_rank(smem_u32(&full[stage]), 0);
-        tma_load_2d_pair(sb, second ? &tA2_hi : &tA_hi, fl, kx, ya);
-        if (!one) tma_load_2d_pair(sb + OP_BYTES, second ? &tA2_lo : &tA_lo, fl, kx, ya);
-        tma_load_2d_pair(sb + 2 * OP_BYTES, second ? &tB2_hi : &tB_hi, fl, kx, yb);
-        if (!one) tma_load_2d_pair(sb + 3 * OP_BYTES, second ? &tB2_lo : &tB_lo, fl, kx, yb);
+        tma_load_2d_pair_hint(sb, second ? &tA2_hi : &tA_hi, fl, kx, ya, pol);
+        if (!one) tma_load_2d_pair_hint(sb + OP_BYTES, second ? &tA2_lo : &tA_lo, fl, kx, ya, pol);
+        tma_load_2d_pair_hint(sb + 2 * OP_BYTES, second ? &tB2_hi : &tB_hi, fl, kx, yb, pol);
+        if (!one) tma_load_2d_pair_hint(sb + 3 * OP_BYTES, second ? &tB2_lo : &tB_lo, fl, kx, yb, pol);
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -523,7 +525,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
         const int cb = half * 128 + h2 * 32;
         double cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)(cb + j) * g.ldc];
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)(cb + j) * g.ldc);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           uint32_t acc[16];
@@ -537,7 +539,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const double v = f32_bits_to_f64(acc[j]);
-            cp[(int64_t)(cb + c * 16 + j) * g.ldc] = g.store ? v : cv[c * 16 + j] - v;
+            __stcs(cp + (int64_t)(cb + c * 16 + j) * g.ldc, g.store ? v : cv[c * 16 + j] - v);
           }
         }
       }
@@ -601,6 +603,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
   const int kchunks = g.K / KC;
 
   if (warp == 0 && lane == 0) {
+    const uint64_t pol = l2_evict_last_policy();
     for (int s = 0; s < S; ++s) {
       prefetch_tmap(&ta.m[s]);
       prefetch_tmap(&tb.m[s]);
@@ -623,8 +626,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
         mbar_expect_tx(&full[stage], STAGE_BYTES);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          tma_load_2d(sb + s * A_BYTES, &ta.m[s], &full[stage], kc * KC, ya);
-          tma_load_2d(sb + S * A_BYTES + s * B_BYTES, &tb.m[s], &full[stage], kc * KC, yb);
+          tma_load_2d_hint(sb + s * A_BYTES, &ta.m[s], &full[stage], kc * KC, ya, pol);
+          tma_load_2d_hint(sb + S * A_BYTES + s * B_BYTES, &tb.m[s], &full[stage], kc * KC, yb, pol);
         }
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
@@ -712,7 +715,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
       double* cp = g.C + row + col0 * g.ldc;
       double cv[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) cv[j] = g.store ? 0.0 : cp[(int64_t)j * g.ldc];
+      for (int j = 0; j < 16; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)j * g.ldc);
       // group g holds an exact integer a_g (|a_g| < 2^24) of weight 2^(-7(g+2)):
       // V = sum_g a_g 2^(7(4-g)) is an integer below 2^53, combined exactly in int64
       long long V[16];
@@ -735,7 +738,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
         if (lower && col0 + j > row) continue;
         const int ec = g.eb[g.b_row0 + bj * TN + 16 * half + j];
         const double x = i53_to_f64_scaled(V[j], er + ec - 7 * (S + 1));
-        cp[(int64_t)j * g.ldc] = g.store ? x : cv[j] - x;
+        __stcs(cp + (int64_t)j * g.ldc, g.store ? x : cv[j] - x);
       }
       ++it;
     }

@@ -16,6 +16,7 @@ constexpr int kSplitRows = 16;   // rows per CTA of the split kernel
 // Tile enumeration of one launch.
 enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2 };
 constexpr int kRasterSuper = 16;  // supertile edge (in 128-tiles) of the lower off-band enumeration
+constexpr int kPairSuper = 16;    // supertile edge (in 256-tiles) of the CTA-pair lower off-band enumeration
 
 struct OzMaps {
   CUtensorMap m[kOzSlices];

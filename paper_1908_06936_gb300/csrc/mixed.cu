@@ -265,7 +265,7 @@ static exa_status region_update(const MixStep& M, cudaStream_t s, int p, int j0,
     ProfScope ps(c, c->tc_pairs ? PK_GEMM_T3_PAIR : PK_GEMM_T3, npan * 2.0 * 128.0 * 128.0 * NB * (double)t3_tiles,
                  16.0 * 128.0 * 128.0 * (double)t3_tiles + npan * 8.0 * (double)m2 * NB, 1, s, true);
     if (c->tc_pairs) {  // 256-tiles on CTA pairs (m2 is a multiple of the 512 panel)
-      const long long t256 = m2 / 256, sp2s = kRasterSuper / 2;
+      const long long t256 = m2 / 256, sp2s = kPairSuper;
       const long long ts = (t256 + sp2s - 1) / sp2s;
       g.nt = (int)t256;
       g.ntiles = ts * (ts + 1) / 2 * sp2s * sp2s;
