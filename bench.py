@@ -47,6 +47,46 @@ def peaks() -> dict:
             "fp64": d["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], "source": src}
 
 
+def probe_peaks() -> dict:
+    """Short timed probes on this GPU: the library's FP64 issue-rate probes (DFMA, DMMA) and the
+    measured library throughput of cuBLAS DGEMM and TF32 GEMM (torch.matmul, 8192^3), CUDA events."""
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+
+    s = torch.cuda.current_stream()
+    out = {"fp64_dfma_probe": exa.exa_probe_fp64_rate(s.cuda_stream, 0),
+           "fp64_dmma_probe": exa.exa_probe_fp64_rate(s.cuda_stream, 1)}
+
+    def gemm_rate(dtype, reps, tf32):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(8192, 8192, dtype=dtype, device="cuda")
+            b = torch.randn(8192, 8192, dtype=dtype, device="cuda")
+            torch.matmul(a, b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = None
+            for _ in range(reps):
+                e0.record(s)
+                torch.matmul(a, b)
+                e1.record(s)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            return 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+
+    out["fp64_dgemm_cublas"] = gemm_rate(torch.float64, 2, False)
+    out["tf32_gemm_cublas"] = gemm_rate(torch.float32, 10, True)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out["sms"] = sms
+    out["how"] = ("probes: every resident CTA, 8 independent chains per thread (DFMA) or warp (DMMA m8n8k4), best of "
+                  "3 launches after a warm-up; cuBLAS: best of 2 (FP64) / 10 (TF32) 8192^3 products")
+    return out
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
@@ -113,22 +153,61 @@ def gpu_id_for_smi() -> str | None:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(locs, Z, n_s: int) -> dict:
-    """Time the FP64 oracle on the first n_s locations of the workload."""
+CPU_CURVE_SIDES = (40, 50, 60, 70)  # oracle timed at n = 1,600 ... 4,900 (jittered m x m grids)
+
+
+def oracle_curve(n: int, sides=CPU_CURVE_SIDES) -> dict:
+    """Time the FP64 oracle's log-likelihood (theta0) on m x m jittered grids and fit
+    t(n) = a n^2 + b n^3 (generation by quadrature Bessel functions is O(n^2), the unblocked
+    Cholesky O(n^3)) by least squares in relative error, then extrapolate to n.  Both CPU legs
+    (cpu_baseline and --impl reference) use this curve."""
+    import numpy as np
+
     import oracle
+    from paper_1908_06936_gb300 import synth
 
+    pts = []
+    for m in sides:
+        locs = synth.jittered_grid(m, 0)
+        z = synth.normals(m * m, 0)
+        t0 = time.perf_counter()
+        oracle.loglik(locs, z, THETA0)
+        pts.append((m * m, time.perf_counter() - t0))
+    ns = np.array([p[0] for p in pts], dtype=float)
+    ts = np.array([p[1] for p in pts])
+    if len(pts) >= 2:
+        A = np.stack([ns ** 2 / ts, ns ** 3 / ts], axis=1)
+        (a, b), *_ = np.linalg.lstsq(A, np.ones_like(ts), rcond=None)
+        if a < 0 or b <= 0:  # fall back to the pure n^3 law
+            a, b = 0.0, float(np.exp(np.mean(np.log(ts) - 3.0 * np.log(ns))))
+    else:
+        a, b = 0.0, float(ts[0] / ns[0] ** 3)
+    t_n = float(a) * float(n) ** 2 + float(b) * float(n) ** 3
+    return {"points": [[int(x), float(y)] for x, y in pts], "a_n2": float(a), "b_n3": float(b), "seconds_at_n": t_n,
+            "work_seconds": float(ts.sum()), "threads": oracle.max_threads()}
+
+
+def oracle_check(m: int, curve: dict) -> dict:
+    """One oracle evaluation on an m x m grid, against the fitted law's prediction."""
+    import oracle
+    from paper_1908_06936_gb300 import synth
+
+    locs = synth.jittered_grid(m, 0)
+    z = synth.normals(m * m, 0)
     t0 = time.perf_counter()
-    r = oracle.loglik(locs[:n_s], Z[:n_s], THETA0)
+    oracle.loglik(locs, z, THETA0)
     dt = time.perf_counter() - t0
-    return {"seconds": dt, "l": r["l"], "threads": oracle.max_threads()}
+    pred = curve["a_n2"] * float(m * m) ** 2 + curve["b_n3"] * float(m * m) ** 3
+    return {"n": m * m, "seconds": dt, "predicted_seconds": pred, "measured_over_predicted": dt / pred}
 
 
-def cpu_baseline_entry(n: int, n_s: int, dt: float, threads: int) -> dict:
-    evals = 1.0 / (dt * (n / n_s) ** 3)
-    return {"value": evals, "unit": "evals/s", "cores": threads, "kind": "oracle",
-            "sample": "oracle log-likelihood of the first %d of the %d locations (%d grid rows of the same field), "
-                      "%.2f s on %d threads; scaled to n=%d by (n/n_s)^3 (Cholesky-dominated)"
-                      % (n_s, n, n_s // int(math.isqrt(n)), dt, threads, n)}
+def cpu_baseline_entry(n: int, curve: dict) -> dict:
+    pts = ", ".join("n=%d %.2f s" % (a, b) for a, b in curve["points"])
+    return {"value": 1.0 / curve["seconds_at_n"], "unit": "evals/s", "cores": curve["threads"], "kind": "oracle",
+            "sample": "oracle log-likelihood timed on jittered grids (%s; %.1f s of CPU work on %d threads), "
+                      "t = a n^2 + b n^3 fitted (a = %.3e s, b = %.3e s), extrapolated to n=%d"
+                      % (pts, curve["work_seconds"], curve["threads"], curve["a_n2"], curve["b_n3"], n),
+            "curve": curve}
 
 
 # ----------------------------------------------------------------------------- workload
@@ -154,8 +233,9 @@ def make_inputs(m: int, seed: int):
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch's algorithmic bytes) of the same
 # kernel on a C larger than L2; the per-launch traffic of the bench is this ratio times the
 # average algorithmic bytes of its timed launches.  Keyed by kernel class; the capture and its
-# command are summarised in profiles/gemm_t3_pair_c16384.md.
-TRAFFIC_RATIO = {}
+# command are summarised in profiles/gemm_t3_pair_bench_n90000.md (all 143 launches of one
+# n = 90,000 factorisation, 1-pass metrics).
+TRAFFIC_RATIO = {"gemm_tf32x3_pair": 1.368}
 
 
 def roofline(stats: list, pk: dict) -> dict:
@@ -364,11 +444,49 @@ def configs_leg(args, ctx) -> dict:
     return out
 
 
-def mle_leg(args, ctx) -> dict:
+def theta_grid_leg(args, ctx) -> dict:
+    """Mixed precision against the GPU's FP64 evaluation on the paper's parameter grid (Section III,
+    Example 2: sigma^2 = 1, beta in {0.03, 0.1, 0.3}, nu in {0.5, 1, 2}) at n = 22,500 (150 x 150 jittered
+    grid), Z = L eps at each theta from the FP64 factor.  Per theta: |dl|/|l|, the exact band, refinement
+    steps, the status of the mixed call, and both device times."""
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import synth
+
+    dl = torch.as_tensor(synth.jittered_grid(150, 8), device="cuda")
+    de = torch.as_tensor(synth.normals(22500, 8), device="cuda")
+    rows = []
+    for beta in (0.03, 0.1, 0.3):
+        for nu in (0.5, 1.0, 2.0):
+            th = (1.0, beta, nu)
+            row = {"theta": list(th)}
+            try:
+                dz = ctx.simulate(dl, de, th, exa.EXA_FP64)
+                f = ctx.loglik_ex(dl, dz, th, exa.EXA_FP64)
+            except exa.ExaError as err:
+                row["fp64"] = "status %d: %s" % (err.status, err)
+                rows.append(row)
+                continue
+            row["fp64_ms"] = f["ms_total"]
+            row["loglik_fp64"] = f["loglik"]
+            try:
+                mx = ctx.loglik_ex(dl, dz, th, exa.EXA_MIXED_TF32X3)
+                row.update({"mixed_ms": mx["ms_total"], "rel_dl": abs(mx["loglik"] - f["loglik"]) / abs(f["loglik"]),
+                            "exact_band": mx["exact_band"], "n_tiles": mx["n_tiles"], "ir_iters": mx["ir_iters"],
+                            "speedup": f["ms_total"] / mx["ms_total"], "mixed": "ok"})
+            except exa.ExaError as err:
+                row["mixed"] = "status %d: %s" % (err.status, err)
+            rows.append(row)
+    return {"workload": "n=22500 (150x150 jittered grid), Z = L eps per theta (FP64 factor); device times "
+                        "of one evaluation each (exa_result.ms_total)", "rows": rows}
+
+
+def mle_leg(args, ctx, prec_name="mixed") -> dict:
     """Maximum-likelihood fit of one field at n = 40,000 (200x200 jittered grid, theta0 = (1, 0.1, 0.5),
     Z = L eps from the mixed-precision factor): bounded Nelder-Mead in log(theta) from the lower bounds
-    (the paper's start, Section III Example 2), every evaluation a mixed-precision log-likelihood; the
-    optimum is evaluated once more in FP64 for |dl|/|l| there."""
+    (the paper's start, Section III Example 2), every evaluation a log-likelihood in `prec_name`
+    ("mixed" or "fp64"); the optimum is evaluated once more in FP64 for |dl|/|l| there."""
     import math
 
     import torch
@@ -382,28 +500,55 @@ def mle_leg(args, ctx) -> dict:
     dz = ctx.simulate(dl, torch.as_tensor(synth.normals(40000, 6), device="cuda"), th0, exa.EXA_MIXED_TF32X3)
     fails = [0]
 
+    prec = exa.EXA_FP64 if prec_name == "fp64" else exa.EXA_MIXED_TF32X3
+
     def f(_r, t):
         try:
-            return ctx.loglik(dl, dz, list(map(float, t)), exa.EXA_MIXED_TF32X3)
+            return ctx.loglik(dl, dz, list(map(float, t)), prec)
         except exa.ExaError as e:
             if e.status in (2, 6):  # not SPD / refinement stalled: -inf, the search steps away
                 fails[0] += 1
                 return -math.inf
             raise
 
-    f(0, th0)  # warm-up (allocates)
+    f(0, th0)  # warm-up (allocates; one evaluation at theta0, not counted)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = fit_replicates_with(f, 1, ftol=1e-5, xtol=1e-4, max_evals=args.mle_evals)
+    res = fit_replicates_with(f, 1, ftol=1e-5, xtol=1e-4,
+                              max_evals=args.mle_fp64_evals if prec_name == "fp64" else args.mle_evals)
     dt = time.perf_counter() - t0
     th = [float(v) for v in res["theta"][0]]
     lm = float(res["loglik"][0])
     l64 = ctx.loglik(dl, dz, th, exa.EXA_FP64)
     return {"workload": "n=40000 (200x200 jittered grid), Z = L eps at theta0 = (1, 0.1, 0.5); Nelder-Mead in "
-                        "log(theta) from the lower bounds; mixed-precision evaluations",
+                        "log(theta) from the lower bounds; %s evaluations" % prec_name,
             "evals": int(res["evals"][0]), "seconds": dt, "evals_per_s": int(res["evals"][0]) / dt,
-            "not_spd_or_stalled": fails[0], "theta_hat": th, "loglik_mixed": lm, "loglik_fp64_at_theta_hat": l64,
+            "not_spd_or_stalled": fails[0], "theta_hat": th, "loglik": lm, "loglik_fp64_at_theta_hat": l64,
             "rel_dl_at_theta_hat": abs(lm - l64) / abs(l64)}
+
+
+def gradient_mle_leg(args, ctx) -> dict:
+    """The gradient configuration's fit at n = 22,500 (150 x 150 jittered grid, Z = L eps at
+    theta0 = (1.5, 0.2, 1.5), FP64 factor): L-BFGS-B with the library's FP64 adjoint gradient against
+    bounded Nelder-Mead on l alone, both from the lower bounds, FP64 evaluations."""
+    import torch
+
+    import paper_1908_06936_gb300 as exa
+    from paper_1908_06936_gb300 import mle, synth
+
+    th0 = (1.5, 0.2, 1.5)
+    dl = torch.as_tensor(synth.jittered_grid(150, 4), device="cuda")
+    dz = ctx.simulate(dl, torch.as_tensor(synth.normals(22500, 4), device="cuda"), th0, exa.EXA_FP64)
+    ctx.loglik_grad(dl, dz, th0)  # warm-up
+    out = {"workload": "n=22500 (150x150 jittered grid), Z = L eps at theta0 = (1.5, 0.2, 1.5); FP64; start at "
+                       "the lower bounds (0.01, 0.01, 0.1)"}
+    for name, fit in (("lbfgsb_gradient", lambda: mle.fit_gradient(dl, dz, maxiter=args.grad_mle_iters, ctx=ctx)),
+                      ("nelder_mead", lambda: mle.fit_derivative_free(dl, dz, maxfev=args.grad_mle_evals, ctx=ctx))):
+        torch.cuda.synchronize()
+        r = fit()
+        out[name] = {"theta_hat": r["theta"], "loglik": r["loglik"], "evals": r["evals"], "seconds": r["seconds"],
+                     "seconds_per_eval": r["time_per_eval"], "method": r["method"]}
+    return out
 
 
 def batched_mle_leg(args) -> dict:
@@ -536,6 +681,12 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         chol_tflops = (n ** 3 / 3.0) / (res["ms_chol"] * 1e-3) / 1e12
         fp64 = None
         if args.fp64_steps > 0:
+            # warm-up: every FP64 kernel loaded and run once (a 1,600-location field); the n = 90,000
+            # buffers are the mixed leg's, already held
+            from paper_1908_06936_gb300 import synth as _synth
+
+            wl = torch.as_tensor(_synth.jittered_grid(40, 9), device="cuda")
+            ctx.loglik_ex(wl, torch.as_tensor(_synth.normals(1600, 9), device="cuda"), THETA0, exa.EXA_FP64)
             ms, rr = [], None
             for _ in range(args.fp64_steps):
                 rr = ctx.loglik_ex(dl, dz, THETA0, exa.EXA_FP64)
@@ -543,16 +694,28 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             fp64 = {"evals_per_s": 1e3 / statistics.mean(ms), "ms_per_eval": statistics.mean(ms),
                     "chol_ms": rr["ms_chol"], "chol_tflops": (n ** 3 / 3.0) / (rr["ms_chol"] * 1e-3) / 1e12,
                     "chol_frac_of_fp64_peak": (n ** 3 / 3.0) / (rr["ms_chol"] * 1e-3) / 1e12 / peaks()["fp64"],
-                    "loglik": rr["loglik"], "steps": args.fp64_steps, "warmup": 0}
+                    "loglik": rr["loglik"], "steps": args.fp64_steps,
+                    "warmup": "one FP64 evaluation at n=1,600 (kernels loaded; the n=90,000 buffers are the mixed leg's)"}
         pk = peaks()
         rl = roofline(stats, pk)
+        probes = probe_peaks() if args.probe_peaks else None
+        if fp64 and probes:
+            best64 = max(probes["fp64_dmma_probe"], probes["fp64_dgemm_cublas"], probes["fp64_dfma_probe"])
+            fp64["chol_frac_of_measured_fp64_peak"] = fp64["chol_tflops"] / best64
+            # clock x SMs x 4 FP64 flops per clock per SM (the part's nominal 1.25 TFLOP/s at 2,070 MHz)
+            if clk.get("sm_mhz"):
+                nominal = 4.0 * probes["sms"] * clk["sm_mhz"] * 1e6 / 1e12
+                fp64["fp64_clock_peak"] = nominal
+                fp64["chol_frac_of_clock_peak"] = fp64["chol_tflops"] / nominal
         batched = batched_leg(args, ctx) if args.batched_steps > 0 else None
         configs = configs_leg(args, ctx) if args.configs else None
         batched_mle = batched_mle_leg(args) if args.batched_mle_evals > 0 else None
         mle = mle_leg(args, ctx) if args.mle_evals > 0 else None
-        # CPU oracle baseline on a bounded sample of the same field
-        n_s = args.cpu_sample
-        cs = oracle_sample(locs, z_host, n_s)
+        mle64 = mle_leg(args, ctx, "fp64") if args.mle_fp64_evals > 0 else None
+        grad_mle = gradient_mle_leg(args, ctx) if args.grad_mle_evals > 0 else None
+        # CPU oracle baseline: a bounded curve of oracle timings, fitted and extrapolated
+        curve = oracle_curve(n)
+        theta_grid = theta_grid_leg(args, ctx) if args.theta_grid else None
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -573,8 +736,13 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "configs": configs,
             "batched_mle": batched_mle,
             "mle_n40000": mle,
+            "mle_n40000_fp64": mle64,
+            "gradient_mle_n22500": grad_mle,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()} for st in stats],
-            "cpu_baseline": cpu_baseline_entry(n, n_s, cs["seconds"], cs["threads"]),
+            "theta_grid_n22500": theta_grid,
+            "peaks_measured_here": probes,
+            "cpu_baseline_check": oracle_check(args.oracle_check_m, curve) if args.oracle_check_m else None,
+            "cpu_baseline": cpu_baseline_entry(n, curve),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
     ctx.close()
@@ -582,29 +750,25 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
 
 def run_reference(args) -> dict:
-    """The FP64 CPU oracle on the host cores, on a bounded sample of the same workload."""
-    import oracle
-    from paper_1908_06936_gb300 import synth
-
+    """The FP64 CPU oracle on the host cores: each step times the oracle curve (n = 1,600 ... 4,900) and
+    extrapolates it to the workload's n by the fitted a n^2 + b n^3 law, exactly as cpu_baseline does."""
     m = args.m
     n = m * m
-    n_s = args.ref_sample
-    locs = synth.jittered_grid(m, 0)
-    # observations of the sample: an exact realisation on the sample's own locations
-    z = oracle.simulate(locs[:n_s], THETA0, synth.normals(n, 0)[:n_s])
     for _ in range(args.warmup):
-        oracle.loglik(locs[:n_s], z, THETA0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.loglik(locs[:n_s], z, THETA0)
-    dt = (time.perf_counter() - t0) / args.steps
-    cb = cpu_baseline_entry(n, n_s, dt, oracle.max_threads())
+        oracle_curve(n, sides=CPU_CURVE_SIDES[:1])
+    curves = [oracle_curve(n) for _ in range(args.steps)]
+    t_n = sorted(c["seconds_at_n"] for c in curves)[len(curves) // 2]  # median over steps
+    curve = min(curves, key=lambda c: abs(c["seconds_at_n"] - t_n))
+    cb = cpu_baseline_entry(n, curve)
     v = cb["value"]
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * (n / n_s) ** 3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_n * 1e3,
+            "ms_per_step_note": "projected time of one n=%d evaluation from the fitted a n^2 + b n^3 law (median over steps); "
+                                "each step measured the oracle curve for %.1f s" % (n, curve["work_seconds"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=%d (%dx%d jittered grid), theta0=(1, 0.03, 1.0); FP64 CPU oracle on a "
-                                   "%d-location sample scaled by (n/n_s)^3" % (n, m, m, n_s), "n": n},
+            "config": {"workload": "n=%d (%dx%d jittered grid), theta0=(1, 0.03, 1.0); FP64 CPU oracle timed on "
+                                   "jittered grids of n = 1,600 ... 4,900 and extrapolated by the fitted a n^2 + b n^3 law"
+                                   % (n, m, m), "n": n},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -622,11 +786,20 @@ def main():
     ap.add_argument("--configs", type=int, default=1, help="also time the n=1,600 and n=22,500 configurations (0 skips)")
     ap.add_argument("--mle-evals", type=int, default=0,
                     help="maximum-likelihood fit at n=40,000 with this many mixed evaluations at most (0 skips)")
+    ap.add_argument("--mle-fp64-evals", type=int, default=0,
+                    help="the same n=40,000 fit with FP64 evaluations, at most this many (0 skips)")
+    ap.add_argument("--grad-mle-evals", type=int, default=0,
+                    help="n=22,500 gradient configuration: Nelder-Mead with this many FP64 evaluations at most "
+                         "against L-BFGS-B with the adjoint gradient (0 skips)")
+    ap.add_argument("--grad-mle-iters", type=int, default=60, help="L-BFGS-B iterations at most")
     ap.add_argument("--batched-mle-evals", type=int, default=0,
                     help="fit theta for the 256 batched replicates with this many evaluations each (0 skips)")
     ap.add_argument("--batched-fp64-steps", type=int, default=1, help="timed FP64 runs of the same batch")
-    ap.add_argument("--cpu-sample", type=int, default=3600, help="oracle sample size for cpu_baseline")
-    ap.add_argument("--ref-sample", type=int, default=2500, help="oracle sample size per reference step")
+    ap.add_argument("--probe-peaks", type=int, default=1, help="time the FP64 and TF32 peak probes (0 skips)")
+    ap.add_argument("--theta-grid", type=int, default=1,
+                    help="mixed vs FP64 on the paper's theta grid at n=22,500 (0 skips)")
+    ap.add_argument("--oracle-check-m", type=int, default=0,
+                    help="also time the oracle once on an m x m grid to check the n^3 extrapolation (0 skips)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -338,6 +338,15 @@ exa_status exa_ctx_set_batched_mixed(exa_ctx* ctx, int band, int max_iter);
 exa_status exa_simulate(exa_ctx* ctx, const double* d_locs, const double* d_eps, const double theta[3], int64_t n,
                         exa_prec prec, double* d_z);
 
+/* Issue-rate probe of the FP64 pipes (measurement only; no counterpart in the
+ * paper): kind 0 times FP64 fused multiply-adds, kind 1 the FP64 tensor-core MMA
+ * (mma.sync m8n8k4), each with eight independent chains per thread or warp and
+ * every resident CTA, best of three timed launches after a warm-up, on
+ * cuda_stream (NULL: the legacy default stream).  *tflops (host) receives the
+ * rate in TFLOP/s (2 flops per multiply-add).  Synchronises the stream.
+ * EXA_ERR_ARG for another kind or a NULL tflops, EXA_ERR_CUDA on a failed call. */
+exa_status exa_probe_fp64_rate(void* cuda_stream, int kind, double* tflops);
+
 /* Allocation-free FP64 log-likelihood (no counterpart in the paper; an
  * interface for callers that cannot allocate device memory).
  *

@@ -20,7 +20,7 @@ __all__ = [
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_predict", "exa_fisher", "exa_ctx_set_model",
+    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_probe_fp64_rate", "exa_predict", "exa_fisher", "exa_ctx_set_model",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
                 "exa_ctx_set_model": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_double]),
                 "exa_ctx_set_far_tile_margin": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_ctx_set_gradient_inverse": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_probe_fp64_rate": (ctypes.c_int, [_P, ctypes.c_int, _PD]),
                 "exa_batched_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                                         ctypes.POINTER(_P), _P, ctypes.c_int, _P, _P,
                                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -346,6 +347,15 @@ def exa_ctx_set_tc_pairs(ctx: int, on: int) -> int:
 
 def exa_ctx_set_far_tile_margin(ctx: int, bits: int) -> int:
     return lib().exa_ctx_set_far_tile_margin(_P(ctx), int(bits))
+
+
+def exa_probe_fp64_rate(cuda_stream: int, kind: int) -> float:
+    """FP64 issue-rate probe (kind 0: DFMA, 1: DMMA) in TFLOP/s; raises on failure."""
+    v = ctypes.c_double()
+    st = lib().exa_probe_fp64_rate(_P(cuda_stream or None), int(kind), ctypes.byref(v))
+    if st != EXA_OK:
+        raise ExaError(st, "exa_probe_fp64_rate failed")
+    return v.value
 
 
 def exa_ctx_set_gradient_inverse(ctx: int, fp64: int) -> int:

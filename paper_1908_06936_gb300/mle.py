@@ -55,7 +55,7 @@ def fit_derivative_free(locs, z, x0=None, prec=EXA_FP64, method="Nelder-Mead", m
             "seconds": dt, "time_per_eval": dt / max(1, len(hist)), "history": hist, "method": method}
 
 
-def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None) -> dict:
+def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec=EXA_FP64) -> dict:
     from scipy.optimize import minimize
 
     c = ctx or Context()
@@ -64,9 +64,9 @@ def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None) -> d
     def fg(th):
         th = np.clip(np.asarray(th, dtype=np.float64), THETA_LOWER, THETA_UPPER)
         try:
-            l, g = c.loglik_grad(locs, z, th.tolist())
+            l, g = c.loglik_grad(locs, z, th.tolist(), prec)
         except ExaError as e:
-            if e.status == 2:
+            if e.status in (2, 6):  # not SPD / refinement stalled: outside the usable region
                 hist.append((th.tolist(), -math.inf))
                 return 1e300, np.zeros(3)
             raise
