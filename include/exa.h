@@ -117,6 +117,13 @@ exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
  * runs on the others.  0 restores the default (16).                        */
 exa_status exa_ctx_set_lookahead(exa_ctx* ctx, int sms);
 
+/* Mixed precision, one-panel phase: once the trailing matrix has fewer than `rows`
+ * rows, the look-ahead stream's SM share grows linearly from exa_ctx_set_lookahead's
+ * to `sms` (reached at rows / 3) and the trailing update's shrinks by as much, since
+ * the look-ahead stream's panel then sets the pace.  rows = 0 turns the ramp off;
+ * rows < 0 and sms = 0 restore the defaults (61440 rows, 76 SMs).            */
+exa_status exa_ctx_set_lookahead_late(exa_ctx* ctx, int64_t rows, int sms);
+
 /* Mixed precision: while the trailing matrix still has at least min_rows rows,
  * panels are applied in pairs (the off-band TF32x3 update of the two panels
  * accumulates in one pass, K = 1024, so each FP64 tile is read and written once
@@ -302,6 +309,22 @@ typedef struct {
   double timed_bytes;     /* algorithmic bytes of the timed launch groups only */
 } exa_kernel_stat;
 exa_status exa_profile_enable(exa_ctx* ctx, int on);
+
+/* Launch timeline (with profiling enabled): start and end of every timed launch
+ * group, in ms from the first timed group of each evaluation (one evaluation per
+ * batch of records), and the stream it ran on (0: the context stream, 1: the
+ * mixed factorisation's look-ahead stream).  exa_profile_timeline_enable clears
+ * the records and turns recording on (1) or off (0); exa_profile_timeline copies
+ * up to max records into out (host), oldest first, and returns how many
+ * (reset != 0 clears them).  At most 2^20 records are kept.                  */
+typedef struct {
+  char name[32];    /* kernel class (as exa_kernel_stat) */
+  int32_t stream;   /* 0 context stream, 1 look-ahead stream */
+  float start_ms;
+  float end_ms;
+} exa_timeline_rec;
+exa_status exa_profile_timeline_enable(exa_ctx* ctx, int on);
+int exa_profile_timeline(exa_ctx* ctx, exa_timeline_rec* out, int max, int reset);
 /* Copy up to max per-class records into out (host); returns how many.  Waits
  * for pending timed launches.  reset != 0 zeroes the accumulators.         */
 int exa_profile_read(exa_ctx* ctx, exa_kernel_stat* out, int max, int reset);

@@ -19,8 +19,8 @@ __all__ = [
     "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "EXA_MIXED_FP32", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
-    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_profile_enable",
-    "exa_profile_read", "KernelStat", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_probe_fp64_rate", "exa_predict", "exa_fisher", "exa_ctx_set_model",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_ctx_set_lookahead_late", "exa_profile_enable",
+    "exa_profile_read", "KernelStat", "exa_profile_timeline_enable", "exa_profile_timeline", "TimelineRec", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_probe_fp64_rate", "exa_predict", "exa_fisher", "exa_ctx_set_model",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -45,6 +45,11 @@ class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
                 ("timed_flops", ctypes.c_double), ("timed_bytes", ctypes.c_double)]
+
+
+class TimelineRec(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("stream", ctypes.c_int32), ("start_ms", ctypes.c_float),
+                ("end_ms", ctypes.c_float)]
 
 
 class ExaResult(ctypes.Structure):
@@ -91,6 +96,7 @@ def lib() -> ctypes.CDLL:
                 "exa_ctx_set_mixed_band": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_ctx_set_lookahead": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_ctx_set_panel_fusion": (ctypes.c_int, [_P, ctypes.c_int64]),
+                "exa_ctx_set_lookahead_late": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int]),
                 "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_loglik_noalloc": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
@@ -107,6 +113,8 @@ def lib() -> ctypes.CDLL:
                                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                         ctypes.POINTER(ctypes.c_float)]),
                 "exa_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.c_int]),
+                "exa_profile_timeline_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+                "exa_profile_timeline": (ctypes.c_int, [_P, ctypes.POINTER(TimelineRec), ctypes.c_int, ctypes.c_int]),
                 "exa_gemm_update": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, _P, _P, _P, _I64,
                                                    ctypes.c_int]),
             }
@@ -246,6 +254,10 @@ def exa_ctx_set_lookahead(ctx: int, sms: int) -> int:
     return lib().exa_ctx_set_lookahead(_P(ctx), int(sms))
 
 
+def exa_ctx_set_lookahead_late(ctx: int, rows: int, sms: int) -> int:
+    return lib().exa_ctx_set_lookahead_late(_P(ctx), int(rows), int(sms))
+
+
 def exa_ctx_set_panel_fusion(ctx: int, min_rows: int) -> int:
     return lib().exa_ctx_set_panel_fusion(_P(ctx), int(min_rows))
 
@@ -330,6 +342,17 @@ def exa_profile_read(ctx: int, reset: int = 0) -> list[dict]:
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "timed_launches": buf[i].timed_launches,
              "ms": buf[i].ms, "flops": buf[i].flops, "bytes": buf[i].bytes, "timed_flops": buf[i].timed_flops,
              "timed_bytes": buf[i].timed_bytes} for i in range(k)]
+
+
+def exa_profile_timeline_enable(ctx: int, on: int) -> int:
+    return lib().exa_profile_timeline_enable(_P(ctx), int(on))
+
+
+def exa_profile_timeline(ctx: int, max_records: int = 1 << 20, reset: int = 0) -> list[tuple]:
+    """Timeline of timed launch groups: (kernel class, stream 0/1, start ms, end ms)."""
+    buf = (TimelineRec * max_records)()
+    k = lib().exa_profile_timeline(_P(ctx), buf, int(max_records), int(reset))
+    return [(buf[i].name.decode(), buf[i].stream, buf[i].start_ms, buf[i].end_ms) for i in range(k)]
 
 
 def exa_ctx_set_batched(ctx: int, tile_nb: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,

@@ -31,6 +31,8 @@ struct exa_ctx {
   size_t held_bytes = 0;
   int tile_nb = 128;     // FP64 tile
   int lookahead_sms = 0;  // SMs reserved for the look-ahead stream (0: default)
+  int64_t late_rows = -1; // one-panel phase: below this many trailing rows the look-ahead share grows (-1: default)
+  int late_sms = 0;       // ... linearly up to this many SMs at late_rows / 3 (0: default)
   int64_t fuse_min_rows = -1;  // two-panel trailing passes down to this many rows (0: off, < 0: default)
   int mixed_band = 0;    // exact-product band (256-wide tiles); 0: from Sigma; < 0: all tiles
   int64_t last_pivot = -1;

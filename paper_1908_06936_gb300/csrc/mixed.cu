@@ -18,6 +18,8 @@ constexpr double kIrFailTol = 1e-8;
 constexpr double kIrQuadTol = 1e-10;  // refinement stops once |z^T d| <= kIrQuadTol |z^T x|
 constexpr int kLookaheadSMs = 16;         // SMs left to the look-ahead stream during a trailing update
 constexpr int64_t kFuseMinRows = 61440;   // two panels per trailing pass down to this many rows
+constexpr int64_t kLateRows = 61440;      // one-panel phase: the look-ahead share grows below this many rows
+constexpr int kLateSMs = 76;              // ... up to this many SMs
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 
@@ -389,15 +391,28 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
     if ((st = region_update(M, ms, k, k + 2, B(k), nullptr, 0)) != EXA_OK) return st;
     ++k;
   }
+  // As the trailing matrix shrinks, the main stream's update of it gets shorter than the
+  // look-ahead stream's panel (FP64 diagonal block, panel solve, splits), which then sets
+  // the pace: below late_rows trailing rows the look-ahead stream's SM share grows linearly
+  // to late_sms (reached at late_rows / 3) and the main stream's shrinks by as much.
+  const int64_t late_rows = c->late_rows < 0 ? kLateRows : c->late_rows;
+  const int late_sms = c->late_sms > 0 ? c->late_sms : kLateSMs;
   for (; k + 1 < T; ++k) {
+    const int64_t rows = npad - (int64_t)(k + 2) * NB;  // rows of the main stream's region update
+    int side_k = side_ctas;
+    if (late_rows > 0 && rows < late_rows && late_sms > side_ctas) {
+      const double f = fmin(1.0, (double)(late_rows - rows) / (double)(late_rows - late_rows / 3));
+      side_k = side_ctas + (int)(f * (late_sms - side_ctas));
+      side_k = side_k < sms - 2 ? side_k & ~1 : (sms - 2) & ~1;
+    }
     // block column k+1 first (everything the side stream needs), on the whole GPU
     if ((st = column_update(M, ms, k, k + 1, B(k), 0)) != EXA_OK) return st;
     cudaEventRecord(c->la_ev[0], ms);
     cudaStreamWaitEvent(ss, c->la_ev[0], 0);
-    if ((st = panel_factor(M, ss, k + 1, B(k + 1), side_ctas)) != EXA_OK) return st;
+    if ((st = panel_factor(M, ss, k + 1, B(k + 1), side_k)) != EXA_OK) return st;
     cudaEventRecord(c->la_ev[1], ss);
     // the rest of the trailing matrix on the remaining SMs
-    if ((st = region_update(M, ms, k, k + 2, B(k), nullptr, main_ctas)) != EXA_OK) return st;
+    if ((st = region_update(M, ms, k, k + 2, B(k), nullptr, sms - side_k)) != EXA_OK) return st;
     cudaStreamWaitEvent(ms, c->la_ev[1], 0);
   }
   return EXA_OK;
@@ -590,6 +605,13 @@ using namespace exa;
 extern "C" exa_status exa_ctx_set_far_tile_margin(exa_ctx* c, int bits) {
   if (!c || bits < 0) return c ? set_err(c, EXA_ERR_ARG, "far-tile margin must be >= 0") : EXA_ERR_ARG;
   c->far_tile_margin = bits;
+  return EXA_OK;
+}
+
+extern "C" exa_status exa_ctx_set_lookahead_late(exa_ctx* c, int64_t rows, int sms) {
+  if (!c || sms < 0 || sms > 150) return c ? set_err(c, EXA_ERR_ARG, "bad late look-ahead share") : EXA_ERR_ARG;
+  c->late_rows = rows < 0 ? -1 : rows;
+  c->late_sms = sms;
   return EXA_OK;
 }
 

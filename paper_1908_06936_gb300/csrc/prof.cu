@@ -42,7 +42,7 @@ ProfScope::~ProfScope() {
   const int ev1 = take_event(p);
   if (ev1 < 0) return;
   cudaEventRecord(p.pool[ev1], s_);
-  p.recs.push_back({kind_, ev0_, ev1, flops_, bytes_});
+  p.recs.push_back({kind_, ev0_, ev1, flops_, bytes_, (c_->side && s_ == c_->side) ? 1 : 0});
 }
 
 void prof_collect(exa_ctx* c) {
@@ -53,6 +53,7 @@ void prof_collect(exa_ctx* c) {
   }
   cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
+  const cudaEvent_t base = p.pool[p.recs.front().ev0];
   for (const ProfRec& r : p.recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.pool[r.ev0], p.pool[r.ev1]) == cudaSuccess) {
@@ -60,8 +61,14 @@ void prof_collect(exa_ctx* c) {
       p.timed[r.kind] += 1;
       p.timed_flops[r.kind] += r.flops;
       p.timed_bytes[r.kind] += r.bytes;
+      float a = 0.f, b = 0.f;
+      if (p.timeline_on && p.timeline.size() < kTimelineMax &&
+          cudaEventElapsedTime(&a, base, p.pool[r.ev0]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, base, p.pool[r.ev1]) == cudaSuccess)
+        p.timeline.push_back({r.kind, r.side, a, b});
     }
   }
+  cudaGetLastError();
   p.recs.clear();
   p.used = 0;
 }
@@ -86,6 +93,31 @@ extern "C" exa_status exa_profile_enable(exa_ctx* c, int on) {
   prof_collect(c);
   c->prof.on = on != 0;
   return EXA_OK;
+}
+
+extern "C" exa_status exa_profile_timeline_enable(exa_ctx* c, int on) {
+  if (!c) return EXA_ERR_ARG;
+  prof_collect(c);
+  c->prof.timeline_on = on != 0;
+  c->prof.timeline.clear();
+  return EXA_OK;
+}
+
+extern "C" int exa_profile_timeline(exa_ctx* c, exa_timeline_rec* out, int max, int reset) {
+  if (!c || !out || max <= 0) return 0;
+  prof_collect(c);
+  Prof& p = c->prof;
+  const int k = (int)(p.timeline.size() < (size_t)max ? p.timeline.size() : (size_t)max);
+  for (int i = 0; i < k; ++i) {
+    const TimelineRec& r = p.timeline[i];
+    memset(&out[i], 0, sizeof(out[i]));
+    strncpy(out[i].name, kNames[r.kind], sizeof(out[i].name) - 1);
+    out[i].stream = r.side;
+    out[i].start_ms = r.t0;
+    out[i].end_ms = r.t1;
+  }
+  if (reset) p.timeline.clear();
+  return k;
 }
 
 extern "C" int exa_profile_read(exa_ctx* c, exa_kernel_stat* out, int max, int reset) {

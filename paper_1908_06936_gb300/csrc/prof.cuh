@@ -34,6 +34,12 @@ struct ProfRec {
   int kind;
   int ev0, ev1;
   double flops, bytes;
+  int side;  // issued on the look-ahead stream
+};
+
+struct TimelineRec {
+  int kind, side;
+  float t0, t1;  // ms from the first timed scope of the batch
 };
 
 struct Prof {
@@ -48,7 +54,11 @@ struct Prof {
   std::vector<cudaEvent_t> pool;
   std::vector<ProfRec> recs;
   size_t used = 0;
+  bool timeline_on = false;          // keep start / end of every timed scope
+  std::vector<TimelineRec> timeline; // bounded (kTimelineMax records)
 };
+
+constexpr size_t kTimelineMax = 1u << 20;
 
 // Scope around the launch(es) of one kernel class on the context's stream.
 class ProfScope {

@@ -10,6 +10,7 @@ kernel (``-s``) and capture one launch (``-c 1``).
   python -m paper_1908_06936_gb300.profile_cases gemm-oz --c 16384
   python -m paper_1908_06936_gb300.profile_cases potrf --n 16384
   python -m paper_1908_06936_gb300.profile_cases matern --m 128
+  python -m paper_1908_06936_gb300.profile_cases timeline --m 300 --out timeline.json
 
 gemm-pair / gemm-oz: exa_gemm_update, C -= A B^T with C (c x c, FP64) and A, B
 (c x k, FP64, standard normal); gemm-pair is the CTA-pair TF32x3 trailing-update
@@ -17,7 +18,10 @@ kernel (k = 1024 reduces two operand pairs per pass, as the fused two-panel pass
 of the factorisation), gemm-oz the exact digit-slice band kernel (k <= 512).
 potrf: exa_potrf of the Matern covariance of an m x m jittered grid (FP64 tiled
 Cholesky: potrf_diag, trsm_panel, syrk_update).  matern: exa_covariance of an
-m x m jittered grid (the generation kernel, lower triangle, one copy).
+m x m jittered grid (the generation kernel, lower triangle, one copy).  timeline: one
+mixed-precision log-likelihood of an m x m jittered grid after a warm-up, with the library's
+launch timeline recorded (exa_profile_timeline: start and end of every launch group on the
+context and look-ahead streams), written as JSON to --out, plus per-stream busy time.
 """
 from __future__ import annotations
 
@@ -43,7 +47,10 @@ def main(argv=None) -> dict:
     from paper_1908_06936_gb300 import synth
 
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["gemm-pair", "gemm-oz", "potrf", "matern"])
+    ap.add_argument("case", choices=["gemm-pair", "gemm-oz", "potrf", "matern", "timeline"])
+    ap.add_argument("--out", default="timeline.json", help="timeline case: output file")
+    ap.add_argument("--late", type=int, nargs=2, default=None, metavar=("ROWS", "SMS"),
+                    help="timeline case: exa_ctx_set_lookahead_late(ROWS, SMS) before the evaluations")
     ap.add_argument("--c", type=int, default=16384, help="rows and columns of C (gemm cases)")
     ap.add_argument("--k", type=int, default=512, help="inner dimension (gemm cases)")
     ap.add_argument("--m", type=int, default=128, help="grid side, n = m^2 (potrf, matern)")
@@ -79,6 +86,30 @@ def main(argv=None) -> dict:
             call()
             ms = _timed(call, s)
             out.update({"n": n, "ms": ms, "tflops_n3_over_3": n ** 3 / 3.0 / (ms * 1e-3) / 1e12})
+        elif args.case == "timeline":
+            m = args.m
+            n = m * m
+            locs = torch.as_tensor(synth.jittered_grid(m, 0), device="cuda")
+            z = torch.as_tensor(synth.normals(n, 0), device="cuda")
+            if args.late:
+                ctx.check(exa.exa_ctx_set_lookahead_late(ctx.handle, args.late[0], args.late[1]))
+            ctx.loglik_ex(locs, z, args.theta, exa.EXA_MIXED_TF32X3)
+            exa.exa_profile_enable(ctx.handle, 1)
+            exa.exa_profile_timeline_enable(ctx.handle, 1)
+            r = ctx.loglik_ex(locs, z, args.theta, exa.EXA_MIXED_TF32X3)
+            tl = exa.exa_profile_timeline(ctx.handle)
+            exa.exa_profile_enable(ctx.handle, 0)
+            with open(args.out, "w") as fh:
+                json.dump({"n": n, "theta": list(args.theta), "result": {k: r[k] for k in ("ms_gen", "ms_chol",
+                                                                                             "ms_solve", "ms_total")},
+                           "timeline": tl}, fh)
+            busy = {}
+            for name, st, a, b in tl:
+                busy.setdefault(st, 0.0)
+                busy[st] += b - a
+            out.update({"n": n, "late": args.late, "loglik": r["loglik"], "records": len(tl), "ms_total": r["ms_total"],
+                        "ms_chol": r["ms_chol"],
+                        "busy_ms_by_stream": busy})
         else:
             m = args.m
             n = m * m
