@@ -547,7 +547,7 @@ def gradient_mle_leg(args, ctx) -> dict:
         torch.cuda.synchronize()
         r = fit()
         out[name] = {"theta_hat": r["theta"], "loglik": r["loglik"], "evals": r["evals"], "seconds": r["seconds"],
-                     "seconds_per_eval": r["time_per_eval"], "method": r["method"]}
+                     "seconds_per_eval": r["time_per_eval"], "method": r["method"], "message": r.get("message")}
     return out
 
 

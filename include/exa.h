@@ -102,13 +102,13 @@ void exa_ctx_destroy(exa_ctx* ctx);
 /* Replace the stream work is issued on.                                    */
 exa_status exa_ctx_set_stream(exa_ctx* ctx, void* cuda_stream);
 
-/* Mixed precision: number of 256-wide tile rows next to the diagonal whose
+/* Mixed precision: number of 512-wide panel rows next to the diagonal whose
  * products use the exact digit-slice arithmetic (the rest use TF32x3).
  * band >= 1 fixes it; a negative value makes every tile exact; 0 (the
  * default) picks it per evaluation from Sigma itself: the widest tile-row
  * offset d whose tiles hold some |Sigma_ij| >= 0.8 sigma^2 (where the Schur
- * complement cancels most), and every tile when nu > 1.2 (smooth fields
- * cancel everywhere).  If the reduced-precision factor loses positive
+ * complement cancels most), one panel more when nu >= 0.75, and every tile
+ * when nu > 1.2 (smooth fields cancel everywhere).  If the reduced-precision factor loses positive
  * definiteness the evaluation is repeated with every tile exact.           */
 exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
 
@@ -132,6 +132,14 @@ exa_status exa_ctx_set_lookahead_late(exa_ctx* ctx, int64_t rows, int sms);
  * and at least four panels.  0 turns it off; a negative value restores the
  * default (61440).  Results differ from the one-panel order only by rounding. */
 exa_status exa_ctx_set_panel_fusion(exa_ctx* ctx, int64_t min_rows);
+
+/* Mixed precision: refinement stopping rule.  resid_target > 0: refine
+ * x = Sigma^-1 z until ||z - Sigma x||_2 / ||z||_2 <= resid_target (or the
+ * residual stops halving, or 10 steps); 0 (the default): stop once a correction
+ * changes z^T x by less than 1e-10 relative (q, and l, are then final to that
+ * accuracy).  exa_result.ir_resid reports the last residual computed.
+ * EXA_ERR_ARG for a negative or non-finite target.                          */
+exa_status exa_ctx_set_refinement(exa_ctx* ctx, double resid_target);
 
 /* Message describing the last error on this context ("" if none).  The
  * string is owned by the context and valid until its next call.           */

@@ -1,0 +1,341 @@
+// FP64 factorisation and inversion of one 512 x 512 diagonal block of the mixed-precision
+// Cholesky (the diagonal tiles that the MP variant of Section II-A, Fig. 1(d), keeps in double
+// precision), as ONE cooperative launch on a few SMs.
+//
+// On this part FP64 issues at ~4 flops per clock per SM, so the block's ~90 MFLOP (Cholesky
+// 512^3/3 and inverse 512^3/3) need ~0.7 ms on 16 SMs; chained as ~30 small launches they took
+// ~4.8 ms, the pace-setter of the look-ahead stream.  Here every CTA of a cooperative grid works
+// through the same steps, separated by grid-wide barriers (bounded waits; every CTA reaches every
+// barrier; a failed pivot only turns values into NaN and is recorded in the status):
+//
+//   Cholesky, right-looking in 64-wide steps j (c0 = 64 j):
+//     (a) CTA 0: D = chol(A_jj) and V_j = D^-1 in shared memory (unblocked, column by column)
+//     (b) L_rj = A_rj V_j^T for the 32-row strips r below, into a scratch panel P (one task per
+//         strip and 32-column half)
+//     (c) A_rc -= L_rj L_cj^T over the 32 x 32 lower tiles of the trailing block, from P, while P
+//         is copied into the matrix; CTA 0 updates the next leaf first and runs its (a) meanwhile
+//   Inverse W = L^-1 by doubling: the 64-inverses V_j are the leaves; a 2b block
+//   [[X_A, 0], [L_BA, X_B]] has inverse [[W_A, 0], [-W_B (L_BA W_A), W_B]], formed for
+//   b = 64, 128, 256 as two rounds of 32 x 32 product tasks each.
+//
+// Outputs: L in the block's lower triangle (upper triangle untouched), log L_ii summed in row
+// order per 128 sub-tile, the four 128 x 128 sub-tile inverses (row-major, zero above the
+// diagonal) and the 512 x 512 inverse (row-major, zero above the diagonal).
+#include <math.h>
+
+#include "exa_internal.cuh"
+
+namespace exa {
+
+constexpr int kDB = 512;        // block size
+constexpr int kDW = 64;         // Cholesky step / inverse leaf
+constexpr int kDT = 32;         // product task tile
+constexpr int kDThreads = 256;
+constexpr int kDSteps = kDB / kDW;
+// scratch (doubles): the eight 64-inverses, the 256 x 256 product of the widest inverse round,
+// then the current Cholesky step's panel (448 x 64)
+constexpr int64_t kDiagT = (int64_t)kDSteps * kDW * kDW;
+constexpr int64_t kDiagP = kDiagT + 256 * 256;
+constexpr int64_t kDiagBar = kDiagP + (int64_t)(kDB - kDW) * kDW;  // barrier counter and abort flag
+constexpr int64_t kDiagScratch = kDiagBar + 2;
+constexpr long long kDiagSpin = 2000000000LL;  // bound of one barrier wait, SM clock cycles (~1 s)
+
+struct DiagArgs {
+  double* a;            // column-major matrix, element (i, j) at a[i + j * ld]
+  int64_t ld, k0;       // block origin (k0, k0)
+  double* w_sub;        // four 128 x 128 row-major sub-tile inverses (w_all + (k0 / 128) 128^2)
+  double* logdet;       // four sub-tile log sums (logdet_part + k0 / 128)
+  double* w2;           // 512 x 512 row-major inverse
+  double* scr;          // kDiagScratch doubles
+  DevStatus* st;
+};
+
+// Grid-wide barrier of the cooperative launch (all CTAs co-resident): CTA leader arrives on a
+// monotone counter and waits, bounded, until all G CTAs of barrier number `n` (1, 2, ...) have
+// arrived.  On time-out the status records it, the abort flag releases every later wait, and the
+// (then meaningless) results are discarded by the caller through the status.
+__device__ __forceinline__ void grid_barrier(unsigned int* count, volatile int* abort, unsigned int target,
+                                             DevStatus* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const long long t0 = clock64();
+    while (*(volatile unsigned int*)count < target && !*abort) {
+      if (clock64() - t0 > kDiagSpin) {
+        if (atomicExch((int*)abort, 1) == 0 && atomicExch(&st->timeout, 1) == 0) st->timeout_where = 71;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// acc[u][v] (u, v in {0, 1}) += sum_k A(r, k) B(c, k) over k in [0, K) for the 32 x 32 tile
+// rows r = 2 ty + u, columns c = 2 tx + v (ty, tx in [0, 16)), with
+// A(r, k) = pa[r * ars + k * acs] and B(c, k) = pb[c * brs + k * bcs]; K a multiple of 32.
+__device__ __forceinline__ void tile_gemm(double acc[2][2], const double* pa, int64_t ars, int64_t acs,
+                                          const double* pb, int64_t brs, int64_t bcs, int K, double* sA,
+                                          double* sB) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += kDT) {
+    __syncthreads();  // the previous chunk (or the caller's use of sA / sB) is finished
+    for (int idx = tid; idx < kDT * kDT; idx += kDThreads) {
+      // consecutive threads walk the dimension with the smaller stride
+      const int p = idx & 31, q = idx >> 5;
+      const int ra = (acs == 1) ? q : p, ka = (acs == 1) ? p : q;
+      const int rb = (bcs == 1) ? q : p, kb = (bcs == 1) ? p : q;
+      // L2 loads (ld.global.cg): the operands were written by other CTAs since the last barrier
+      sA[ra * (kDT + 1) + ka] = __ldcg(pa + (int64_t)ra * ars + (int64_t)(k0 + ka) * acs);
+      sB[rb * (kDT + 1) + kb] = __ldcg(pb + (int64_t)rb * brs + (int64_t)(k0 + kb) * bcs);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kDT; ++k) {
+      const double a0 = sA[(2 * ty) * (kDT + 1) + k], a1 = sA[(2 * ty + 1) * (kDT + 1) + k];
+      const double b0 = sB[(2 * tx) * (kDT + 1) + k], b1 = sB[(2 * tx + 1) * (kDT + 1) + k];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+  }
+}
+
+__device__ __forceinline__ void zero_acc(double acc[2][2]) { acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0; }
+
+// (a) of step j on one CTA: chol of the 64 x 64 diagonal block and its inverse, in S (64 x 65).
+__device__ void diag_leaf(const DiagArgs& g, int j, double* S) {
+  const int tid = threadIdx.x;
+  const int64_t c0 = g.k0 + (int64_t)j * kDW;
+  double* A = g.a + c0 + c0 * g.ld;
+  constexpr int sd = kDW + 1;
+  for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
+    const int i = idx & (kDW - 1), c = idx / kDW;
+    S[i * sd + c] = (i >= c) ? __ldcg(A + i + (int64_t)c * g.ld) : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < kDW; ++c) {
+    double d = S[c * sd + c];
+    if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
+      if (tid == 0) {
+        atomicMin(&g.st->pivot, (long long)(c0 + c));
+        atomicExch(&g.st->info, 1);
+      }
+      d = NAN;  // the rest becomes NaN; every barrier is still reached
+    }
+    const double lc = sqrt(d), inv = 1.0 / lc;
+    __syncthreads();  // every thread has read S[c][c]
+    for (int i = c + 1 + tid; i < kDW; i += kDThreads) S[i * sd + c] *= inv;
+    if (tid == 0) S[c * sd + c] = lc;
+    __syncthreads();
+    // rank-1 update of the trailing lower triangle: 4 threads per column l
+    {
+      const int l = tid & (kDW - 1), part = tid / kDW;
+      if (l > c) {
+        const double slc = S[l * sd + c];
+        for (int i = l + part; i < kDW; i += kDThreads / kDW) S[i * sd + l] = fma(-S[i * sd + c], slc, S[i * sd + l]);
+      }
+    }
+    __syncthreads();
+  }
+  // L back to the matrix (lower triangle)
+  for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
+    const int i = idx & (kDW - 1), c = idx / kDW;
+    if (i >= c) A[i + (int64_t)c * g.ld] = S[i * sd + c];
+  }
+  __syncthreads();
+  // in-place inverse, column c from the already inverted trailing part:
+  //   V_cc = 1 / L_cc,  V_ic = -V_cc sum_{l=c+1..i} V_il L_lc  (i > c)
+  __shared__ double tmp[kDW];
+  for (int c = kDW - 1; c >= 0; --c) {
+    const double vcc = 1.0 / S[c * sd + c];
+    for (int i = c + 1 + tid; i < kDW; i += kDThreads) {
+      double t = 0.0;
+      for (int l = c + 1; l <= i; ++l) t = fma(S[i * sd + l], S[l * sd + c], t);
+      tmp[i] = t;
+    }
+    __syncthreads();
+    for (int i = c + 1 + tid; i < kDW; i += kDThreads) S[i * sd + c] = -tmp[i] * vcc;
+    if (tid == 0) S[c * sd + c] = vcc;
+    __syncthreads();
+  }
+  double* V = g.scr + (int64_t)j * kDW * kDW;  // row-major, zero above the diagonal
+  for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
+    const int r = idx / kDW, c = idx & (kDW - 1);
+    V[idx] = (c <= r) ? S[r * sd + c] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_constant__ DiagArgs g) {
+  extern __shared__ double smem[];
+  double* S = smem;                          // 64 x 65 leaf workspace (CTA 0)
+  double* sA = smem + kDW * (kDW + 1);       // 32 x 33 staging
+  double* sB = sA + kDT * (kDT + 1);
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  unsigned int* bar = (unsigned int*)(g.scr + kDiagBar);
+  volatile int* abort = (volatile int*)(bar + 1);
+  unsigned int nbar = 0;
+  auto sync_all = [&]() { grid_barrier(bar, abort, (++nbar) * (unsigned int)G, g.st); };
+  const int64_t ld = g.ld, k0 = g.k0;
+  double* a = g.a;
+  double* P = g.scr + kDiagP;  // the current step's panel below the leaf, 448 x 64 row-major
+
+  // ---------------- Cholesky in 64-wide steps ----------------
+  // Per step j: (b) the panel below the leaf into P, then (c) the trailing update from P while
+  // P is copied into the matrix; CTA 0 takes the three tiles of the next leaf first and factors
+  // it during the rest of (c) (look-ahead), so the serial leaves overlap the updates.
+  if (b == 0) diag_leaf(g, 0, S);
+  sync_all();
+  for (int j = 0; j < kDSteps; ++j) {
+    const int64_t c0 = k0 + (int64_t)j * kDW;
+    const int below = kDB - (j + 1) * kDW;  // rows of the block below step j
+    const int ns = below / kDT;             // 32-row strips
+    const double* V = g.scr + (int64_t)j * kDW * kDW;
+    // (b) P(r, c) = sum_k A(c0 + 64 + r, c0 + k) V(c, k): one task per strip and 32-column half
+    //     (V is lower triangular, so the first half needs only the first 32 columns of A)
+    for (int t = b; t < 2 * ns; t += G) {
+      const int strip = t >> 1, half = t & 1;
+      const int64_t r0 = c0 + kDW + (int64_t)strip * kDT;
+      double acc[2][2];
+      zero_acc(acc);
+      tile_gemm(acc, a + r0 + c0 * ld, 1, ld, V + half * kDT * kDW, kDW, 1, (half + 1) * kDT, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) P[(strip * kDT + 2 * ty + u) * kDW + half * kDT + 2 * tx + v] = acc[u][v];
+    }
+    sync_all();
+    // (c) A_rc -= L_r L_c^T over the 32 x 32 lower tiles (R >= C) of the rows below step j, from P;
+    //     tiles 0..2 (the next leaf) on CTA 0, which then factors that leaf; the others, and the copy
+    //     of P into the matrix, on CTAs 1..G-1
+    const int nt = ns * (ns + 1) / 2;
+    auto update_tile = [&](int t) {
+      int R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while (R * (R + 1) / 2 > t) --R;
+      while ((R + 1) * (R + 2) / 2 <= t) ++R;
+      const int C = t - R * (R + 1) / 2;
+      const int64_t rr = c0 + kDW + (int64_t)R * kDT, cc = c0 + kDW + (int64_t)C * kDT;
+      double acc[2][2];
+      zero_acc(acc);
+      tile_gemm(acc, P + (int64_t)R * kDT * kDW, kDW, 1, P + (int64_t)C * kDT * kDW, kDW, 1, kDW, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int i = 2 * ty + u, c = 2 * tx + v;
+          if (R == C && c > i) continue;
+          double* pc = a + (rr + i) + (cc + c) * ld;
+          *pc = __ldcg(pc) - acc[u][v];
+        }
+    };
+    const int lead = nt < 3 ? nt : 3;
+    if (b == 0) {
+      for (int t = 0; t < lead; ++t) update_tile(t);
+      if (j + 1 < kDSteps) {
+        __syncthreads();  // the leaf's tiles are written
+        diag_leaf(g, j + 1, S);
+      }
+    } else {
+      for (int t = lead + (b - 1); t < nt; t += G - 1) update_tile(t);
+      for (int64_t idx = (int64_t)(b - 1) * kDThreads + tid; idx < (int64_t)below * kDW;
+           idx += (int64_t)(G - 1) * kDThreads) {
+        const int r = (int)(idx % below), c = (int)(idx / below);
+        a[(c0 + kDW + r) + (c0 + c) * ld] = __ldcg(P + (int64_t)r * kDW + c);
+      }
+    }
+    sync_all();
+  }
+
+  // ---------------- log-determinant parts, leaves of the inverse ----------------
+  for (int s4 = b; s4 < 4 && tid == 0; s4 += G) {
+    double s = 0.0;
+    for (int i = 0; i < 128; ++i) {
+      const int64_t r = k0 + 128 * s4 + i;
+      s += log(__ldcg(a + r + r * ld));
+    }
+    g.logdet[s4] = s;
+  }
+  double* w2 = g.w2;
+  // W2 <- zero above the diagonal, the 64-inverses on the diagonal (other lower entries later)
+  for (int64_t idx = (int64_t)b * kDThreads + tid; idx < (int64_t)kDB * kDB; idx += (int64_t)G * kDThreads) {
+    const int r = (int)(idx / kDB), c = (int)(idx % kDB);
+    if (c > r) {
+      w2[idx] = 0.0;
+    } else if (r / kDW == c / kDW) {
+      const double* V = g.scr + (int64_t)(r / kDW) * kDW * kDW;
+      w2[idx] = __ldcg(V + (r % kDW) * kDW + (c % kDW));
+    }
+  }
+  sync_all();
+
+  // ---------------- inverse by doubling: widths h = 64, 128, 256 ----------------
+  double* T = g.scr + kDiagT;  // h x h product, row-major
+  for (int h = kDW; h < kDB; h *= 2) {
+    const int pairs = kDB / (2 * h);             // blocks of width 2h
+    const int tiles = (h / kDT) * (h / kDT);     // 32 x 32 tiles of one h x h product
+    // round 1: T_p = L_BA W_A  (L_BA: rows p 2h + h .., columns p 2h ..; W_A lower, row-major in w2)
+    for (int t = b; t < pairs * tiles; t += G) {
+      const int p = t / tiles, q = t % tiles, ti = q / (h / kDT), tj = q % (h / kDT);
+      const int64_t o = (int64_t)p * 2 * h;  // block origin within the 512 block
+      double acc[2][2];
+      zero_acc(acc);
+      // T(r, c) = sum_k L(o + h + r, o + k) W(o + k, o + c): W_A(k, c) = 0 for k < c
+      const int kstart = tj * kDT;
+      tile_gemm(acc, a + (k0 + o + h + ti * kDT) + (k0 + o + kstart) * ld, 1, ld,
+                w2 + (o + kstart) * kDB + (o + tj * kDT), 1, kDB, h - kstart, sA, sB);
+      double* Tp = T + (int64_t)p * h * h;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) Tp[(ti * kDT + 2 * ty + u) * h + tj * kDT + 2 * tx + v] = acc[u][v];
+    }
+    sync_all();
+    // round 2: W_BA = -W_B T_p  (W_B lower, row-major in w2 at (o + h, o + h))
+    for (int t = b; t < pairs * tiles; t += G) {
+      const int p = t / tiles, q = t % tiles, ti = q / (h / kDT), tj = q % (h / kDT);
+      const int64_t o = (int64_t)p * 2 * h;
+      const double* Tp = T + (int64_t)p * h * h;
+      double acc[2][2];
+      zero_acc(acc);
+      // W_BA(r, c) = -sum_k W_B(r, k) T(k, c): W_B(r, k) = 0 for k > r
+      const int kend = (ti + 1) * kDT;
+      tile_gemm(acc, w2 + (o + h + ti * kDT) * kDB + (o + h), kDB, 1, Tp + tj * kDT, 1, h, kend, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) w2[(o + h + ti * kDT + 2 * ty + u) * kDB + o + tj * kDT + 2 * tx + v] = -acc[u][v];
+    }
+    sync_all();
+  }
+
+  // ---------------- the four 128 sub-tile inverses (diagonal blocks of W2) ----------------
+  for (int64_t idx = (int64_t)b * kDThreads + tid; idx < 4 * 128 * 128; idx += (int64_t)G * kDThreads) {
+    const int s = (int)(idx / (128 * 128)), rc = (int)(idx % (128 * 128)), r = rc / 128, c = rc % 128;
+    g.w_sub[idx] = __ldcg(w2 + (int64_t)(128 * s + r) * kDB + 128 * s + c);
+  }
+}
+
+size_t diag_block_scratch_doubles() { return (size_t)kDiagScratch; }
+
+cudaError_t launch_diag_block(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_sub, double* logdet_part,
+                              double* w2, double* scratch, DevStatus* st, int grid) {
+  const size_t smem = (size_t)(kDW * (kDW + 1) + 2 * kDT * (kDT + 1)) * sizeof(double);
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([&] {
+    return cudaFuncSetAttribute(diag_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  if (grid < 2) grid = 2;  // CTA 0 runs the leaves; the updates need at least one more CTA
+  e = cudaMemsetAsync(scratch + kDiagBar, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  DiagArgs g{a, ld, k0, w_sub, logdet_part, w2, scratch, st};
+  void* args[] = {&g};
+  // cooperative launch: every CTA is resident at once, so the grid barriers cannot wait on an
+  // unscheduled CTA
+  return cudaLaunchCooperativeKernel((const void*)diag_block_kernel, grid, kDThreads, args, smem, s);
+}
+
+}  // namespace exa

@@ -145,6 +145,13 @@ cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int
                               const MaternTable* tab = nullptr, int panel = 256, double* a2 = nullptr);
 // W (sub*nb square, row-major) <- block diagonal of `sub` inverted nb x nb tiles, zero elsewhere.
 cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w);
+// FP64 Cholesky and inverse of the 512 x 512 diagonal block at (k0, k0) as one cooperative launch
+// of `grid` CTAs (>= 2): L in place, log sums of the four 128 sub-tiles into logdet_part[0..3], their
+// inverses (row-major) into w_sub, the block inverse (row-major) into w2; scratch holds
+// diag_block_scratch_doubles() doubles.
+size_t diag_block_scratch_doubles();
+cudaError_t launch_diag_block(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_sub, double* logdet_part,
+                              double* w2, double* scratch, DevStatus* st, int grid);
 
 // FP64 tiled Cholesky steps (tile nb <= 128, multiple of 64; n multiple of nb).
 // The triangular-solve steps accept nb <= 256.

@@ -22,6 +22,7 @@ constexpr int64_t kLateRows = 61440;      // one-panel phase: the look-ahead sha
 constexpr int kLateSMs = 76;              // ... up to this many SMs
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
+constexpr double kWideBandNu = 0.75;     // from this smoothness one more panel of the band is exact
 
 size_t split_bytes(int64_t rows, int K, bool t3, bool oz) {
   const size_t t3_bytes = t3 ? (size_t)rows * K * 4 : 0;
@@ -88,53 +89,23 @@ static exa_status panel_factor(const MixStep& M, cudaStream_t s, int k, SplitOpe
   exa_ctx* c = M.c;
   double* a = M.a;
   const int64_t ld = M.ld, npad = M.npad;
-  const int NB = kMixNB, nb = kMixSub, SUB = kMixNB / kMixSub;
+  const int NB = kMixNB, nb = kMixSub;
   double* W = (double*)c->w_all.p;
-  double* P = (double*)c->panel.p;       // (NB - 128) x 128 FP64 panel of the in-block TRSM
-  double* tmp = P + (size_t)NB * nb;     // 128 x 128 scratch
   double* LD = (double*)c->logdet_part.p;
   // NB x NB inverse of the diagonal block (row-major); every block's is kept when asked
   double* W2 = c->keep_block_inverses ? (double*)c->mx_wall.p + (size_t)k * kMixNB * kMixNB : (double*)c->mx_w2.p;
-  const double dnb = nb;
   const int64_t k0 = (int64_t)k * NB;
   cudaError_t e = cudaSuccess;
-  // 1. FP64 factorisation of the diagonal block as SUB sub-tiles of 128
-  for (int kk = 0; kk < SUB && e == cudaSuccess; ++kk) {
-    const int64_t s0 = k0 + (int64_t)kk * nb;
-    const int64_t mm = (int64_t)(SUB - 1 - kk) * nb;  // rows below within the block
-    {
-      ProfScope ps(c, PK_POTRF, dnb * dnb * dnb, 24.0 * dnb * dnb, 1, s, true);
-      e = launch_potrf_diag(s, a, ld, s0, nb, W, LD, c->d_status);
-    }
-    if (e == cudaSuccess && mm > 0) {
-      ProfScope p2(c, PK_TRSM64, 2.0 * (double)mm * dnb * dnb, 24.0 * (double)mm * dnb, 1, s, true);
-      e = launch_trsm_panel(s, a, ld, s0, nb, mm, W, P, c->d_status);
-    }
-    if (e == cudaSuccess && mm > 0) {
-      ProfScope p3(c, PK_SYRK64, (double)mm * ((double)mm + 64.0) * dnb, 16.0 * (double)mm * (double)mm, 1, s, true);
-      e = launch_syrk_update(s, a, ld, s0 + nb, mm, nb, P, c->d_status);
-    }
+  // 1. FP64 Cholesky of the diagonal block, its 128 sub-tile inverses and log sums, and
+  // 2. its inverse W = L_kk^-1: one cooperative launch (diag_block.cu)
+  {
+    const int grid = ctas > 0 ? (ctas < 32 ? ctas : 32) : 32;
+    const double nb3 = (double)NB * NB * NB;
+    ProfScope ps(c, PK_POTRF, 2.0 * nb3 / 3.0, 8.0 * (3.0 * NB * NB + 4.0 * nb * nb), 1, s, true);
+    e = launch_diag_block(s, a, ld, k0, W + (k0 / nb) * (int64_t)nb * nb, LD + k0 / nb, W2, (double*)c->mx_dscr.p,
+                          c->d_status, grid);
   }
   if (e != cudaSuccess) return cuda_err(c, e, "diagonal block launch");
-  if (k == M.T - 1 && !c->keep_block_inverses) return EXA_OK;
-  // 2. W = L_kk^-1 by block rows: W_ii from the tiles, W_ij = -W_ii sum_{l=j}^{i-1} L_il W_lj
-  {
-    ProfScope ps(c, PK_DGEMM_SMALL, (double)NB * NB * NB / 3.0, 8.0 * 4.0 * NB * NB, 1 + SUB * (SUB - 1), s, true);
-    const double* wk = W + (k0 / nb) * (int64_t)nb * nb;
-    e = launch_assemble_wblocks(s, wk, nb, SUB, W2);
-    for (int i = 1; i < SUB && e == cudaSuccess; ++i) {
-      for (int j = 0; j < i && e == cudaSuccess; ++j) {
-        const int K = (i - j) * nb;
-        const double* Lrow = a + (k0 + (int64_t)i * nb) + (k0 + (int64_t)j * nb) * ld;
-        e = launch_dgemm_nt_small(s, nb, nb, K, 1.0, Lrow, 1, ld, W2 + (int64_t)(j * nb) * NB + j * nb, 1, NB, 0.0,
-                                  tmp, nb, 1, c->d_status);
-        if (e == cudaSuccess)
-          e = launch_dgemm_nt_small(s, nb, nb, nb, -1.0, wk + (int64_t)i * nb * nb, nb, 1, tmp, 1, nb, 0.0,
-                                    W2 + (int64_t)(i * nb) * NB + j * nb, NB, 1, c->d_status);
-      }
-    }
-  }
-  if (e != cudaSuccess) return cuda_err(c, e, "block inverse launch");
   if (k == M.T - 1) return EXA_OK;  // the last block has no panel below it
   const int64_t r0 = k0 + NB;
   const int64_t m = npad - r0;
@@ -349,6 +320,8 @@ exa_status factor_mixed(exa_ctx* c, double* a, int64_t ld, int64_t npad, exa_pre
   const int nbuf = fuse ? 4 : 2;
   if ((st = ensure_split(c, c->sp_b, c->mx_split_b, NB, NB, true, true)) != EXA_OK) return st;
   if ((st = ensure(c, c->mx_w2, (size_t)NB * NB * sizeof(double), "diagonal block inverse")) != EXA_OK) return st;
+  if ((st = ensure(c, c->mx_dscr, diag_block_scratch_doubles() * sizeof(double), "diagonal block scratch")) != EXA_OK)
+    return st;
   if (c->keep_block_inverses &&
       (st = ensure(c, c->mx_wall, (size_t)T * NB * NB * sizeof(double), "diagonal block inverses")) != EXA_OK)
     return st;
@@ -472,6 +445,11 @@ exa_status mixed_generate_factor(exa_ctx* c, const double* d_locs, int64_t n, co
         break;
       }
     }
+    // smoother fields cancel farther from the diagonal: at n = 22,500, theta = (1, 0.1, 1) the
+    // rule above gives 3 panels and |dl|/|l| = 1.2e-6, one panel more 8.8e-7; at n = 90,000,
+    // theta = (1, 0.03, 1) one more panel also saves a refinement step
+    if (theta[2] >= kWideBandNu) band += 1;
+    if (band > T) band = T;
   } else if (band < 0) {
     band = T;
   }
@@ -547,6 +525,9 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   double* sp = (double*)c->mx_symv.p;
   double rel = 0.0, prev = 1e300;
   bool q_done = false;
+  // stopping rule: a caller's residual target (exa_ctx_set_refinement), rounding level for the
+  // gradient (which needs Sigma^-1 z itself), else the quadratic-form rule (target < 0)
+  const double target = c->ir_target > 0.0 ? c->ir_target : (c->ir_tight ? 0.0 : -1.0);
   int it = 0;
   const int kMaxIt = 10;
   for (;; ++it) {
@@ -560,7 +541,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     if (e != cudaSuccess) return cuda_err(c, e, "refinement launch");
     if ((st = read_status(c)) != EXA_OK) return st;  // synchronises
     rel = sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]);
-    if (!(rel > 1e-15) || it >= kMaxIt || rel > 0.5 * prev) break;
+    if (!(rel > (target > 0.0 ? target : 1e-15)) || it >= kMaxIt || rel > 0.5 * prev) break;
     prev = rel;
     e = solve_llt(c, A, npad, npad, r, d, work, (int*)red);
     if (e == cudaSuccess) e = launch_axpy(s, 1.0, d, x, npad);
@@ -570,7 +551,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
       e = cudaMemcpyAsync(c->h_scalars + 4, c->d_scalars + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
     if ((st = read_status(c)) != EXA_OK) return st;
-    if (!c->ir_tight && fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
+    if (target < 0.0 && fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
       q_done = true;
       ++it;
       break;
@@ -605,6 +586,14 @@ using namespace exa;
 extern "C" exa_status exa_ctx_set_far_tile_margin(exa_ctx* c, int bits) {
   if (!c || bits < 0) return c ? set_err(c, EXA_ERR_ARG, "far-tile margin must be >= 0") : EXA_ERR_ARG;
   c->far_tile_margin = bits;
+  return EXA_OK;
+}
+
+extern "C" exa_status exa_ctx_set_refinement(exa_ctx* c, double resid_target) {
+  if (!c) return EXA_ERR_ARG;
+  if (!(resid_target >= 0.0) || !isfinite(resid_target))
+    return set_err(c, EXA_ERR_ARG, "refinement target must be finite and >= 0");
+  c->ir_target = resid_target;
   return EXA_OK;
 }
 

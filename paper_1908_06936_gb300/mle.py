@@ -56,32 +56,40 @@ def fit_derivative_free(locs, z, x0=None, prec=EXA_FP64, method="Nelder-Mead", m
 
 
 def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec=EXA_FP64) -> dict:
+    """L-BFGS-B with the library's analytic gradient, in u = log(theta) (the three parameters span
+    orders of magnitude between the bounds; the chain rule gives dl/du = theta * dl/dtheta) on the
+    objective -l / n.  Evaluations that are not SPD (or whose refinement stalls) return a large
+    value and a zero gradient, so the line search steps back."""
     from scipy.optimize import minimize
 
     c = ctx or Context()
     hist: list = []
+    n = float(locs.shape[0])
+    lo, hi = np.log(THETA_LOWER), np.log(THETA_UPPER)
 
-    def fg(th):
-        th = np.clip(np.asarray(th, dtype=np.float64), THETA_LOWER, THETA_UPPER)
+    def fg(u):
+        th = np.exp(np.clip(np.asarray(u, dtype=np.float64), lo, hi))
         try:
             l, g = c.loglik_grad(locs, z, th.tolist(), prec)
         except ExaError as e:
             if e.status in (2, 6):  # not SPD / refinement stalled: outside the usable region
                 hist.append((th.tolist(), -math.inf))
-                return 1e300, np.zeros(3)
+                return 1e10, np.zeros(3)
             raise
         hist.append((th.tolist(), l))
-        return -l, -np.asarray(g)
+        return -l / n, -(th * np.asarray(g)) / n
 
     x0 = np.asarray(THETA_LOWER if x0 is None else x0, dtype=np.float64)
     t0 = time.perf_counter()
-    r = minimize(fg, x0, jac=True, method="L-BFGS-B", bounds=list(zip(THETA_LOWER, THETA_UPPER)),
+    r = minimize(fg, np.log(x0), jac=True, method="L-BFGS-B", bounds=list(zip(lo, hi)),
                  options={"maxiter": maxiter})
     dt = time.perf_counter() - t0
     if ctx is None:
         c.close()
-    return {"theta": r.x.tolist(), "loglik": -r.fun, "evals": len(hist), "seconds": dt,
-            "time_per_eval": dt / max(1, len(hist)), "history": hist, "method": "L-BFGS-B+analytic gradient"}
+    th = np.exp(np.clip(r.x, lo, hi))
+    return {"theta": th.tolist(), "loglik": -r.fun * n, "evals": len(hist), "seconds": dt,
+            "time_per_eval": dt / max(1, len(hist)), "history": hist,
+            "method": "L-BFGS-B in log(theta) + analytic gradient", "message": str(r.message)}
 
 
 # ---------------------------------------------------------------------------

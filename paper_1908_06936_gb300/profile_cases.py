@@ -51,6 +51,10 @@ def main(argv=None) -> dict:
     ap.add_argument("--out", default="timeline.json", help="timeline case: output file")
     ap.add_argument("--late", type=int, nargs=2, default=None, metavar=("ROWS", "SMS"),
                     help="timeline case: exa_ctx_set_lookahead_late(ROWS, SMS) before the evaluations")
+    ap.add_argument("--fuse", type=int, default=None,
+                    help="timeline case: exa_ctx_set_panel_fusion(ROWS) before the evaluations")
+    ap.add_argument("--lookahead", type=int, default=None,
+                    help="timeline case: exa_ctx_set_lookahead(SMS) before the evaluations")
     ap.add_argument("--c", type=int, default=16384, help="rows and columns of C (gemm cases)")
     ap.add_argument("--k", type=int, default=512, help="inner dimension (gemm cases)")
     ap.add_argument("--m", type=int, default=128, help="grid side, n = m^2 (potrf, matern)")
@@ -93,6 +97,10 @@ def main(argv=None) -> dict:
             z = torch.as_tensor(synth.normals(n, 0), device="cuda")
             if args.late:
                 ctx.check(exa.exa_ctx_set_lookahead_late(ctx.handle, args.late[0], args.late[1]))
+            if args.fuse is not None:
+                ctx.check(exa.exa_ctx_set_panel_fusion(ctx.handle, args.fuse))
+            if args.lookahead is not None:
+                ctx.check(exa.exa_ctx_set_lookahead(ctx.handle, args.lookahead))
             ctx.loglik_ex(locs, z, args.theta, exa.EXA_MIXED_TF32X3)
             exa.exa_profile_enable(ctx.handle, 1)
             exa.exa_profile_timeline_enable(ctx.handle, 1)
@@ -107,7 +115,8 @@ def main(argv=None) -> dict:
             for name, st, a, b in tl:
                 busy.setdefault(st, 0.0)
                 busy[st] += b - a
-            out.update({"n": n, "late": args.late, "loglik": r["loglik"], "records": len(tl), "ms_total": r["ms_total"],
+            out.update({"n": n, "late": args.late, "fuse": args.fuse, "lookahead": args.lookahead,
+                        "loglik": r["loglik"], "records": len(tl), "ms_total": r["ms_total"],
                         "ms_chol": r["ms_chol"],
                         "busy_ms_by_stream": busy})
         else:

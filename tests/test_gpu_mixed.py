@@ -238,3 +238,28 @@ def test_panel_fusion_setting(ctx):
     assert exa.exa_ctx_set_panel_fusion(ctx.handle, 12345) == exa.EXA_OK
     assert exa.exa_ctx_set_panel_fusion(ctx.handle, -7) == exa.EXA_OK
     assert exa.exa_ctx_set_panel_fusion(0, 1) == exa.EXA_ERR_ARG
+
+
+def test_refinement_to_residual_target(ctx):
+    # with a residual target the refinement continues past the quadratic-form rule: the relative
+    # residual ||z - Sigma x|| / ||z|| reaches 1e-14 (the refinement pin), and l is unchanged to
+    # well within the mixed bound
+    import paper_1908_06936_gb300 as exa
+
+    theta = (1.0, 0.1, 0.5)
+    locs, Z = workload(40, seed=12, theta0=theta)
+    dl, dz = to_dev(locs), to_dev(Z)
+    ref = oracle.loglik(locs, Z, theta)
+    a = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+    assert exa.exa_ctx_set_refinement(ctx.handle, 1e-14) == exa.EXA_OK
+    try:
+        b = ctx.loglik_ex(dl, dz, theta, exa.EXA_MIXED_TF32X3)
+    finally:
+        exa.exa_ctx_set_refinement(ctx.handle, 0.0)
+    print("default: %d steps, resid %.2e; target 1e-14: %d steps, resid %.2e" % (a["ir_iters"], a["ir_resid"],
+                                                                               b["ir_iters"], b["ir_resid"]))
+    assert b["ir_resid"] <= 1e-14
+    assert b["ir_iters"] >= a["ir_iters"]
+    assert abs(b["quad"] - ref["quad"]) <= 1e-12 * abs(ref["quad"])
+    assert abs(b["loglik"] - ref["l"]) <= 1e-6 * abs(ref["l"])
+    assert exa.exa_ctx_set_refinement(ctx.handle, -1.0) == exa.EXA_ERR_ARG
