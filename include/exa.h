@@ -130,7 +130,7 @@ exa_status exa_ctx_set_lookahead_late(exa_ctx* ctx, int64_t rows, int sms);
  * per pair; band tiles keep one exact pass per panel) while the look-ahead
  * stream factors the next two panels.  Needs CTA pairs (exa_ctx_set_tc_pairs)
  * and at least four panels.  0 turns it off; a negative value restores the
- * default (61440).  Results differ from the one-panel order only by rounding. */
+ * default (40960).  Results differ from the one-panel order only by rounding. */
 exa_status exa_ctx_set_panel_fusion(exa_ctx* ctx, int64_t min_rows);
 
 /* Mixed precision: refinement stopping rule.  resid_target > 0: refine

@@ -106,73 +106,129 @@ __device__ __forceinline__ void tile_gemm(double acc[2][2], const double* pa, in
 
 __device__ __forceinline__ void zero_acc(double acc[2][2]) { acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0; }
 
-// (a) of step j on one CTA: chol of the 64 x 64 diagonal block and its inverse, in S (64 x 65).
+// (a) of step j on one CTA: chol of the 64 x 64 diagonal block and its inverse, in shared memory
+// (S: 64 x 65 factor, V: 64 x 65 inverse, T: 2 x 32 x 33 products).  Blocked so that only one
+// warp runs the sequential parts: four 16-column panels, each factored and inverted by warp 0
+// (warp-synchronous), solved below and applied to the trailing columns by all warps; then the
+// 64-inverse by doubling from the four 16-inverses.  On this part FP64 issues at ~2 multiply-adds
+// per clock per SM and its divide and square root are long software sequences, so the leaf is
+// latency-bound: the warp-level panels take the ~200 CTA-wide barriers of a column-by-column
+// leaf down to ~25.
+constexpr int kLeafPW = 16;
+constexpr int kLeafSmem = 2 * kDW * (kDW + 1) + 2 * 32 * 33;  // doubles
+
 __device__ void diag_leaf(const DiagArgs& g, int j, double* S) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t c0 = g.k0 + (int64_t)j * kDW;
   double* A = g.a + c0 + c0 * g.ld;
   constexpr int sd = kDW + 1;
+  double* V = S + kDW * sd;    // inverse, 64 x 65
+  double* T = V + kDW * sd;    // two 32 x 33 products
   for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
     const int i = idx & (kDW - 1), c = idx / kDW;
     S[i * sd + c] = (i >= c) ? __ldcg(A + i + (int64_t)c * g.ld) : 0.0;
+    V[(idx / kDW) * sd + (idx & (kDW - 1))] = 0.0;
   }
   __syncthreads();
-  for (int c = 0; c < kDW; ++c) {
-    double d = S[c * sd + c];
-    if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread reads the same value
-      if (tid == 0) {
-        atomicMin(&g.st->pivot, (long long)(c0 + c));
-        atomicExch(&g.st->info, 1);
+  for (int p0 = 0; p0 < kDW; p0 += kLeafPW) {
+    if (warp == 0) {
+      // factor the 16 x 16 diagonal block (lane = row within the block)
+      for (int c = 0; c < kLeafPW; ++c) {
+        double d = S[(p0 + c) * sd + p0 + c];
+        if (!(d > 0.0) || !isfinite(d)) {  // uniform across the warp
+          if (lane == 0) {
+            atomicMin(&g.st->pivot, (long long)(c0 + p0 + c));
+            atomicExch(&g.st->info, 1);
+          }
+          d = NAN;  // the rest becomes NaN; every barrier is still reached
+        }
+        const double lc = sqrt(d), inv = 1.0 / lc;
+        __syncwarp();
+        if (lane > c && lane < kLeafPW) S[(p0 + lane) * sd + p0 + c] *= inv;
+        if (lane == c) S[(p0 + c) * sd + p0 + c] = lc;
+        __syncwarp();
+        for (int e = lane; e < kLeafPW * kLeafPW; e += 32) {
+          const int i = e / kLeafPW, l = e % kLeafPW;
+          if (l > c && i >= l)
+            S[(p0 + i) * sd + p0 + l] = fma(-S[(p0 + i) * sd + p0 + c], S[(p0 + l) * sd + p0 + c], S[(p0 + i) * sd + p0 + l]);
+        }
+        __syncwarp();
       }
-      d = NAN;  // the rest becomes NaN; every barrier is still reached
-    }
-    const double lc = sqrt(d), inv = 1.0 / lc;
-    __syncthreads();  // every thread has read S[c][c]
-    for (int i = c + 1 + tid; i < kDW; i += kDThreads) S[i * sd + c] *= inv;
-    if (tid == 0) S[c * sd + c] = lc;
-    __syncthreads();
-    // rank-1 update of the trailing lower triangle: 4 threads per column l
-    {
-      const int l = tid & (kDW - 1), part = tid / kDW;
-      if (l > c) {
-        const double slc = S[l * sd + c];
-        for (int i = l + part; i < kDW; i += kDThreads / kDW) S[i * sd + l] = fma(-S[i * sd + c], slc, S[i * sd + l]);
+      // invert it into V's diagonal block, column by column from the last:
+      //   V_cc = 1 / L_cc,  V_ic = -V_cc sum_{l=c+1..i} V_il L_lc  (i > c)
+      for (int c = kLeafPW - 1; c >= 0; --c) {
+        const double vcc = 1.0 / S[(p0 + c) * sd + p0 + c];
+        if (lane > c && lane < kLeafPW) {
+          double t = 0.0;
+          for (int l = c + 1; l <= lane; ++l) t = fma(V[(p0 + lane) * sd + p0 + l], S[(p0 + l) * sd + p0 + c], t);
+          V[(p0 + lane) * sd + p0 + c] = -t * vcc;
+        }
+        if (lane == c) V[(p0 + c) * sd + p0 + c] = vcc;
+        __syncwarp();
       }
     }
     __syncthreads();
+    const int m = kDW - p0 - kLeafPW;  // rows below the panel within the leaf
+    if (m > 0) {
+      // panel rows below by forward substitution, one row per thread:
+      //   L_rq = (A_rq - sum_{k < q} L_rk L_qk) / L_qq   (multiplied by V_qq = 1 / L_qq)
+      // (substitution rather than a product with the 16-inverse: on the ill-conditioned blocks of
+      // smooth fields the product's forward error, ~cond(L) u, shows in the log-determinant)
+      if (tid < m) {
+        const int r = p0 + kLeafPW + tid;
+        for (int q = 0; q < kLeafPW; ++q) {
+          double t = S[r * sd + p0 + q];
+          for (int k = 0; k < q; ++k) t = fma(-S[r * sd + p0 + k], S[(p0 + q) * sd + p0 + k], t);
+          S[r * sd + p0 + q] = t * V[(p0 + q) * sd + p0 + q];
+        }
+      }
+      __syncthreads();
+      // trailing update of the leaf: S_il -= sum_k L_ik L_lk over the panel's 16 columns
+      for (int idx = tid; idx < m * m; idx += kDThreads) {
+        const int i = p0 + kLeafPW + idx / m, l = p0 + kLeafPW + idx % m;
+        if (i < l) continue;
+        double t = S[i * sd + l];
+#pragma unroll
+        for (int k = 0; k < kLeafPW; ++k) t = fma(-S[i * sd + p0 + k], S[l * sd + p0 + k], t);
+        S[i * sd + l] = t;
+      }
+      __syncthreads();
+    }
   }
   // L back to the matrix (lower triangle)
   for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
     const int i = idx & (kDW - 1), c = idx / kDW;
     if (i >= c) A[i + (int64_t)c * g.ld] = S[i * sd + c];
   }
-  __syncthreads();
-  // in-place inverse, column c from the already inverted trailing part:
-  //   V_cc = 1 / L_cc,  V_ic = -V_cc sum_{l=c+1..i} V_il L_lc  (i > c)
-  __shared__ double tmp[kDW];
-  for (int c = kDW - 1; c >= 0; --c) {
-    const double vcc = 1.0 / S[c * sd + c];
-    for (int i = c + 1 + tid; i < kDW; i += kDThreads) {
+  // V = L^-1 by doubling: [[V_A, 0], [L_BA, V_B]]^-1 has off-diagonal block -V_B (L_BA V_A)
+  for (int h = kLeafPW; h < kDW; h *= 2) {
+    const int pairs = kDW / (2 * h);
+    for (int idx = tid; idx < pairs * h * h; idx += kDThreads) {
+      const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
       double t = 0.0;
-      for (int l = c + 1; l <= i; ++l) t = fma(S[i * sd + l], S[l * sd + c], t);
-      tmp[i] = t;
+      for (int k = c; k < h; ++k) t = fma(S[(o + h + r) * sd + o + k], V[(o + k) * sd + o + c], t);
+      T[p * 32 * 33 + r * 33 + c] = t;
     }
     __syncthreads();
-    for (int i = c + 1 + tid; i < kDW; i += kDThreads) S[i * sd + c] = -tmp[i] * vcc;
-    if (tid == 0) S[c * sd + c] = vcc;
+    for (int idx = tid; idx < pairs * h * h; idx += kDThreads) {
+      const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
+      double t = 0.0;
+      for (int k = 0; k <= r; ++k) t = fma(V[(o + h + r) * sd + o + h + k], T[p * 32 * 33 + k * 33 + c], t);
+      V[(o + h + r) * sd + o + c] = -t;
+    }
     __syncthreads();
   }
-  double* V = g.scr + (int64_t)j * kDW * kDW;  // row-major, zero above the diagonal
+  double* Vg = g.scr + (int64_t)j * kDW * kDW;  // row-major, zero above the diagonal
   for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
     const int r = idx / kDW, c = idx & (kDW - 1);
-    V[idx] = (c <= r) ? S[r * sd + c] : 0.0;
+    Vg[idx] = (c <= r) ? V[r * sd + c] : 0.0;
   }
 }
 
 __global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_constant__ DiagArgs g) {
   extern __shared__ double smem[];
-  double* S = smem;                          // 64 x 65 leaf workspace (CTA 0)
-  double* sA = smem + kDW * (kDW + 1);       // 32 x 33 staging
+  double* S = smem;                          // leaf workspace (CTA 0), kLeafSmem doubles
+  double* sA = smem + kLeafSmem;             // 32 x 33 staging
   double* sB = sA + kDT * (kDT + 1);
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   unsigned int* bar = (unsigned int*)(g.scr + kDiagBar);
@@ -322,7 +378,7 @@ size_t diag_block_scratch_doubles() { return (size_t)kDiagScratch; }
 
 cudaError_t launch_diag_block(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_sub, double* logdet_part,
                               double* w2, double* scratch, DevStatus* st, int grid) {
-  const size_t smem = (size_t)(kDW * (kDW + 1) + 2 * kDT * (kDT + 1)) * sizeof(double);
+  const size_t smem = (size_t)(kLeafSmem + 2 * kDT * (kDT + 1)) * sizeof(double);
   static PerDeviceOnce attr_once;
   cudaError_t e = attr_once([&] {
     return cudaFuncSetAttribute(diag_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
