@@ -518,29 +518,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       }
       fence_after();
       const int64_t row = g.c_row0 + (int64_t)bi * TILE + (int64_t)rank * HALF_ROWS + r;
-      const int64_t col0 = g.c_col0 + (int64_t)bj * TILE;
+      const int64_t col0 = g.c_col0 + (int64_t)bj * TILE + half * 128;
       double* cp = g.C + row + col0 * g.ldc;
-#pragma unroll 1
-      for (int h2 = 0; h2 < 4; ++h2) {
-        const int cb = half * 128 + h2 * 32;
-        double cv[32];
+      // eight 16-column chunks of this warp's 128 columns, the C loads of chunk q + 1 issued
+      // before chunk q is drained from TMEM, so their latency hides behind its conversion and stores
+      double cbuf[2][16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)(cb + j) * g.ldc);
+      for (int j = 0; j < 16; ++j) cbuf[0][j] = g.store ? 0.0 : __ldcs(cp + (int64_t)j * g.ldc);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          uint32_t acc[16];
-          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * TILE + cb + c * 16, acc);
-          tmem_ld_wait();
-          if (h2 == 3 && c == 1) {
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(accempty_l[b]);
-          }
+      for (int q = 0; q < 8; ++q) {
+        if (q + 1 < 8) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const double v = f32_bits_to_f64(acc[j]);
-            __stcs(cp + (int64_t)(cb + c * 16 + j) * g.ldc, g.store ? v : cv[c * 16 + j] - v);
-          }
+          for (int j = 0; j < 16; ++j)
+            cbuf[(q + 1) & 1][j] = g.store ? 0.0 : __ldcs(cp + (int64_t)((q + 1) * 16 + j) * g.ldc);
+        }
+        uint32_t acc[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * TILE + half * 128 + q * 16, acc);
+        tmem_ld_wait();
+        if (q == 7) {
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(accempty_l[b]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const double v = f32_bits_to_f64(acc[j]);
+          __stcs(cp + (int64_t)(q * 16 + j) * g.ldc, g.store ? v : cbuf[q & 1][j] - v);
         }
       }
       ++it;
