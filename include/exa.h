@@ -212,7 +212,14 @@ exa_status exa_ctx_set_gradient_inverse(exa_ctx* ctx, int fp64);
  *             stay FP64), then x = Sigma^-1 z refined in FP64 against an FP64
  *             copy of Sigma, q = z^T x; a replicate whose refinement stalls
  *             above a 1e-8 relative residual reports EXA_ERR_IR_NOCONV.
- *             Other precisions return EXA_ERR_ARG.
+ *             EXA_MIXED_TF32X3: the same precision pattern on the tensor cores,
+ *             step-synchronous over 128-wide tile columns: per step one launch
+ *             factors every replicate's FP64 diagonal tile, then grouped tcgen05
+ *             launches run every replicate's panel solve and trailing update as
+ *             TF32x3 128 x 128 tiles (FP32 accumulation, FP64 tiles); the same
+ *             FP64 refinement.  exa_ctx_set_batched's tile and CTA options and
+ *             the FP64 band of exa_ctx_set_batched_mixed apply to the persistent
+ *             forms only.  EXA_MIXED_BF16X3 returns EXA_ERR_ARG.
  *   h_n       host array of nrep sizes (each >= 1).
  *   d_locs    host array of nrep DEVICE pointers, replicate r has h_n[r] x 2 locations.
  *   d_z       host array of nrep DEVICE pointers, h_n[r] observations each.

@@ -35,6 +35,7 @@
 
 #include "bessel.cuh"
 #include "ctx.cuh"
+#include "gemm_tc.cuh"
 
 namespace exa {
 
@@ -757,12 +758,28 @@ __global__ void __launch_bounds__(kIrThreads) batched_ir_kernel(
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
+struct TcStep {
+  int diag_off, ndiag;       // DiagTileTask range
+  int wsplit_off, psplit_off, nset, max_m;  // SplitTask ranges (inverse tiles, panels) and panel rows
+  int trsm_off, ntrsm;       // TcTask ranges
+  int upd_off, nupd;
+};
+
 struct BatchPlan {
   std::vector<int64_t> ns;
   int nb = 0;
   int stall = 0;
   bool mixed = false;
   int ntasks = 0;
+  // tensor-core form (step-synchronous): per-step launch ranges, and the buffers the device task
+  // lists point into (a change of any of them rebuilds the lists)
+  bool tc = false;
+  std::vector<TcStep> steps;
+  const void* tc_mat = nullptr;
+  const void* tc_work = nullptr;
+  const void* tc_meta = nullptr;
+  int64_t ps_rows = 0;
+  SplitOperand ps, ws;
 };
 
 // Work-list order.  Every task gets its bottom level: the longest path, in
@@ -1023,6 +1040,292 @@ static exa_status batched_run(exa_ctx* c, int nrep, const int64_t* h_n, const do
   return EXA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core batched form (EXA_MIXED_TF32X3): step-synchronous over 128-wide tile columns,
+// every replicate advancing together.  Per step k, for the replicates that still have tile
+// column k:
+//   1. FP64 Cholesky and inverse W_k of each diagonal tile (one launch, a CTA per tile);
+//   2. TF32 hi/lo splits of every W_k and of every panel below (two launches, all replicates'
+//      rows stacked in one operand);
+//   3. panel solve L_ik = A_ik W_k^T as ONE grouped tcgen05 launch of TF32x3 128 x 128 tiles;
+//   4. split of the solved panels (one launch);
+//   5. trailing update A_ij -= L_ik L_jk^T as ONE grouped tcgen05 launch over every replicate's
+//      trailing lower tiles.
+// Then the FP64 refinement of x = Sigma^-1 z per replicate (as the FP32 form).  Everything is
+// stream-ordered with no host synchronisation (graph-capturable); the task lists depend only on
+// the replicate sizes and are uploaded when they change.
+// ---------------------------------------------------------------------------
+constexpr int kTcNB = 128;
+
+__global__ void batched_tc_finish_kernel(int nrep, const BMeta* __restrict__ M, const DevStatus* __restrict__ rst,
+                                         const DevStatus* __restrict__ st, int* __restrict__ cnt,
+                                         int32_t* __restrict__ rstatus) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrep) return;
+  const BMeta m = M[r];
+  if (rstatus[r] == EXA_OK) {
+    if (st->timeout) rstatus[r] = EXA_ERR_TIMEOUT;
+    else if (rst[r].info) rstatus[r] = EXA_ERR_NOT_SPD;
+  }
+  cnt[m.co + tri_index((int)m.T - 1, (int)m.T - 1)] = (int)m.T;  // factorisation done (refinement's check)
+}
+
+static exa_status batched_run_tc(exa_ctx* c, int nrep, const int64_t* h_n, const double* const* d_locs,
+                                 const double* const* d_z, const double* d_theta, double* d_loglik,
+                                 int32_t* d_status) {
+  constexpr int NB = kTcNB;
+  cudaStream_t s = c->stream;
+  BatchPlan& P = *c->bplan;
+  const bool same_shape = P.tc && P.nb == NB && (int)P.ns.size() == nrep && std::equal(P.ns.begin(), P.ns.end(), h_n);
+  std::vector<BMeta> meta(nrep);
+  int64_t mo = 0, wo = 0, co = 0, lo = 0, vo = 0, gt = 0;
+  int Tmax = 0;
+  for (int r = 0; r < nrep; ++r) {
+    BMeta& m = meta[r];
+    m.n = h_n[r];
+    m.npad = round_up(h_n[r], NB);
+    m.T = m.npad / NB;
+    m.mo = mo;
+    m.wo = wo;
+    m.co = co;
+    m.lo = lo;
+    m.vo = vo;
+    m.gt = gt;
+    m.locs = d_locs[r];
+    m.z = d_z[r];
+    mo += round_up(m.npad * m.npad, 32);
+    wo += m.T * NB * NB;
+    co += m.T * (m.T + 1) / 2;
+    lo += m.T;
+    vo += m.npad;
+    gt += m.T * (m.T + 1) / 2;
+    Tmax = m.T > Tmax ? (int)m.T : Tmax;
+  }
+  if (Tmax > 32000) return set_err(c, EXA_ERR_ARG, "replicate too large for the batched form");
+  std::vector<int> order(nrep);
+  for (int r = 0; r < nrep; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return h_n[x] > h_n[y]; });
+  // panel rows of step 0 (the most): every replicate's rows below its first tile
+  int64_t ps_rows = 0;
+  for (int r = 0; r < nrep; ++r) ps_rows += meta[r].npad - NB;
+  ps_rows = round_up(ps_rows > 0 ? ps_rows : NB, NB);
+  // device layout of bt_meta: meta | order | params | tables | ctl | counters | replicate statuses
+  const size_t meta_b = round_up((int64_t)nrep * sizeof(BMeta), 256);
+  const size_t ord_b = round_up((int64_t)nrep * sizeof(int), 256);
+  const size_t par_b = round_up((int64_t)nrep * sizeof(MaternParams), 256);
+  const size_t tab_b = round_up((int64_t)nrep * sizeof(MaternTable), 256);
+  const size_t ctl_b = 256;
+  const size_t cnt_b = round_up(co * (int64_t)sizeof(int), 256);
+  const size_t rst_b = round_up((int64_t)nrep * sizeof(DevStatus), 256);
+  constexpr int64_t kNodes = kTabSeg * (kTabDeg + 1);
+  const size_t nodes_b = (size_t)nrep * kNodes * sizeof(double);
+  exa_status st;
+  if ((st = ensure(c, c->bt_meta, meta_b + ord_b + par_b + tab_b + ctl_b + cnt_b + rst_b, "batched metadata")) !=
+      EXA_OK)
+    return st;
+  if ((st = ensure(c, c->bt_mat, (size_t)mo * sizeof(double), "batched matrices")) != EXA_OK) return st;
+  if ((st = ensure(c, c->bt_mat2, (size_t)mo * sizeof(double), "batched FP64 copies")) != EXA_OK) return st;
+  const size_t work_b = (size_t)(wo + lo) * sizeof(double);
+  if ((st = ensure(c, c->bt_work, work_b > nodes_b ? work_b : nodes_b, "batched inverses")) != EXA_OK) return st;
+  if ((st = ensure(c, c->bt_vec, (size_t)3 * vo * sizeof(double), "batched vectors")) != EXA_OK) return st;
+  const bool ps_new = c->bt_ps.bytes < split_bytes(ps_rows, NB, true, false) + 1024 ||
+                      c->bt_ws.bytes < split_bytes((int64_t)nrep * NB, NB, true, false) + 1024;
+  if ((st = ensure_split(c, P.ps, c->bt_ps, ps_rows, NB, true, false)) != EXA_OK) return st;
+  if ((st = ensure_split(c, P.ws, c->bt_ws, (int64_t)nrep * NB, NB, true, false)) != EXA_OK) return st;
+  uint8_t* base = (uint8_t*)c->bt_meta.p;
+  BMeta* dM = (BMeta*)base;
+  int* dOrd = (int*)(base + meta_b);
+  MaternParams* dP = (MaternParams*)(base + meta_b + ord_b);
+  MaternTable* dTab = (MaternTable*)(base + meta_b + ord_b + par_b);
+  int* dCnt = (int*)(base + meta_b + ord_b + par_b + tab_b + ctl_b);
+  DevStatus* dRst = (DevStatus*)(base + meta_b + ord_b + par_b + tab_b + ctl_b + cnt_b);
+  double* mat = (double*)c->bt_mat.p;
+  double* wbuf = (double*)c->bt_work.p;
+  double* ldpart = wbuf + wo;
+  // task lists (rebuilt when the sizes or the buffers they point into change)
+  const bool rebuild = !same_shape || ps_new || P.tc_mat != c->bt_mat.p || P.tc_work != c->bt_work.p ||
+                       P.tc_meta != c->bt_meta.p;
+  std::vector<DiagTileTask> diag;
+  std::vector<SplitTask> spl;
+  std::vector<TcTask> tc;
+  if (rebuild) {
+    P.steps.clear();
+    for (int k = 0; k < Tmax; ++k) {
+      TcStep stp{};
+      stp.diag_off = (int)diag.size();
+      for (int r = 0; r < nrep; ++r) {
+        const BMeta& m = meta[r];
+        if (m.T <= k) continue;
+        diag.push_back({mat + m.mo, m.npad, (int64_t)k * NB, ldpart + m.lo + k, wbuf + m.wo + (int64_t)k * NB * NB,
+                        dRst + r});
+      }
+      stp.ndiag = (int)diag.size() - stp.diag_off;
+      // replicates with a panel below tile k
+      std::vector<int> set;
+      for (int r = 0; r < nrep; ++r)
+        if (meta[r].T > k + 1) set.push_back(r);
+      stp.nset = (int)set.size();
+      stp.wsplit_off = (int)spl.size();
+      for (int q = 0; q < stp.nset; ++q) {
+        const BMeta& m = meta[set[q]];
+        spl.push_back({wbuf + m.wo + (int64_t)k * NB * NB, NB, 1, NB, q * NB});
+      }
+      stp.psplit_off = (int)spl.size();
+      std::vector<int> prow(stp.nset);
+      int rows = 0;
+      stp.max_m = 0;
+      for (int q = 0; q < stp.nset; ++q) {
+        const BMeta& m = meta[set[q]];
+        const int mr = (int)(m.npad - (int64_t)(k + 1) * NB);
+        prow[q] = rows;
+        spl.push_back({mat + m.mo + (int64_t)(k + 1) * NB + (int64_t)k * NB * m.npad, 1, m.npad, mr, rows});
+        rows += mr;
+        stp.max_m = mr > stp.max_m ? mr : stp.max_m;
+      }
+      stp.trsm_off = (int)tc.size();
+      for (int q = 0; q < stp.nset; ++q) {
+        const BMeta& m = meta[set[q]];
+        const int nbk = (int)(m.T - k - 1);
+        for (int i = 0; i < nbk; ++i)
+          tc.push_back({mat + m.mo + (int64_t)(k + 1 + i) * NB + (int64_t)k * NB * m.npad, m.npad, prow[q] + i * NB,
+                        q * NB, 0, 0});
+      }
+      stp.ntrsm = (int)tc.size() - stp.trsm_off;
+      stp.upd_off = (int)tc.size();
+      for (int q = 0; q < stp.nset; ++q) {
+        const BMeta& m = meta[set[q]];
+        const int nbk = (int)(m.T - k - 1);
+        for (int i = 0; i < nbk; ++i)
+          for (int j = 0; j <= i; ++j)
+            tc.push_back({mat + m.mo + (int64_t)(k + 1 + i) * NB + (int64_t)(k + 1 + j) * NB * m.npad, m.npad,
+                          prow[q] + i * NB, prow[q] + j * NB, i == j ? 1 : 0, 0});
+      }
+      stp.nupd = (int)tc.size() - stp.upd_off;
+      P.steps.push_back(stp);
+    }
+  }
+  // device task area: diag | split | tc (offsets fixed by the counts)
+  const size_t diag_b = round_up((int64_t)(rebuild ? diag.size() : (size_t)P.ntasks) * sizeof(DiagTileTask), 256);
+  (void)diag_b;
+  size_t nd = 0, nsp = 0, ntc = 0;
+  if (rebuild) {
+    nd = diag.size();
+    nsp = spl.size();
+    ntc = tc.size();
+  } else {
+    const TcStep& L = P.steps.back();
+    nd = (size_t)L.diag_off + L.ndiag;
+    nsp = (size_t)L.psplit_off + L.nset;
+    ntc = (size_t)L.upd_off + L.nupd;
+  }
+  const size_t d_b = round_up((int64_t)nd * sizeof(DiagTileTask), 256);
+  const size_t s_b = round_up((int64_t)nsp * sizeof(SplitTask), 256);
+  const size_t t_b = round_up((int64_t)ntc * sizeof(TcTask), 256);
+  if ((st = ensure(c, c->bt_tasks, d_b + s_b + t_b + 256, "batched task lists")) != EXA_OK) return st;
+  DiagTileTask* dDiag = (DiagTileTask*)c->bt_tasks.p;
+  SplitTask* dSpl = (SplitTask*)((uint8_t*)c->bt_tasks.p + d_b);
+  TcTask* dTc = (TcTask*)((uint8_t*)c->bt_tasks.p + d_b + s_b);
+  // host staging (pinned, owned by the context so captured copies stay valid)
+  const size_t stage_need = meta_b + ord_b + (rebuild ? d_b + s_b + t_b : 0);
+  if (c->bt_stage_bytes < stage_need) {
+    if (c->bt_stage) cudaFreeHost(c->bt_stage);
+    c->bt_stage = nullptr;
+    c->bt_stage_bytes = 0;
+    if (cudaMallocHost(&c->bt_stage, stage_need) != cudaSuccess) return set_err(c, EXA_ERR_NOMEM, "pinned staging");
+    c->bt_stage_bytes = stage_need;
+  }
+  uint8_t* hs = (uint8_t*)c->bt_stage;
+  memcpy(hs, meta.data(), nrep * sizeof(BMeta));
+  memcpy(hs + meta_b, order.data(), nrep * sizeof(int));
+  cudaError_t e = cudaMemcpyAsync(dM, hs, meta_b + ord_b, cudaMemcpyHostToDevice, s);
+  if (rebuild && e == cudaSuccess) {
+    uint8_t* ht = hs + meta_b + ord_b;
+    memcpy(ht, diag.data(), diag.size() * sizeof(DiagTileTask));
+    memcpy(ht + d_b, spl.data(), spl.size() * sizeof(SplitTask));
+    memcpy(ht + d_b + s_b, tc.data(), tc.size() * sizeof(TcTask));
+    e = cudaMemcpyAsync(c->bt_tasks.p, ht, d_b + s_b + t_b, cudaMemcpyHostToDevice, s);
+    P.ns.assign(h_n, h_n + nrep);
+    P.nb = NB;
+    P.tc = true;
+    P.mixed = true;
+    P.stall = 0;
+    P.ntasks = (int)nd;
+    P.tc_mat = c->bt_mat.p;
+    P.tc_work = c->bt_work.p;
+    P.tc_meta = c->bt_meta.p;
+    P.ps_rows = ps_rows;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(dCnt, 0, cnt_b + rst_b, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(DevStatus), s);
+  if (e != cudaSuccess) return cuda_err(c, e, "batched setup");
+  double* dNodes = wbuf;  // scratch until the factorisation overwrites it
+  {
+    ProfScope ps(c, PK_OTHER, 0.0, 0.0, 3);
+    batched_params_kernel<<<(nrep + 63) / 64, 64, 0, s>>>(nrep, d_theta, dP, d_status, c->nugget, c->metric,
+                                                          c->radius);
+    batched_table_nodes_kernel<<<dim3((unsigned)((kNodes + 127) / 128), (unsigned)nrep), 128, 0, s>>>(dP, dNodes);
+    batched_table_coef_kernel<<<dim3((kTabSeg + 127) / 128, (unsigned)nrep), 128, 0, s>>>(dNodes, dTab);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(c, PK_GEN, 0.0, 16.0 * (double)gt * NB * NB / 2);
+    batched_gen_kernel<NB><<<(unsigned)gt, 256, 0, s>>>(nrep, dM, dP, dTab, mat, (double*)c->bt_mat2.p);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "batched generation");
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.K = NB;
+  g.panel = NB;
+  g.enum_mode = kEnumTasks;
+  g.st = c->d_status;
+  for (size_t k = 0; k < P.steps.size() && e == cudaSuccess; ++k) {
+    const TcStep& stp = P.steps[k];
+    {
+      ProfScope ps(c, PK_POTRF, (double)stp.ndiag * NB * NB * NB * 2.0 / 3.0, 0.0, 2);
+      e = launch_potrf128_tasks(s, dDiag + stp.diag_off, stp.ndiag);
+    }
+    if (e != cudaSuccess || stp.nset == 0) continue;
+    {
+      ProfScope ps(c, PK_SPLIT, 0.0, 16.0 * (double)(stp.ntrsm + stp.nset) * NB * NB, 2);
+      e = launch_split_rows_tasks(s, dSpl + stp.wsplit_off, stp.nset, NB, NB, P.ws);
+      if (e == cudaSuccess) e = launch_split_rows_tasks(s, dSpl + stp.psplit_off, stp.nset, stp.max_m, NB, P.ps);
+    }
+    if (e == cudaSuccess) {
+      g.tasks = dTc + stp.trsm_off;
+      g.ntiles = stp.ntrsm;
+      g.store = 1;
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)stp.ntrsm * NB * NB * NB, 16.0 * (double)stp.ntrsm * NB * NB);
+      e = launch_gemm_t3(s, P.ps, P.ws, g);
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(c, PK_SPLIT, 0.0, 16.0 * (double)stp.ntrsm * NB * NB);
+      e = launch_split_rows_tasks(s, dSpl + stp.psplit_off, stp.nset, stp.max_m, NB, P.ps);
+    }
+    if (e == cudaSuccess && stp.nupd > 0) {
+      g.tasks = dTc + stp.upd_off;
+      g.ntiles = stp.nupd;
+      g.store = 0;
+      ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)stp.nupd * NB * NB * NB, 16.0 * (double)stp.nupd * NB * NB);
+      e = launch_gemm_t3(s, P.ps, P.ps, g);
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "batched tensor-core factorisation");
+  batched_tc_finish_kernel<<<(nrep + 127) / 128, 128, 0, s>>>(nrep, dM, dRst, c->d_status, dCnt, d_status);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    double lower = 0.0;
+    for (int r = 0; r < nrep; ++r) lower += 0.5 * (double)meta[r].npad * (double)(meta[r].npad + 1);
+    ProfScope ps(c, PK_TRSV, 0.0, 16.0 * lower);
+    batched_ir_kernel<NB><<<nrep, kIrThreads, 0, s>>>(dOrd, dM, mat, (double*)c->bt_mat2.p, wbuf, ldpart, dCnt,
+                                                       (double*)c->bt_vec.p, vo, d_loglik, d_status,
+                                                       c->batched_max_iter);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "batched refinement launch");
+  return EXA_OK;
+}
+
 void release_batched(exa_ctx* c) {
   if (c->bt_stage) cudaFreeHost(c->bt_stage);
   c->bt_stage = nullptr;
@@ -1044,9 +1347,14 @@ extern "C" exa_status exa_loglik_batched(exa_ctx* c, int32_t nrep, const int64_t
     return set_err(c, EXA_ERR_ARG, "bad batched arguments");
   for (int r = 0; r < nrep; ++r)
     if (h_n[r] < 1 || !d_locs[r] || !d_z[r]) return set_err(c, EXA_ERR_ARG, "replicate %d: bad size or pointer", r);
-  if (prec != EXA_FP64 && prec != EXA_MIXED_FP32)
-    return set_err(c, EXA_ERR_ARG, "the batched form runs in EXA_FP64 or EXA_MIXED_FP32");
+  if (prec != EXA_FP64 && prec != EXA_MIXED_FP32 && prec != EXA_MIXED_TF32X3)
+    return set_err(c, EXA_ERR_ARG, "the batched form runs in EXA_FP64, EXA_MIXED_FP32 or EXA_MIXED_TF32X3");
   if (!c->bplan) c->bplan = new BatchPlan();
+  if (prec == EXA_MIXED_TF32X3) return batched_run_tc(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status);
+  if (c->bplan->tc) {  // the persistent form rebuilds its own work list
+    c->bplan->tc = false;
+    c->bplan->ns.clear();
+  }
   const bool mixed = prec == EXA_MIXED_FP32;
   if (c->batched_nb == 32)
     return mixed ? batched_run<32, true>(c, nrep, h_n, d_locs, d_z, d_theta, d_loglik, d_status)

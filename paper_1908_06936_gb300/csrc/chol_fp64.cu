@@ -123,16 +123,16 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
 // panel).
 constexpr int kPotrfPW = 16;
 
+// The tile's log sum goes to *logdet_out.
 template <int NB>
-__global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restrict__ a, int64_t ld, int64_t k0,
-                                                                 double* __restrict__ logdet_part, DevStatus* st) {
+__device__ __forceinline__ void potrf_blocked_body(double* __restrict__ a, int64_t ld, int64_t k0,
+                                                   double* __restrict__ logdet_out, DevStatus* st) {
   constexpr int PW = kPotrfPW, sd = NB + 1;
   extern __shared__ double sm[];
   double* S = sm;                // NB x sd, element (i, j) at S[i * sd + j]
   double* lg = sm + NB * sd;     // NB logs
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int k = (int)(k0 / NB);
   if (failed(st)) return;
   double* A = a + k0 + k0 * ld;
   if (tid == 0) s_bad = -1;
@@ -209,8 +209,14 @@ __global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restr
   if (tid == 0) {
     double s = 0.0;
     for (int i = 0; i < NB; ++i) s += lg[i];
-    logdet_part[k] = s;
+    *logdet_out = s;
   }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restrict__ a, int64_t ld, int64_t k0,
+                                                                 double* __restrict__ logdet_part, DevStatus* st) {
+  potrf_blocked_body<NB>(a, ld, k0, logdet_part + k0 / NB, st);
 }
 
 // W_k = L_kk^-1 (row-major, zeros above the diagonal) for the NB x NB diagonal tile that
@@ -226,9 +232,10 @@ __global__ void __launch_bounds__(256) potrf_diag_blocked_kernel(double* __restr
 // Rump and Oishi, SIAM J. Sci. Comput. 26, 2005), so W is as accurate as if the sums
 // were formed in twice the precision: its rounding errors, which the condition number
 // of an ill-conditioned tile would magnify, stay out of the panel solve A W^T.
+// CTA `cta` of `nctas` takes rows cta + nctas w of W (the tile's inverse, row-major at W).
 template <int NB>
-__global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restrict__ a, int64_t ld, int64_t k0,
-                                                         double* __restrict__ w_out, const DevStatus* st) {
+__device__ __forceinline__ void trtri_rows_body(const double* __restrict__ a, int64_t ld, int64_t k0,
+                                                double* __restrict__ W, const DevStatus* st, int cta, int nctas) {
   constexpr int sd = NB + 1, Q = NB / 32;
   extern __shared__ double sm[];
   double* S = sm;  // S[l * sd + j] = L(l, j) for l >= j, 0 above
@@ -240,9 +247,8 @@ __global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restric
     S[l * sd + j] = (l >= j) ? A[l + (int64_t)j * ld] : 0.0;
   }
   __syncthreads();
-  double* W = w_out + (k0 / NB) * (int64_t)NB * NB;
   const int nw = blockDim.x >> 5;
-  for (int i = blockIdx.x + gridDim.x * warp; i < NB; i += gridDim.x * nw) {
+  for (int i = cta + nctas * warp; i < NB; i += nctas * nw) {
     // hi[q] + lo[q] = sum_{m > l} x_m L_mj for column j = lane + 32 q
     double hi[Q], lo[Q];
 #pragma unroll
@@ -269,6 +275,40 @@ __global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restric
         }
     }
   }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restrict__ a, int64_t ld, int64_t k0,
+                                                         double* __restrict__ w_out, const DevStatus* st) {
+  trtri_rows_body<NB>(a, ld, k0, w_out + (k0 / NB) * (int64_t)NB * NB, st, blockIdx.x, gridDim.x);
+}
+
+// Batched diagonal tiles (NB = 128): task blockIdx.y factors its tile, then (second launch)
+// 16 CTAs per task invert it.
+__global__ void __launch_bounds__(256) potrf128_tasks_kernel(const DiagTileTask* __restrict__ tasks) {
+  const DiagTileTask t = tasks[blockIdx.y];
+  potrf_blocked_body<128>(t.a, t.ld, t.k0, t.logdet, t.st);
+}
+
+__global__ void __launch_bounds__(256) trtri128_tasks_kernel(const DiagTileTask* __restrict__ tasks) {
+  const DiagTileTask t = tasks[blockIdx.y];
+  trtri_rows_body<128>(t.a, t.ld, t.k0, t.w, t.st, blockIdx.x, gridDim.x);
+}
+
+cudaError_t launch_potrf128_tasks(cudaStream_t s, const DiagTileTask* d_tasks, int ntasks) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(128 * 129 + 128) * sizeof(double);
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([&] {
+    cudaError_t r = cudaFuncSetAttribute(potrf128_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(trtri128_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
+  potrf128_tasks_kernel<<<dim3(1, (unsigned)ntasks), 256, smem, s>>>(d_tasks);
+  trtri128_tasks_kernel<<<dim3(16, (unsigned)ntasks), 256, smem, s>>>(d_tasks);
+  return cudaGetLastError();
 }
 
 template <int NB>

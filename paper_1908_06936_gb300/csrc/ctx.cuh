@@ -73,6 +73,7 @@ struct exa_ctx {
   exa::DevBuf fs_m;         // Fisher information: Sigma^-1 D_k for k = 0, 1, 2
   // batched
   exa::DevBuf bt_mat, bt_meta, bt_vec, bt_work, bt_mat2;
+  exa::DevBuf bt_tasks, bt_ps, bt_ws;  // tensor-core batched form: task lists, panel and inverse split operands
   exa::BatchPlan* bplan = nullptr;  // cached work list of the last shape set
   void* bt_stage = nullptr;         // pinned host staging for the work list / metadata
   size_t bt_stage_bytes = 0;

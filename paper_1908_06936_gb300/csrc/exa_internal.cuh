@@ -145,6 +145,16 @@ cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int
                               const MaternTable* tab = nullptr, int panel = 256, double* a2 = nullptr);
 // W (sub*nb square, row-major) <- block diagonal of `sub` inverted nb x nb tiles, zero elsewhere.
 cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w);
+// One diagonal tile of a batched factorisation: FP64 Cholesky of the 128 x 128 tile at (k0, k0) of a
+// (column-major, ld), its log sum to *logdet and its inverse (row-major) to w; failures to *st.
+struct DiagTileTask {
+  double* a;
+  int64_t ld, k0;
+  double* logdet;
+  double* w;
+  DevStatus* st;
+};
+cudaError_t launch_potrf128_tasks(cudaStream_t s, const DiagTileTask* d_tasks, int ntasks);
 // FP64 Cholesky and inverse of the 512 x 512 diagonal block at (k0, k0) as one cooperative launch
 // of `grid` CTAs (>= 2): L in place, log sums of the four 128 sub-tiles into logdet_part[0..3], their
 // inverses (row-major) into w_sub, the block inverse (row-major) into w2; scratch holds

@@ -87,6 +87,34 @@ __device__ __forceinline__ bool decode_tile(const GemmArgs& g, long long t, int&
   return (long long)bj * TN <= (long long)bi * TM + TM - 1;
 }
 
+// T3 (128 x 128 tiles): operand rows and output origin of tile t, from the enumeration or the
+// launch's task list.  Returns false if the tile is to be skipped.
+struct T3Tile {
+  int ya, yb;
+  double* C;
+  int64_t ldc;
+  bool diag;
+};
+__device__ __forceinline__ bool t3_tile(const GemmArgs& g, long long t, T3Tile& o) {
+  if (g.enum_mode == kEnumTasks) {
+    const TcTask tk = g.tasks[t];
+    o.ya = tk.a_row;
+    o.yb = tk.b_row;
+    o.C = tk.C;
+    o.ldc = tk.ldc;
+    o.diag = tk.lower != 0;
+    return true;
+  }
+  int bi, bj;
+  if (!decode_tile<128, 128>(g, t, bi, bj)) return false;
+  o.ya = g.a_row0 + bi * 128;
+  o.yb = g.b_row0 + bj * 128;
+  o.C = g.C + (g.c_row0 + (int64_t)bi * 128) + (g.c_col0 + (int64_t)bj * 128) * g.ldc;
+  o.ldc = g.ldc;
+  o.diag = g.lower_mask && (bi == bj);
+  return true;
+}
+
 __device__ __forceinline__ void record_timeout(DevStatus* st, int site) {
   if (atomicExch(&st->timeout, 1) == 0) st->timeout_where = site;
 }
@@ -152,9 +180,9 @@ __global__ void __launch_bounds__(kGemmThreads)
     int last_par[STAGES];
     for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
     for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
-      const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + bj * TN;
+      T3Tile tl;
+      if (!t3_tile(g, t, tl)) continue;
+      const int ya = tl.ya, yb = tl.yb;
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
           *abort = 1;
@@ -187,8 +215,8 @@ __global__ void __launch_bounds__(kGemmThreads)
     uint32_t phase = 0;
     int it = 0;
     for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      T3Tile tl;
+      if (!t3_tile(g, t, tl)) continue;
       const int b = it & 1;
       const uint32_t ap = (it >> 1) & 1;
       if (!mbar_wait(&accempty[b], ap ^ 1, abort)) {
@@ -235,8 +263,8 @@ __global__ void __launch_bounds__(kGemmThreads)
     const int r = quad * 32 + lane;
     int it = 0;
     for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      T3Tile tl;
+      if (!t3_tile(g, t, tl)) continue;
       const int b = it & 1;
       const uint32_t ap = (it >> 1) & 1;
       if (!mbar_wait(&accfull[b], ap, abort)) {
@@ -245,17 +273,16 @@ __global__ void __launch_bounds__(kGemmThreads)
         break;
       }
       fence_after();
-      const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
-      const int64_t col0 = g.c_col0 + (int64_t)bj * TN;
-      const bool diag = g.lower_mask && (bi == bj);
-      double* cp = g.C + row + col0 * g.ldc;
+      const bool diag = tl.diag;
+      const int64_t ldc = tl.ldc;
+      double* cp = tl.C + r;
       // two rounds of 32 C loads in flight per thread (64 KB per SM), then drain TMEM
 #pragma unroll 1
       for (int h2 = 0; h2 < 2; ++h2) {
         const int cb = half * 64 + h2 * 32;
         double cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)(cb + j) * g.ldc);
+        for (int j = 0; j < 32; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)(cb + j) * ldc);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           uint32_t acc[16];
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(kGemmThreads)
             const int cc = cb + c * 16 + j;
             if (diag && cc > r) continue;
             const double v = f32_bits_to_f64(acc[j]);
-            __stcs(cp + (int64_t)cc * g.ldc, g.store ? v : cv[c * 16 + j] - v);
+            __stcs(cp + (int64_t)cc * ldc, g.store ? v : cv[c * 16 + j] - v);
           }
         }
       }
@@ -774,12 +801,12 @@ __device__ __forceinline__ uint32_t tf32_bits_of(unsigned long long D, unsigned 
   return (uint32_t)(sign >> 32) | ((uint32_t)fe << 23) | (uint32_t)((mag >> 29) & 0x7FFFFFu);
 }
 
-__global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
-                                                         int rows, int K, float* __restrict__ hi,
-                                                         float* __restrict__ lo, __nv_bfloat16_raw* __restrict__ dig,
-                                                         int64_t dig_stride, int* __restrict__ ex, int out_row0) {
+// Rows [r0, r0 + kSplitRows) of the split (one CTA).
+__device__ __forceinline__ void split_rows_body(const double* __restrict__ src, int64_t rs, int64_t cs, int rows,
+                                                int K, float* __restrict__ hi, float* __restrict__ lo,
+                                                __nv_bfloat16_raw* __restrict__ dig, int64_t dig_stride,
+                                                int* __restrict__ ex, int out_row0, int r0) {
   extern __shared__ double tile[];  // kSplitRows x (K + 1)
-  const int r0 = blockIdx.x * kSplitRows;
   const int tid = threadIdx.x;
   const int ld = K + 1;
   // coalesced along whichever source dimension is contiguous; 16 loads in flight per thread
@@ -873,6 +900,24 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
   }
 }
 
+__global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ src, int64_t rs, int64_t cs,
+                                                         int rows, int K, float* __restrict__ hi,
+                                                         float* __restrict__ lo, __nv_bfloat16_raw* __restrict__ dig,
+                                                         int64_t dig_stride, int* __restrict__ ex, int out_row0) {
+  split_rows_body(src, rs, cs, rows, K, hi, lo, dig, dig_stride, ex, out_row0, blockIdx.x * kSplitRows);
+}
+
+// Many pieces in one launch: blockIdx.y = piece, blockIdx.x = 16-row chunk of it.
+__global__ void __launch_bounds__(256) split_rows_tasks_kernel(const SplitTask* __restrict__ tasks, int K,
+                                                               float* __restrict__ hi, float* __restrict__ lo,
+                                                               __nv_bfloat16_raw* __restrict__ dig,
+                                                               int64_t dig_stride, int* __restrict__ ex) {
+  const SplitTask t = tasks[blockIdx.y];
+  const int r0 = blockIdx.x * kSplitRows;
+  if (r0 >= t.rows) return;  // uniform over the CTA, before any barrier
+  split_rows_body(t.src, t.rs, t.cs, t.rows, K, hi, lo, dig, dig_stride, ex, t.out_row0, r0);
+}
+
 // Per 256-row block maximum of the row exponents (rows past the end count as -infinity).
 __global__ void __launch_bounds__(256) row_exp_blockmax_kernel(const int* __restrict__ ex, int64_t rows,
                                                                int* __restrict__ exb) {
@@ -953,6 +998,22 @@ cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int
   split_rows_kernel<<<(rows + kSplitRows - 1) / kSplitRows, 256, smem, s>>>(src, rs, cs, rows, K, op.hi, op.lo,
                                                         (__nv_bfloat16_raw*)op.dig, (int64_t)op.rows * op.K, op.ex,
                                                         out_row0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_rows_tasks(cudaStream_t s, const SplitTask* d_tasks, int ntasks, int max_rows, int K,
+                                    SplitOperand& op) {
+  if (ntasks <= 0 || max_rows <= 0) return cudaSuccess;
+  if (K > kSplitMaxK) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kSplitRows * (K + 1) * sizeof(double);
+  static PerDeviceOnce attr_once;
+  cudaError_t e = attr_once([] {
+    return cudaFuncSetAttribute(split_rows_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSplitRows * (kSplitMaxK + 1) * (int)sizeof(double));
+  });
+  if (e != cudaSuccess) return e;
+  split_rows_tasks_kernel<<<dim3((unsigned)((max_rows + kSplitRows - 1) / kSplitRows), (unsigned)ntasks), 256, smem,
+                            s>>>(d_tasks, K, op.hi, op.lo, (__nv_bfloat16_raw*)op.dig, (int64_t)op.rows * op.K, op.ex);
   return cudaGetLastError();
 }
 

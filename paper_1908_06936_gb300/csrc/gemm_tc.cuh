@@ -13,8 +13,26 @@ constexpr int kOzSlices = 5;  // 7-bit digits per value in the exact (band) prod
 constexpr int kSplitMaxK = 512;  // longest row the split kernel converts
 constexpr int kSplitRows = 16;   // rows per CTA of the split kernel
 
-// Tile enumeration of one launch.
-enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2 };
+// Tile enumeration of one launch (kEnumTasks: T3 only, tile t described by GemmArgs::tasks[t]).
+enum : int { kEnumFull = 0, kEnumLowerOffBand = 1, kEnumBand = 2, kEnumTasks = 3 };
+
+// One 128 x 128 output tile of a grouped T3 launch: C (column-major, ldc) -= / = A B^T with the
+// tile's A rows from a_row and B rows from b_row of the launch's operands; lower != 0 writes only
+// entries on or below the tile's diagonal.
+struct TcTask {
+  double* C;
+  int64_t ldc;
+  int a_row, b_row;
+  int lower, pad;
+};
+
+// One piece of a batched split: rows [0, rows) of src (element (r, k) at src[r rs + k cs]) to
+// operand rows [out_row0, out_row0 + rows).
+struct SplitTask {
+  const double* src;
+  int64_t rs, cs;
+  int rows, out_row0;
+};
 constexpr int kRasterSuper = 16;  // supertile edge (in 128-tiles) of the lower off-band enumeration
 constexpr int kPairSuper = 16;    // supertile edge (in 256-tiles) of the CTA-pair lower off-band enumeration
 
@@ -50,6 +68,7 @@ struct GemmArgs {
   int a2_row0, b2_row0;
   const int* ea2_blk;
   const int* eb2_blk;
+  const TcTask* tasks;        // kEnumTasks: device array of ntiles tile descriptions (T3 only)
   DevStatus* st;
 };
 
@@ -74,6 +93,9 @@ cudaError_t launch_row_exp_blockmax(cudaStream_t s, SplitOperand& op, int64_t ro
 // rows [0, rows) of src (element (r, k) at src[r*rs + k*cs]) -> operand rows [out_row0, ...)
 cudaError_t launch_split_rows(cudaStream_t s, const double* src, int64_t rs, int64_t cs, int rows, int K,
                               SplitOperand& op, int out_row0);
+// ntasks pieces in one launch (max_rows: the longest piece), each to its own operand rows.
+cudaError_t launch_split_rows_tasks(cudaStream_t s, const SplitTask* d_tasks, int ntasks, int max_rows, int K,
+                                    SplitOperand& op);
 // max_ctas > 0 caps the persistent grid (to leave SMs to concurrent work).
 cudaError_t launch_gemm_t3(cudaStream_t s, const SplitOperand& A, const SplitOperand& B, const GemmArgs& g,
                            int max_ctas = 0);

@@ -256,7 +256,7 @@ def test_batched_mixed_full_config_vs_fp64(ctx):
     assert rel.max() <= MIXED_TOL, (rel.max(), int(rel.argmax()))
 
 
-def test_batched_rejects_tensor_core_split_precisions(ctx):
+def test_batched_rejects_bf16x3_and_unknown_precisions(ctx):
     import torch
     import paper_1908_06936_gb300 as exa
 
@@ -264,9 +264,103 @@ def test_batched_rejects_tensor_core_split_precisions(ctx):
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     st = torch.empty(1, dtype=torch.int32, device="cuda")
     th = to_dev(np.array([1.0, 0.1, 0.5]))
-    for prec in (exa.EXA_MIXED_TF32X3, exa.EXA_MIXED_BF16X3, 7):
+    for prec in (exa.EXA_MIXED_BF16X3, 7):
         rc = exa.exa_loglik_batched(ctx.handle, 1, [36], [to_dev(locs[0])], [to_dev(zs[0])], th, prec, out, st)
         assert rc == exa.EXA_ERR_ARG
+
+
+# ---- tensor-core form (EXA_MIXED_TF32X3): grouped tcgen05 TF32x3 panel solves and updates ----
+TC = 3  # EXA_MIXED_TF32X3
+
+
+def test_batched_tc_vs_oracle(ctx):
+    # uneven sizes, ragged tiles, one replicate of a single point, parameters perturbed per replicate
+    sides = [5, 9, 12, 17, 20, 1, 3, 25, 8, 14, 31, 40]
+    locs, zs = make_batch(sides, seed=51)
+    thetas = synth.theta_perturbations((1.0, 0.1, 0.5), len(sides), seed=6)
+    got, st = run(ctx, locs, zs, thetas, prec=TC)
+    assert np.all(st == 0), st
+    for r in range(len(sides)):
+        ref = oracle.loglik(locs[r], zs[r], thetas[r])["l"]
+        assert abs(got[r] - ref) <= MIXED_TOL * abs(ref), (r, got[r], ref)
+
+
+def test_batched_tc_matches_the_persistent_forms(ctx):
+    # the same batch through the FP64 persistent form, the FP32 persistent form and the tensor-core form
+    sides = [20, 33, 47, 28, 60]
+    locs, zs = make_batch(sides, seed=52)
+    th = np.tile([1.0, 0.1, 0.5], (len(sides), 1))
+    f64, s64 = run(ctx, locs, zs, th, prec=0)
+    tc, stc = run(ctx, locs, zs, th, prec=TC)
+    f32, s32 = run(ctx, locs, zs, th, prec=MIXED)
+    tc2, stc2 = run(ctx, locs, zs, th, prec=TC)  # after the persistent form rebuilt its plan
+    assert np.all(s64 == 0) and np.all(stc == 0) and np.all(s32 == 0) and np.all(stc2 == 0)
+    assert np.array_equal(tc, tc2)  # bitwise repeatable
+    assert np.all(np.abs(tc - f64) <= MIXED_TOL * np.abs(f64)), (tc, f64)
+
+
+def test_batched_tc_not_spd_replicate_is_isolated(ctx):
+    # a replicate with a non-finite location has a non-finite pivot: it reports EXA_ERR_NOT_SPD and
+    # NaN, the others are unaffected
+    import paper_1908_06936_gb300 as exa
+
+    sides = [12, 15, 18]
+    locs, zs = make_batch(sides, seed=53)
+    locs[1] = locs[1].copy()
+    locs[1][150, 0] = float("nan")
+    th = np.tile([1.0, 0.1, 0.5], (3, 1))
+    got, st = run(ctx, locs, zs, th, prec=TC)
+    assert st[1] == exa.EXA_ERR_NOT_SPD and math.isnan(got[1])
+    for r in (0, 2):
+        assert st[r] == 0
+        ref = oracle.loglik(locs[r], zs[r], (1.0, 0.1, 0.5))["l"]
+        assert abs(got[r] - ref) <= MIXED_TOL * abs(ref)
+
+
+def test_batched_tc_graph_replay(ctx):
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    sides = [11, 19, 16, 30]
+    locs, zs = make_batch(sides, seed=81)
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.tile([1.0, 0.1, 0.5], 4))
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    st = torch.empty(4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        exa.exa_ctx_set_stream(ctx.handle, s.cuda_stream)
+        ctx.check(exa.exa_loglik_batched(ctx.handle, 4, ns, dl, dz, th, TC, out, st))
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctx.check(exa.exa_loglik_batched(ctx.handle, 4, ns, dl, dz, th, TC, out, st))
+    exa.exa_ctx_set_stream(ctx.handle, torch.cuda.current_stream().cuda_stream)
+    for new in ([1.3, 0.08, 0.7], [0.6, 0.15, 0.4]):
+        th.copy_(torch.tensor(new * 4, dtype=torch.float64))
+        g.replay()
+        torch.cuda.synchronize()
+        res, sts = out.cpu().numpy(), st.cpu().numpy()
+        assert np.all(sts == 0)
+        for r in range(4):
+            ref = oracle.loglik(locs[r], zs[r], new)["l"]
+            assert abs(res[r] - ref) <= MIXED_TOL * abs(ref)
+
+
+def test_batched_tc_full_config_vs_fp64(ctx):
+    # the 256-replicate configuration: every replicate within the mixed bound of the FP64 form
+    sides = synth.replicate_sides(256, seed=5)
+    locs = [synth.jittered_grid(int(m), 1000 + r) for r, m in enumerate(sides)]
+    zs = [synth.normals(int(m) ** 2, 1000 + r) for r, m in enumerate(sides)]
+    th = np.tile([1.0, 0.1, 0.5], (256, 1))
+    ref, st64 = run(ctx, locs, zs, th, prec=0)
+    got, st = run(ctx, locs, zs, th, prec=TC)
+    assert np.all(st64 == 0) and np.all(st == 0)
+    rel = np.abs(got - ref) / np.abs(ref)
+    print("tensor-core batched: max |dl|/|l| = %.2e" % rel.max())
+    assert rel.max() <= MIXED_TOL, (rel.max(), int(rel.argmax()))
 
 
 def test_batched_autotune_picks_a_candidate_and_keeps_results(ctx, tmp_path):
