@@ -294,8 +294,8 @@ def batched_leg(args, ctx) -> dict:
     dl = [torch.as_tensor(synth.jittered_grid(int(m), 1000 + r), device="cuda") for r, m in enumerate(sides)]
     dz = [torch.as_tensor(synth.normals(int(m) ** 2, 1000 + r), device="cuda") for r, m in enumerate(sides)]
     th = torch.tensor([1.0, 0.1, 0.5] * nrep, dtype=torch.float64, device="cuda")
-    out = {p: torch.empty(nrep, dtype=torch.float64, device="cuda") for p in ("fp64", "mixed")}
-    st = {p: torch.empty(nrep, dtype=torch.int32, device="cuda") for p in ("fp64", "mixed")}
+    out = {p: torch.empty(nrep, dtype=torch.float64, device="cuda") for p in ("fp64", "mixed", "tc")}
+    st = {p: torch.empty(nrep, dtype=torch.int32, device="cuda") for p in ("fp64", "mixed", "tc")}
     flops = sum(((n + 63) // 64 * 64) ** 3 / 3.0 for n in ns)
     s = torch.cuda.Stream()
     res = {}
@@ -323,6 +323,22 @@ def batched_leg(args, ctx) -> dict:
             e1.record(s)
             s.synchronize()
             res["mixed"] = e0.elapsed_time(e1) / reps
+            # tensor-core form (128-wide tiles, TF32x3 panel solves and updates): graph replay too
+            args_t = (ctx.handle, nrep, ns, dl, dz, th, exa.EXA_MIXED_TF32X3, out["tc"], st["tc"])
+            for _ in range(2):
+                ctx.check(exa.exa_loglik_batched(*args_t))
+            s.synchronize()
+            gt = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gt, stream=s):
+                ctx.check(exa.exa_loglik_batched(*args_t))
+            gt.replay()
+            s.synchronize()
+            e0.record(s)
+            for _ in range(reps):
+                gt.replay()
+            e1.record(s)
+            s.synchronize()
+            res["tc"] = e0.elapsed_time(e1) / reps
             exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)  # FP64 leg: tile 64, all resident CTAs
             ctx.check(exa.exa_loglik_batched(ctx.handle, nrep, ns, dl, dz, th, exa.EXA_FP64, out["fp64"], st["fp64"]))
             e0.record(s)
@@ -335,20 +351,26 @@ def batched_leg(args, ctx) -> dict:
         finally:
             exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
             exa.exa_ctx_set_stream(ctx.handle, torch.cuda.current_stream().cuda_stream)
-    lm, l64 = out["mixed"].cpu().numpy(), out["fp64"].cpu().numpy()
-    ok = bool((st["mixed"] == 0).all().item() and (st["fp64"] == 0).all().item())
+    lm, lt, l64 = out["mixed"].cpu().numpy(), out["tc"].cpu().numpy(), out["fp64"].cpu().numpy()
+    ok = bool(all((st[p] == 0).all().item() for p in st))
     rel = np.abs(lm - l64) / np.abs(l64)
+    rel_t = np.abs(lt - l64) / np.abs(l64)
     leg = {"workload": "256 replicate fields, n_i = m_i^2, m_i ~ U{20..80} (jittered grids), theta0=(1, 0.1, 0.5), "
                        "per-replicate Z",
            "sum_n": int(sum(ns)), "flops_n3_over_3": flops, "all_status_ok": ok}
-    for p in ("fp64", "mixed"):
+    for p in ("fp64", "mixed", "tc"):
         leg[p] = {"ms_per_batch": res[p], "replicate_evals_per_s": nrep / (res[p] / 1e3),
                   "tflops": flops / (res[p] / 1e3) / 1e12}
     leg["mixed"]["graph_replays"] = max(1, args.batched_steps)
+    leg["mixed"]["prec"] = "EXA_MIXED_FP32 (persistent dataflow, FP32 off-diagonal tiles)"
     leg["mixed"]["autotuned"] = {"tile_nb": tuned["tile_nb"], "ctas_per_sm": tuned["ctas_per_sm"]}
+    leg["tc"]["graph_replays"] = max(1, args.batched_steps)
+    leg["tc"]["prec"] = "EXA_MIXED_TF32X3 (step-synchronous, tcgen05 TF32x3 panel solves and updates, tile 128)"
     leg["fp64"]["tile_nb"] = 64
     leg["speedup_mixed_vs_fp64"] = res["fp64"] / res["mixed"]
+    leg["speedup_tc_vs_fp64"] = res["fp64"] / res["tc"]
     leg["max_rel_dl_vs_fp64"] = float(rel.max())
+    leg["tc_max_rel_dl_vs_fp64"] = float(rel_t.max())
     return leg
 
 

@@ -360,7 +360,10 @@ exa_status exa_ctx_set_batched(exa_ctx* ctx, int tile_nb, int ctas_per_sm, long 
  * stream), keeps the fastest in the context and returns it (tile_nb,
  * ctas_per_sm, best_ms: host outputs).  Synchronises the stream.  d_loglik /
  * d_status hold the last candidate's results.  On any failure the previous
- * configuration is kept and the error returned.                            */
+ * configuration is kept and the error returned.  EXA_MIXED_TF32X3 (the
+ * tensor-core form, one configuration: 128-wide tiles) is run twice the same
+ * way and reported as tile_nb = 128, ctas_per_sm = 0; the context's options
+ * of the persistent forms stay as they were.                               */
 exa_status exa_batched_autotune(exa_ctx* ctx, int32_t nrep, const int64_t* h_n, const double* const* d_locs,
                                 const double* const* d_z, const double* d_theta, exa_prec prec, double* d_loglik,
                                 int32_t* d_status, int* tile_nb, int* ctas_per_sm, float* best_ms);

@@ -1282,7 +1282,7 @@ static exa_status batched_run_tc(exa_ctx* c, int nrep, const int64_t* h_n, const
   for (size_t k = 0; k < P.steps.size() && e == cudaSuccess; ++k) {
     const TcStep& stp = P.steps[k];
     {
-      ProfScope ps(c, PK_POTRF, (double)stp.ndiag * NB * NB * NB * 2.0 / 3.0, 0.0, 2);
+      ProfScope ps(c, PK_POTRF, (double)stp.ndiag * NB * NB * NB * 2.0 / 3.0, 0.0, 1);
       e = launch_potrf128_tasks(s, dDiag + stp.diag_off, stp.ndiag);
     }
     if (e != cudaSuccess || stp.nset == 0) continue;
@@ -1392,9 +1392,13 @@ extern "C" exa_status exa_batched_autotune(exa_ctx* c, int32_t nrep, const int64
     return cuda_err(c, cudaGetLastError(), "autotune events");
   }
   exa_status st = EXA_OK;
+  // the tensor-core form has one configuration (128-wide tiles, grids sized by the task
+  // lists): it is timed once and reported with ctas_per_sm = 0
+  const bool tc = prec == EXA_MIXED_TF32X3;
   for (int nb : {64, 32}) {
-    const int top = max_ctas_per_sm(nb, mode);
+    const int top = tc ? 1 : max_ctas_per_sm(nb, mode);
     for (int cps : {top, top - 1}) {
+      if (tc && (nb != 64 || cps != 1)) continue;
       if (cps < 1 || st != EXA_OK) continue;
       c->batched_nb = nb;
       c->batched_ctas_per_sm = cps;
@@ -1412,8 +1416,8 @@ extern "C" exa_status exa_batched_autotune(exa_ctx* c, int32_t nrep, const int64
           st = cuda_err(c, e != cudaSuccess ? e : cudaGetLastError(), "autotune timing");
         } else if (ms < best) {
           best = ms;
-          bnb = nb;
-          bcps = cps;
+          bnb = tc ? keep_nb : nb;
+          bcps = tc ? keep_cps : cps;
         }
       }
     }
@@ -1427,8 +1431,8 @@ extern "C" exa_status exa_batched_autotune(exa_ctx* c, int32_t nrep, const int64
   }
   c->batched_nb = bnb;
   c->batched_ctas_per_sm = bcps;
-  *tile_nb = bnb;
-  *ctas_per_sm = bcps;
+  *tile_nb = tc ? 128 : bnb;
+  *ctas_per_sm = tc ? 0 : bcps;
   *best_ms = best;
   return EXA_OK;
 }

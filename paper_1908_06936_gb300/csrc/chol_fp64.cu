@@ -123,17 +123,20 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
 // panel).
 constexpr int kPotrfPW = 16;
 
-// The tile's log sum goes to *logdet_out.
+// The tile's log sum goes to *logdet_out.  Returns true (on every thread) when the tile was
+// factored; L then also sits in the first NB x (NB + 1) doubles of shared memory.
 template <int NB>
-__device__ __forceinline__ void potrf_blocked_body(double* __restrict__ a, int64_t ld, int64_t k0,
+__device__ __forceinline__ bool potrf_blocked_body(double* __restrict__ a, int64_t ld, int64_t k0,
                                                    double* __restrict__ logdet_out, DevStatus* st) {
   constexpr int PW = kPotrfPW, sd = NB + 1;
   extern __shared__ double sm[];
   double* S = sm;                // NB x sd, element (i, j) at S[i * sd + j]
   double* lg = sm + NB * sd;     // NB logs
-  __shared__ int s_bad;
+  __shared__ int s_bad, s_skip;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (failed(st)) return;
+  if (tid == 0) s_skip = failed(st) ? 1 : 0;  // one read, so that every thread takes the same path
+  __syncthreads();
+  if (s_skip) return false;
   double* A = a + k0 + k0 * ld;
   if (tid == 0) s_bad = -1;
   // load the lower triangle (column-major source, consecutive threads on consecutive rows)
@@ -197,7 +200,7 @@ __device__ __forceinline__ void potrf_blocked_body(double* __restrict__ a, int64
       atomicMin(&st->pivot, (long long)(k0 + s_bad));
       atomicExch(&st->info, 1);
     }
-    return;
+    return false;
   }
   // write L back (lower triangle) and the log-determinant part (fixed-order sum)
   for (int idx = tid; idx < NB * NB; idx += 256) {
@@ -211,6 +214,7 @@ __device__ __forceinline__ void potrf_blocked_body(double* __restrict__ a, int64
     for (int i = 0; i < NB; ++i) s += lg[i];
     *logdet_out = s;
   }
+  return true;
 }
 
 template <int NB>
@@ -283,31 +287,72 @@ __global__ void __launch_bounds__(256) trtri_rows_kernel(const double* __restric
   trtri_rows_body<NB>(a, ld, k0, w_out + (k0 / NB) * (int64_t)NB * NB, st, blockIdx.x, gridDim.x);
 }
 
-// Batched diagonal tiles (NB = 128): task blockIdx.y factors its tile, then (second launch)
-// 16 CTAs per task invert it.
-__global__ void __launch_bounds__(256) potrf128_tasks_kernel(const DiagTileTask* __restrict__ tasks) {
-  const DiagTileTask t = tasks[blockIdx.y];
-  potrf_blocked_body<128>(t.a, t.ld, t.k0, t.logdet, t.st);
-}
+// Batched diagonal tiles (NB = 128), one CTA per task: the blocked Cholesky above, then the
+// inverse W = L^-1 (row-major, zeros above the diagonal) from L in shared memory: the eight
+// 16 x 16 diagonal blocks inverted by the eight warps (column by column), then by doubling,
+// [[W_A, 0], [L_BA, W_B]]^-1 = [[W_A, 0], [-W_B (L_BA W_A), W_B]] for widths 16, 32, 64, with
+// the products in shared memory.  Plain FP64 sums: W preconditions the FP64 refinement and
+// feeds TF32 panel solves, so the compensated row inverse of the single-field FP64 path (16
+// CTAs per tile) is not needed here, and one CTA per tile keeps a batch of hundreds of tiles
+// at one wave or two.
+constexpr int kInvSmem = 128 * 129 + 128 + 64 * 64;  // doubles: L, logs, one product
 
-__global__ void __launch_bounds__(256) trtri128_tasks_kernel(const DiagTileTask* __restrict__ tasks) {
-  const DiagTileTask t = tasks[blockIdx.y];
-  trtri_rows_body<128>(t.a, t.ld, t.k0, t.w, t.st, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(256) potrf_inv128_tasks_kernel(const DiagTileTask* __restrict__ tasks) {
+  constexpr int NB = 128, sd = NB + 1, PW = 16;
+  const DiagTileTask t = tasks[blockIdx.x];
+  if (!potrf_blocked_body<NB>(t.a, t.ld, t.k0, t.logdet, t.st)) return;  // uniform over the CTA
+  extern __shared__ double sm[];
+  const double* S = sm;            // L(i, j) at S[i * sd + j]
+  double* T = sm + NB * sd + NB;   // products, at most 64 x 64
+  double* W = t.w;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int idx = tid; idx < NB * NB; idx += 256) {
+    const int r = idx / NB, c = idx % NB;
+    if (c > r) W[idx] = 0.0;  // the strict upper triangle
+  }
+  __syncthreads();
+  {
+    const int p0 = warp * PW;  // warp w inverts diagonal block w
+    for (int c = PW - 1; c >= 0; --c) {
+      const double vcc = 1.0 / S[(p0 + c) * sd + p0 + c];
+      if (lane > c && lane < PW) {
+        double acc = 0.0;
+        for (int l = c + 1; l <= lane; ++l) acc = fma(W[(p0 + lane) * NB + p0 + l], S[(p0 + l) * sd + p0 + c], acc);
+        W[(p0 + lane) * NB + p0 + c] = -acc * vcc;
+      }
+      if (lane == c) W[(p0 + c) * NB + p0 + c] = vcc;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int h = PW; h < NB; h *= 2) {
+    const int pairs = NB / (2 * h);
+    for (int idx = tid; idx < pairs * h * h; idx += 256) {
+      const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
+      double acc = 0.0;
+      for (int k = c; k < h; ++k) acc = fma(S[(o + h + r) * sd + o + k], W[(o + k) * NB + o + c], acc);
+      T[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < pairs * h * h; idx += 256) {
+      const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
+      double acc = 0.0;
+      for (int k = 0; k <= r; ++k) acc = fma(W[(o + h + r) * NB + o + h + k], T[p * h * h + k * h + c], acc);
+      W[(o + h + r) * NB + o + c] = -acc;
+    }
+    __syncthreads();
+  }
 }
 
 cudaError_t launch_potrf128_tasks(cudaStream_t s, const DiagTileTask* d_tasks, int ntasks) {
   if (ntasks <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(128 * 129 + 128) * sizeof(double);
+  const size_t smem = (size_t)kInvSmem * sizeof(double);
   static PerDeviceOnce attr_once;
   cudaError_t e = attr_once([&] {
-    cudaError_t r = cudaFuncSetAttribute(potrf128_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(trtri128_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return r;
+    return cudaFuncSetAttribute(potrf_inv128_tasks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return e;
-  potrf128_tasks_kernel<<<dim3(1, (unsigned)ntasks), 256, smem, s>>>(d_tasks);
-  trtri128_tasks_kernel<<<dim3(16, (unsigned)ntasks), 256, smem, s>>>(d_tasks);
+  potrf_inv128_tasks_kernel<<<(unsigned)ntasks, 256, smem, s>>>(d_tasks);
   return cudaGetLastError();
 }
 

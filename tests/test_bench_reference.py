@@ -1,5 +1,5 @@
 """bench.py's reference arm (the FP64 CPU oracle on the host cores) keeps the JSON-line
-contract: run for real on a small sample, no GPU needed."""
+contract: run for real (the oracle timed on small grids, extrapolated), no GPU needed."""
 import json
 import os
 import subprocess
@@ -11,8 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_json_line():
     env = dict(os.environ, RANK="0", WORLD_SIZE="1")
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
-                          "--warmup", "1", "--ref-sample", "300"], cwd=ROOT, env=env, capture_output=True, text=True,
-                         timeout=600)
+                          "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -24,7 +23,11 @@ def test_reference_arm_json_line():
     assert d["unit"] == "evals/s" and d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["value"] > 0 and d["config"]["n"] == 90000 and "workload" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "300" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "jittered grids" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    # the sample's cost scales to the full workload by (n / n_s)^3
+    # each step timed the oracle on several grid sizes; the fitted a n^2 + b n^3 law gives the full workload's time
+    cv = cb["curve"]
+    assert len(cv["points"]) >= 2 and cv["a_n2"] >= 0 and cv["b_n3"] > 0
+    n = d["config"]["n"]
+    assert abs(cv["a_n2"] * n ** 2 + cv["b_n3"] * n ** 3 - cv["seconds_at_n"]) <= 1e-9 * cv["seconds_at_n"]
     assert abs(d["ms_per_step"] / 1e3 - 1.0 / d["value"]) <= 1e-9 * d["ms_per_step"] / 1e3

@@ -388,3 +388,34 @@ def test_batched_autotune_picks_a_candidate_and_keeps_results(ctx, tmp_path):
     for r_ in range(4):
         ref = oracle.loglik(locs[r_], zs[r_], (1.0, 0.1, 0.5))["l"]
         assert abs(got[r_] - ref) <= MIXED_TOL * abs(ref)
+
+
+def test_batched_autotune_tc_form_reports_its_single_configuration(ctx):
+    # the tensor-core form has one configuration: autotune times it and leaves the persistent
+    # forms' options alone
+    import torch
+    import paper_1908_06936_gb300 as exa
+
+    sides = [8, 15, 21, 12]
+    locs, zs = make_batch(sides, seed=96)
+    ns = [l.shape[0] for l in locs]
+    dl = [to_dev(l) for l in locs]
+    dz = [to_dev(z) for z in zs]
+    th = to_dev(np.tile([1.0, 0.1, 0.5], 4))
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    st = torch.empty(4, dtype=torch.int32, device="cuda")
+    ctx.check(exa.exa_ctx_set_batched(ctx.handle, 32, 1, 0, 0))
+    try:
+        rc, nb, cps, ms = exa.exa_batched_autotune(ctx.handle, 4, ns, dl, dz, th, TC, out, st)
+        ctx.check(rc)
+        assert nb == 128 and cps == 0 and ms > 0
+        assert np.all(st.cpu().numpy() == 0)
+        got = out.cpu().numpy()
+        f32, s32 = run(ctx, locs, zs, np.tile([1.0, 0.1, 0.5], (4, 1)), prec=MIXED)  # still tile 32, 1 CTA/SM
+        assert np.all(s32 == 0)
+    finally:
+        exa.exa_ctx_set_batched(ctx.handle, 0, 0, 0, 0)
+    for r_ in range(4):
+        ref = oracle.loglik(locs[r_], zs[r_], (1.0, 0.1, 0.5))["l"]
+        assert abs(got[r_] - ref) <= MIXED_TOL * abs(ref)
+        assert abs(f32[r_] - ref) <= MIXED_TOL * abs(ref)
