@@ -233,9 +233,9 @@ def make_inputs(m: int, seed: int):
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch's algorithmic bytes) of the same
 # kernel on a C larger than L2; the per-launch traffic of the bench is this ratio times the
 # average algorithmic bytes of its timed launches.  Keyed by kernel class; the capture and its
-# command are summarised in profiles/gemm_t3_pair_bench_n90000.md (all 143 launches of one
+# command are summarised in profiles/gemm_t3_pair_bench_n90000.md (all 122 launches of one
 # n = 90,000 factorisation, 1-pass metrics).
-TRAFFIC_RATIO = {"gemm_tf32x3_pair": 1.368}
+TRAFFIC_RATIO = {"gemm_tf32x3_pair": 1.522}
 
 
 def roofline(stats: list, pk: dict) -> dict:

@@ -36,7 +36,7 @@ constexpr int kDSteps = kDB / kDW;
 // then the current Cholesky step's panel (448 x 64)
 constexpr int64_t kDiagT = (int64_t)kDSteps * kDW * kDW;
 constexpr int64_t kDiagP = kDiagT + 256 * 256;
-constexpr int64_t kDiagBar = kDiagP + (int64_t)(kDB - kDW) * kDW;  // barrier counter and abort flag
+constexpr int64_t kDiagBar = kDiagP + (int64_t)(kDB - kDW) * kDW;  // barrier counter, abort flag, lead counter
 constexpr int64_t kDiagScratch = kDiagBar + 2;
 constexpr long long kDiagSpin = 2000000000LL;  // bound of one barrier wait, SM clock cycles (~1 s)
 
@@ -107,15 +107,21 @@ __device__ __forceinline__ void tile_gemm(double acc[2][2], const double* pa, in
 __device__ __forceinline__ void zero_acc(double acc[2][2]) { acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0; }
 
 // (a) of step j on one CTA: chol of the 64 x 64 diagonal block and its inverse, in shared memory
-// (S: 64 x 65 factor, V: 64 x 65 inverse, T: 2 x 32 x 33 products).  Blocked so that only one
-// warp runs the sequential parts: four 16-column panels, each factored and inverted by warp 0
-// (warp-synchronous), solved below and applied to the trailing columns by all warps; then the
-// 64-inverse by doubling from the four 16-inverses.  On this part FP64 issues at ~2 multiply-adds
-// per clock per SM and its divide and square root are long software sequences, so the leaf is
-// latency-bound: the warp-level panels take the ~200 CTA-wide barriers of a column-by-column
-// leaf down to ~25.
+// (S: 64 x 65 factor, V: 64 x 65 inverse, T: 32 x 33 products, R: 64 reciprocal square roots).
+//
+// Cost model (measured on this part with dependent-chain probes): a dependent FP64 operation
+// costs ~64 SM cycles whatever the number of active lanes, a division ~430, a square root ~675,
+// a reciprocal square root ~430; FP32 ~5.  So the leaf keeps its sequential chain short in
+// FP64 instructions and spreads independent ones over the four SM sub-partitions:
+//   * one reciprocal square root per column, r_c = 1 / sqrt(d_c), which gives the pivot
+//     (d_c r_c), the column scale and the inverse's diagonal (V_cc = r_c): no divisions;
+//   * 16-column panels over all rows of the leaf, factored right-looking by four groups of 64
+//     threads: thread t of group q holds row p0 + t of the panel columns p0 + q + 4u (u < 4)
+//     in registers, the group owning column c scales it, every group updates its own columns;
+//   * the trailing part of the leaf after each panel as one product over all threads;
+//   * the four 16 x 16 diagonal inverses on four warps (one per sub-partition), then doubling.
 constexpr int kLeafPW = 16;
-constexpr int kLeafSmem = 2 * kDW * (kDW + 1) + 2 * 32 * 33;  // doubles
+constexpr int kLeafSmem = 2 * kDW * (kDW + 1) + 32 * 33 + kDW;  // doubles
 
 __device__ void diag_leaf(const DiagArgs& g, int j, double* S) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -123,98 +129,134 @@ __device__ void diag_leaf(const DiagArgs& g, int j, double* S) {
   double* A = g.a + c0 + c0 * g.ld;
   constexpr int sd = kDW + 1;
   double* V = S + kDW * sd;    // inverse, 64 x 65
-  double* T = V + kDW * sd;    // two 32 x 33 products
+  double* T = V + kDW * sd;    // 32 x 33 products
+  double* R = T + 32 * 33;     // r_c = 1 / L_cc
   for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
     const int i = idx & (kDW - 1), c = idx / kDW;
     S[i * sd + c] = (i >= c) ? __ldcg(A + i + (int64_t)c * g.ld) : 0.0;
     V[(idx / kDW) * sd + (idx & (kDW - 1))] = 0.0;
   }
   __syncthreads();
+  const int grp = tid >> 6, t64 = tid & 63;
   for (int p0 = 0; p0 < kDW; p0 += kLeafPW) {
-    if (warp == 0) {
-      // factor the 16 x 16 diagonal block (lane = row within the block)
-      for (int c = 0; c < kLeafPW; ++c) {
-        double d = S[(p0 + c) * sd + p0 + c];
-        if (!(d > 0.0) || !isfinite(d)) {  // uniform across the warp
-          if (lane == 0) {
-            atomicMin(&g.st->pivot, (long long)(c0 + p0 + c));
+    const int i = p0 + t64;  // this thread's row of the panel
+    const bool own = i < kDW;
+    double a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = own ? S[i * sd + p0 + grp + 4 * u] : 0.0;
+#pragma unroll
+    for (int cc = 0; cc < kLeafPW; ++cc) {
+      const int c = p0 + cc;
+      if (grp == (cc & 3)) {  // the group owning column c: pivot, scale (d_c was published in S)
+        double d = S[c * sd + c];
+        if (!(d > 0.0) || !isfinite(d)) {  // uniform across the group
+          if (t64 == 0) {
+            atomicMin(&g.st->pivot, (long long)(c0 + c));
             atomicExch(&g.st->info, 1);
           }
           d = NAN;  // the rest becomes NaN; every barrier is still reached
         }
-        const double lc = sqrt(d), inv = 1.0 / lc;
-        __syncwarp();
-        if (lane > c && lane < kLeafPW) S[(p0 + lane) * sd + p0 + c] *= inv;
-        if (lane == c) S[(p0 + c) * sd + p0 + c] = lc;
-        __syncwarp();
-        for (int e = lane; e < kLeafPW * kLeafPW; e += 32) {
-          const int i = e / kLeafPW, l = e % kLeafPW;
-          if (l > c && i >= l)
-            S[(p0 + i) * sd + p0 + l] = fma(-S[(p0 + i) * sd + p0 + c], S[(p0 + l) * sd + p0 + c], S[(p0 + i) * sd + p0 + l]);
+        const double r = rsqrt(d);
+        if (own && i >= c) {
+          double v = 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u == (cc >> 2)) v = (i == c) ? d * r : a[u] * r;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u == (cc >> 2)) a[u] = v;
+          S[i * sd + c] = v;
         }
-        __syncwarp();
-      }
-      // invert it into V's diagonal block, column by column from the last:
-      //   V_cc = 1 / L_cc,  V_ic = -V_cc sum_{l=c+1..i} V_il L_lc  (i > c)
-      for (int c = kLeafPW - 1; c >= 0; --c) {
-        const double vcc = 1.0 / S[(p0 + c) * sd + p0 + c];
-        if (lane > c && lane < kLeafPW) {
-          double t = 0.0;
-          for (int l = c + 1; l <= lane; ++l) t = fma(V[(p0 + lane) * sd + p0 + l], S[(p0 + l) * sd + p0 + c], t);
-          V[(p0 + lane) * sd + p0 + c] = -t * vcc;
-        }
-        if (lane == c) V[(p0 + c) * sd + p0 + c] = vcc;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    const int m = kDW - p0 - kLeafPW;  // rows below the panel within the leaf
-    if (m > 0) {
-      // panel rows below by forward substitution, one row per thread:
-      //   L_rq = (A_rq - sum_{k < q} L_rk L_qk) / L_qq   (multiplied by V_qq = 1 / L_qq)
-      // (substitution rather than a product with the 16-inverse: on the ill-conditioned blocks of
-      // smooth fields the product's forward error, ~cond(L) u, shows in the log-determinant)
-      if (tid < m) {
-        const int r = p0 + kLeafPW + tid;
-        for (int q = 0; q < kLeafPW; ++q) {
-          double t = S[r * sd + p0 + q];
-          for (int k = 0; k < q; ++k) t = fma(-S[r * sd + p0 + k], S[(p0 + q) * sd + p0 + k], t);
-          S[r * sd + p0 + q] = t * V[(p0 + q) * sd + p0 + q];
-        }
+        if (t64 == 0) R[c] = r;
       }
       __syncthreads();
+      // a_il -= L_ic L_lc for this group's columns l > c (rows i >= l)
+      if (own && i > c) {
+        const double lic = S[i * sd + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int l = p0 + grp + 4 * u;
+          if (l > c && i >= l) a[u] = fma(-lic, S[l * sd + c], a[u]);
+        }
+      }
+      // publish the next pivot d_{c+1} from its owner's registers
+      if (cc + 1 < kLeafPW && grp == ((cc + 1) & 3) && i == c + 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u == ((cc + 1) >> 2)) S[i * sd + c + 1] = a[u];
+      }
+      __syncthreads();
+    }
+    const int m = kDW - p0 - kLeafPW;  // rows below the panel within the leaf
+    if (m > 0) {
       // trailing update of the leaf: S_il -= sum_k L_ik L_lk over the panel's 16 columns
       for (int idx = tid; idx < m * m; idx += kDThreads) {
-        const int i = p0 + kLeafPW + idx / m, l = p0 + kLeafPW + idx % m;
-        if (i < l) continue;
-        double t = S[i * sd + l];
+        const int ii = p0 + kLeafPW + idx / m, l = p0 + kLeafPW + idx % m;
+        if (ii < l) continue;
+        double t0 = S[ii * sd + l], t1 = 0.0;
 #pragma unroll
-        for (int k = 0; k < kLeafPW; ++k) t = fma(-S[i * sd + p0 + k], S[l * sd + p0 + k], t);
-        S[i * sd + l] = t;
+        for (int k = 0; k < kLeafPW; k += 2) {
+          t0 = fma(-S[ii * sd + p0 + k], S[l * sd + p0 + k], t0);
+          t1 = fma(-S[ii * sd + p0 + k + 1], S[l * sd + p0 + k + 1], t1);
+        }
+        S[ii * sd + l] = t0 + t1;
       }
       __syncthreads();
     }
   }
   // L back to the matrix (lower triangle)
   for (int idx = tid; idx < kDW * kDW; idx += kDThreads) {
-    const int i = idx & (kDW - 1), c = idx / kDW;
-    if (i >= c) A[i + (int64_t)c * g.ld] = S[i * sd + c];
+    const int ii = idx & (kDW - 1), c = idx / kDW;
+    if (ii >= c) A[ii + (int64_t)c * g.ld] = S[ii * sd + c];
   }
+  // the four 16 x 16 diagonal inverses, warp w < 4 taking block w (lane = row), column by column
+  // from the last: V_cc = r_c, V_ic = -r_c sum_{l = c+1..i} V_il L_lc (two partial sums)
+  if (warp < 4 && lane < kLeafPW) {
+    const int q0 = warp * kLeafPW, ii = q0 + lane;
+    for (int c = kLeafPW - 1; c >= 0; --c) {
+      const double rc = R[q0 + c];
+      if (lane > c) {
+        double s0 = 0.0, s1 = 0.0;
+        int l = c + 1;
+        for (; l + 1 <= lane; l += 2) {
+          s0 = fma(V[ii * sd + q0 + l], S[(q0 + l) * sd + q0 + c], s0);
+          s1 = fma(V[ii * sd + q0 + l + 1], S[(q0 + l + 1) * sd + q0 + c], s1);
+        }
+        if (l <= lane) s0 = fma(V[ii * sd + q0 + l], S[(q0 + l) * sd + q0 + c], s0);
+        V[ii * sd + q0 + c] = -(s0 + s1) * rc;
+      } else if (lane == c) {
+        V[ii * sd + q0 + c] = rc;
+      }
+      __syncwarp(0x0000FFFFu);
+    }
+  }
+  __syncthreads();
   // V = L^-1 by doubling: [[V_A, 0], [L_BA, V_B]]^-1 has off-diagonal block -V_B (L_BA V_A)
   for (int h = kLeafPW; h < kDW; h *= 2) {
     const int pairs = kDW / (2 * h);
     for (int idx = tid; idx < pairs * h * h; idx += kDThreads) {
       const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
-      double t = 0.0;
-      for (int k = c; k < h; ++k) t = fma(S[(o + h + r) * sd + o + k], V[(o + k) * sd + o + c], t);
-      T[p * 32 * 33 + r * 33 + c] = t;
+      double t0 = 0.0, t1 = 0.0;
+      int k = c;
+      for (; k + 1 < h; k += 2) {
+        t0 = fma(S[(o + h + r) * sd + o + k], V[(o + k) * sd + o + c], t0);
+        t1 = fma(S[(o + h + r) * sd + o + k + 1], V[(o + k + 1) * sd + o + c], t1);
+      }
+      if (k < h) t0 = fma(S[(o + h + r) * sd + o + k], V[(o + k) * sd + o + c], t0);
+      T[p * 16 * 33 * (h == kLeafPW) + r * 33 + c] = t0 + t1;  // h = 16: pairs at rows 0 and 16
     }
     __syncthreads();
     for (int idx = tid; idx < pairs * h * h; idx += kDThreads) {
       const int p = idx / (h * h), r = (idx / h) % h, c = idx % h, o = p * 2 * h;
-      double t = 0.0;
-      for (int k = 0; k <= r; ++k) t = fma(V[(o + h + r) * sd + o + h + k], T[p * 32 * 33 + k * 33 + c], t);
-      V[(o + h + r) * sd + o + c] = -t;
+      const double* Tp = T + p * 16 * 33 * (h == kLeafPW);
+      double t0 = 0.0, t1 = 0.0;
+      int k = 0;
+      for (; k + 1 <= r; k += 2) {
+        t0 = fma(V[(o + h + r) * sd + o + h + k], Tp[k * 33 + c], t0);
+        t1 = fma(V[(o + h + r) * sd + o + h + k + 1], Tp[(k + 1) * 33 + c], t1);
+      }
+      if (k <= r) t0 = fma(V[(o + h + r) * sd + o + h + k], Tp[k * 33 + c], t0);
+      V[(o + h + r) * sd + o + c] = -(t0 + t1);
     }
     __syncthreads();
   }
@@ -233,7 +275,8 @@ __global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_cons
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   unsigned int* bar = (unsigned int*)(g.scr + kDiagBar);
   volatile int* abort = (volatile int*)(bar + 1);
-  unsigned int nbar = 0;
+  unsigned int* leadcnt = bar + 2;  // lead tiles finished by CTAs other than 0 (monotone)
+  unsigned int nbar = 0, lead_target = 0;
   auto sync_all = [&]() { grid_barrier(bar, abort, (++nbar) * (unsigned int)G, g.st); };
   const int64_t ld = g.ld, k0 = g.k0;
   double* a = g.a;
@@ -287,10 +330,36 @@ __global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_cons
           *pc = __ldcg(pc) - acc[u][v];
         }
     };
+    // the three tiles of the next leaf on CTAs 0, 1, 2 (CTA 0 where the grid is smaller); the
+    // others count their tile on a monotone counter that CTA 0 waits for before the leaf
     const int lead = nt < 3 ? nt : 3;
+    int foreign = 0;  // lead tiles of this step on CTAs other than 0
+    for (int t = 0; t < lead; ++t) {
+      const int owner = t < G ? t : 0;
+      foreign += owner != 0;
+      if (owner == b) update_tile(t);
+    }
+    if (b != 0 && b < lead) {
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(leadcnt, 1u);
+      }
+    }
+    lead_target += (unsigned int)foreign;
     if (b == 0) {
-      for (int t = 0; t < lead; ++t) update_tile(t);
       if (j + 1 < kDSteps) {
+        if (tid == 0) {
+          const long long t0 = clock64();
+          while (*(volatile unsigned int*)leadcnt < lead_target && !*abort) {
+            if (clock64() - t0 > kDiagSpin) {
+              if (atomicExch((int*)abort, 1) == 0 && atomicExch(&g.st->timeout, 1) == 0) g.st->timeout_where = 72;
+              break;
+            }
+            __nanosleep(32);
+          }
+          __threadfence();
+        }
         __syncthreads();  // the leaf's tiles are written
         diag_leaf(g, j + 1, S);
       }
@@ -378,7 +447,10 @@ size_t diag_block_scratch_doubles() { return (size_t)kDiagScratch; }
 
 cudaError_t launch_diag_block(cudaStream_t s, double* a, int64_t ld, int64_t k0, double* w_sub, double* logdet_part,
                               double* w2, double* scratch, DevStatus* st, int grid) {
-  const size_t smem = (size_t)(kLeafSmem + 2 * kDT * (kDT + 1)) * sizeof(double);
+  // at least 116 KB of shared memory, so that no SM holds two CTAs (the FP64 pipe of an SM is
+  // the resource: two CTAs on one SM would leave another idle)
+  size_t smem = (size_t)(kLeafSmem + 2 * kDT * (kDT + 1)) * sizeof(double);
+  if (smem < (size_t)116 * 1024) smem = (size_t)116 * 1024;
   static PerDeviceOnce attr_once;
   cudaError_t e = attr_once([&] {
     return cudaFuncSetAttribute(diag_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

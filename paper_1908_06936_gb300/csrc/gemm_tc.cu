@@ -547,6 +547,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       const int64_t row = g.c_row0 + (int64_t)bi * TILE + (int64_t)rank * HALF_ROWS + r;
       const int64_t col0 = g.c_col0 + (int64_t)bj * TILE + half * 128;
       double* cp = g.C + row + col0 * g.ldc;
+      // L2 prefetch two chunks ahead (lane l: column l / 2 of the chunk, rows 16 (l % 2) .. of
+      // this warp's 32), and in the last two chunks the first two of this pair's next tile: the
+      // loads below then wait on L2 rather than DRAM, and each SM keeps more C lines in flight
+      // than its registers hold
+      const double* pf = g.C + (row - lane + 16 * (lane & 1)) + (col0 + (lane >> 1)) * g.ldc;
+      const double* pf_next = nullptr;
+      if (!g.store) {
+        for (long long t2 = t + npairs; t2 < g.ntiles; t2 += npairs) {
+          int bi2, bj2;
+          if (!decode_pair_tile(g, t2, bi2, bj2)) continue;
+          pf_next = g.C + (g.c_row0 + (int64_t)bi2 * TILE + (int64_t)rank * HALF_ROWS + quad * 32 + 16 * (lane & 1)) +
+                    (g.c_col0 + (int64_t)bj2 * TILE + half * 128 + (lane >> 1)) * g.ldc;
+          break;
+        }
+      }
       // eight 16-column chunks of this warp's 128 columns, the C loads of chunk q + 1 issued
       // before chunk q is drained from TMEM, so their latency hides behind its conversion and stores
       double cbuf[2][16];
@@ -554,6 +569,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
       for (int j = 0; j < 16; ++j) cbuf[0][j] = g.store ? 0.0 : __ldcs(cp + (int64_t)j * g.ldc);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
+        if (!g.store) {
+          if (q + 2 < 8)
+            prefetch_l2(pf + (int64_t)((q + 2) * 16) * g.ldc);
+          else if (pf_next)
+            prefetch_l2(pf_next + (int64_t)((q - 6) * 16) * g.ldc);
+        }
         if (q + 1 < 8) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
