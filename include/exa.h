@@ -135,9 +135,12 @@ exa_status exa_ctx_set_panel_fusion(exa_ctx* ctx, int64_t min_rows);
 
 /* Mixed precision: refinement stopping rule.  resid_target > 0: refine
  * x = Sigma^-1 z until ||z - Sigma x||_2 / ||z||_2 <= resid_target (or the
- * residual stops halving, or 10 steps); 0 (the default): stop once a correction
- * changes z^T x by less than 1e-10 relative (q, and l, are then final to that
- * accuracy).  exa_result.ir_resid reports the last residual computed.
+ * residual stops halving, or 10 steps); 0 (the default): stop once q is final
+ * to 1e-10 relative, that is once a correction d = (L L^T)^-1 r of the residual
+ * r = z - Sigma x changes z^T x by less than that, or once r^T d, the
+ * second-order term of the variational estimate q = z^T x + x^T r + r^T d
+ * (off by r^T (Sigma^-1 - (L L^T)^-1) r), is below it; q is then that estimate.
+ * exa_result.ir_resid reports the last residual computed.
  * EXA_ERR_ARG for a negative or non-finite target.                          */
 exa_status exa_ctx_set_refinement(exa_ctx* ctx, double resid_target);
 

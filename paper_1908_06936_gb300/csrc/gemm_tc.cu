@@ -115,6 +115,13 @@ __device__ __forceinline__ bool t3_tile(const GemmArgs& g, long long t, T3Tile& 
   return true;
 }
 
+// Far 128 x 128 tiles of the single-CTA kernel: the same test as the pair kernel's far tiles,
+// on the 256-row block exponents of the two operand row blocks (never in task mode).
+__device__ __forceinline__ bool far_t3(const GemmArgs& g, const T3Tile& tl) {
+  if (g.enum_mode == kEnumTasks || g.far_thr == INT_MIN || !g.ea_blk || !g.eb_blk) return false;
+  return (long long)g.ea_blk[tl.ya / 256] + (long long)g.eb_blk[tl.yb / 256] <= (long long)g.far_thr;
+}
+
 __device__ __forceinline__ void record_timeout(DevStatus* st, int site) {
   if (atomicExch(&st->timeout, 1) == 0) st->timeout_where = site;
 }
@@ -183,6 +190,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       T3Tile tl;
       if (!t3_tile(g, t, tl)) continue;
       const int ya = tl.ya, yb = tl.yb;
+      const bool one = far_t3(g, tl);  // far tile: the hi halves only
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
           *abort = 1;
@@ -190,11 +198,13 @@ __global__ void __launch_bounds__(kGemmThreads)
           break;
         }
         uint8_t* sb = smem + stage * STAGE_BYTES;
-        mbar_expect_tx(&full[stage], STAGE_BYTES);
+        mbar_expect_tx(&full[stage], one ? 2 * OP_BYTES : STAGE_BYTES);
         tma_load_2d_hint(sb, &tA_hi, &full[stage], kc * KC, ya, pol);
-        tma_load_2d_hint(sb + OP_BYTES, &tA_lo, &full[stage], kc * KC, ya, pol);
         tma_load_2d_hint(sb + 2 * OP_BYTES, &tB_hi, &full[stage], kc * KC, yb, pol);
-        tma_load_2d_hint(sb + 3 * OP_BYTES, &tB_lo, &full[stage], kc * KC, yb, pol);
+        if (!one) {
+          tma_load_2d_hint(sb + OP_BYTES, &tA_lo, &full[stage], kc * KC, ya, pol);
+          tma_load_2d_hint(sb + 3 * OP_BYTES, &tB_lo, &full[stage], kc * KC, yb, pol);
+        }
         last_par[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -226,6 +236,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       }
       fence_after();
       const uint32_t d = tmem + b * TN;
+      const bool one = far_t3(g, tl);
       bool ok = true;
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&full[stage], phase, abort)) {
@@ -242,8 +253,10 @@ __global__ void __launch_bounds__(kGemmThreads)
         for (int kk = 0; kk < KC / 8; ++kk) {  // K = 8 per instruction: advance 32 bytes
           const uint64_t o = (uint64_t)(kk * 2);
           mma_tf32(d, ahi + o, bhi + o, IDESC, (kc | kk) ? 1u : 0u);
-          mma_tf32(d, ahi + o, blo + o, IDESC, 1u);
-          mma_tf32(d, alo + o, bhi + o, IDESC, 1u);
+          if (!one) {
+            mma_tf32(d, ahi + o, blo + o, IDESC, 1u);
+            mma_tf32(d, alo + o, bhi + o, IDESC, 1u);
+          }
         }
         mma_commit(&empty[stage]);
         if (++stage == STAGES) {
@@ -620,6 +633,13 @@ constexpr int BUF_COLS = S * GROUP_COLS;
 constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a power of two
 }  // namespace oz
 
+// CL = 2: the CTAs of a cluster pair take adjacent column tiles (bj even, bj + 1) of one row
+// block, so they need the same A digits: each loads half of the 128 A rows (map `ta`, 64-row
+// boxes) and multicasts it to both, halving the A bytes each CTA pulls through L2 (A is four
+// fifths of a tile's operand bytes).  Each CTA's MMA commit releases the stage in both CTAs
+// (empty[] counts CL arrivals), since both write into both.  Band and full enumerations list
+// the two tiles of a pair consecutively and skip them together; tile counts are even.
+template <int CL>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_constant__ OzMaps ta,
                                                          const __grid_constant__ OzMaps tb,
                                                          const __grid_constant__ GemmArgs g) {
@@ -630,25 +650,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
   uint64_t* empty = full + STAGES;
   uint64_t* accfull = empty + STAGES;
   uint64_t* accempty = accfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+  uint64_t* drain = accempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = CL > 1 ? (int)cluster_rank() : 0;
+  const long long first = CL > 1 ? (long long)(blockIdx.x / CL) : (long long)blockIdx.x;
+  const long long step = CL > 1 ? (long long)(gridDim.x / CL) : (long long)gridDim.x;
+  const long long nunits = g.ntiles / CL;  // tiles, or tile pairs
+  constexpr uint16_t kAll = (uint16_t)((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], kEpiThreads);
     }
+    mbar_init(drain, 1);
     *abort = 0;
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's barriers exist before anything is multicast to them
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const int kchunks = g.K / KC;
@@ -663,7 +691,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
     uint32_t phase = 0;
     int last_par[STAGES];
     for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
-    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+    for (long long u = first; u < nunits && !*abort; u += step) {
+      const long long t = u * CL + rank;
       int bi, bj;
       if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
       const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + bj * TN;
@@ -677,7 +706,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
         mbar_expect_tx(&full[stage], STAGE_BYTES);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          tma_load_2d_hint(sb + s * A_BYTES, &ta.m[s], &full[stage], kc * KC, ya, pol);
+          if (CL > 1)
+            tma_load_2d_mc_hint(sb + s * A_BYTES + rank * (A_BYTES / CL), &ta.m[s], &full[stage], kc * KC,
+                                ya + rank * (TM / CL), kAll, pol);
+          else
+            tma_load_2d_hint(sb + s * A_BYTES, &ta.m[s], &full[stage], kc * KC, ya, pol);
           tma_load_2d_hint(sb + S * A_BYTES + s * B_BYTES, &tb.m[s], &full[stage], kc * KC, yb, pol);
         }
         last_par[stage] = (int)phase;
@@ -698,7 +731,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
     int stage = 0;
     uint32_t phase = 0;
     int it = 0;
-    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+    for (long long u = first; u < nunits && !*abort; u += step) {
+      const long long t = u * CL + rank;
       int bi, bj;
       if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
       const int b = it & 1;
@@ -735,7 +769,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
             mma_bf16(d0 + s * GROUP_COLS, a, bb, idesc(kFmtBF16, TM, TN * (S - s)), (kc | kk | s) ? 1u : 0u);
           }
         }
-        mma_commit(&empty[stage]);
+        if (CL > 1)
+          mma_commit_mc(&empty[stage], kAll);
+        else
+          mma_commit(&empty[stage]);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -745,12 +782,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
       mma_commit(&accfull[b]);
       ++it;
     }
+    if (CL > 1) {  // every MMA (and so every commit to the peer) has finished before the pair leaves
+      mma_commit(drain);
+      volatile int never = 0;
+      mbar_wait(drain, 0, &never);
+    }
   } else if (warp >= 2) {
     const int quad = warp & 3;
     const int half = (warp - 2) >> 2;  // columns [16*half, 16*half + 16)
     const int r = quad * 32 + lane;
     int it = 0;
-    for (long long t = blockIdx.x; t < g.ntiles && !*abort; t += gridDim.x) {
+    for (long long u = first; u < nunits && !*abort; u += step) {
+      const long long t = u * CL + rank;
       int bi, bj;
       if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
       const int b = it & 1;
@@ -796,6 +839,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
   }
   fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's copies into this CTA and commits to its barriers are done
   if (warp == 1) {
     fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
@@ -1000,6 +1044,7 @@ cudaError_t make_split_maps(SplitOperand& op) {
       const void* base = (const uint8_t*)op.dig + (size_t)s * op.rows * op.K * 2;
       if ((e = make_tmap(&op.oz_a.m[s], base, op.rows, op.K, 2, 64, 128)) != cudaSuccess) return e;
       if ((e = make_tmap(&op.oz_b.m[s], base, op.rows, op.K, 2, 64, 32)) != cudaSuccess) return e;
+      if ((e = make_tmap(&op.oz_ah.m[s], base, op.rows, op.K, 2, 64, 64)) != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -1098,17 +1143,41 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
   if (g.ntiles <= 0) return cudaSuccess;
   static PerDeviceOnce attr_once;
   {
-    const cudaError_t e =
-        attr_once([] { return cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES); });
+    const cudaError_t e = attr_once([] {
+      cudaError_t r = cudaFuncSetAttribute(gemm_oz_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(gemm_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+      return r;
+    });
     if (e != cudaSuccess) return e;
   }
   int cap = num_sms();
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
-  const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
   GemmArgs g2 = g;
   g2.ea = A.ex;
   g2.eb = B.ex;
-  gemm_oz_kernel<<<grid, kGemmThreads, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
+  // CTA pairs sharing the A digits when the tiles pair up (even counts) and the launch may use
+  // most of the GPU: a cluster needs two free SMs of one GPC at once, which a small SM share
+  // beside other running kernels may not offer (the launch would then wait for them)
+  if (g.ntiles % 2 == 0 && cap >= 64 && (g.enum_mode == kEnumBand || g.enum_mode == kEnumFull) && g.nt % 2 == 0) {
+    const long long pairs = g.ntiles / 2;
+    const int grid = 2 * (int)(pairs < cap / 2 ? pairs : cap / 2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = oz::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_oz_kernel<2>, A.oz_ah, B.oz_b, g2);
+  }
+  const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
+  gemm_oz_kernel<1><<<grid, kGemmThreads, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
   return cudaGetLastError();
 }
 

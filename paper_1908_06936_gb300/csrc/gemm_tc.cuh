@@ -85,6 +85,7 @@ struct SplitOperand {
   CUtensorMap t_hi, t_lo;     // boxes 32 x 128
   OzMaps oz_a;                // boxes 64 x 128 (A role)
   OzMaps oz_b;                // boxes 64 x 32  (B role)
+  OzMaps oz_ah;               // boxes 64 x 64  (A role, half a tile: multicast by a CTA pair)
 };
 
 cudaError_t make_split_maps(SplitOperand& op);

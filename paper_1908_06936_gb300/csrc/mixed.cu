@@ -191,6 +191,10 @@ static exa_status column_update(const MixStep& M, cudaStream_t s, int p, int j, 
     g.a_row0 = off + (int)rb;
     g.nt = NB / 128;
     g.ntiles = ((m - rb) / 128) * g.nt;
+    // far tiles (one TF32 product) by the same test as the trailing update's, when CTA pairs
+    // (and so far tiles) are on
+    g.ea_blk = g.eb_blk = c->tc_pairs ? sp.exb : nullptr;
+    g.far_thr = c->tc_pairs ? M.far_thr : INT_MIN;
     ProfScope ps(c, PK_GEMM_T3, 2.0 * (double)(m - rb) * NB * NB, 16.0 * (double)(m - rb) * NB, 1, s, true);
     e = launch_gemm_t3(s, sp, sp, g, ctas);
   }
@@ -516,14 +520,15 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   if (e == cudaSuccess) e = solve_llt(c, A, npad, npad, zp, x, work, (int*)red);
   if (e != cudaSuccess) return cuda_err(c, e, "solve launch");
   // iterative refinement of x = Sigma^-1 z with the FP64 residual.  It stops when the
-  // residual no longer halves or reaches rounding level, or once a correction d
-  // changes the quadratic form z^T x by less than kIrQuadTol relative: later
-  // corrections are smaller still, so q (and l) are final to that accuracy.
+  // residual no longer halves or reaches rounding level, or once the quadratic form is final
+  // to kIrQuadTol relative: a correction d changes z^T x by less than that, or the
+  // second-order term r^T d of the variational estimate is below it (q is then that estimate).
   if ((st = ensure(c, c->mx_symv, (size_t)symv_tiled_partials(npad) * sizeof(double), "symmetric product partials")) !=
       EXA_OK)
     return st;
   double* sp = (double*)c->mx_symv.p;
   double rel = 0.0, prev = 1e300;
+  double q_var = NAN;  // the variational estimate, when it ended the refinement
   bool q_done = false;
   // stopping rule: a caller's residual target (exa_ctx_set_refinement), rounding level for the
   // gradient (which needs Sigma^-1 z itself), else the quadratic-form rule (target < 0)
@@ -544,17 +549,33 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     if (!(rel > (target > 0.0 ? target : 1e-15)) || it >= kMaxIt || rel > 0.5 * prev) break;
     prev = rel;
     e = solve_llt(c, A, npad, npad, r, d, work, (int*)red);
+    // the variational estimate of q before x moves: with r = z - Sigma x and d = (L L^T)^-1 r,
+    // q = z^T x + x^T r + r^T Sigma^-1 r, so q_hat = z^T x + x^T r + r^T d is off by
+    // r^T (Sigma^-1 - (L L^T)^-1) r, second order in the residual (about the contraction
+    // factor of the refinement times r^T d), where z^T (x + d) is off to first order
+    if (e == cudaSuccess) e = launch_dot(s, x, r, npad, part, c->d_scalars + 6);
+    if (e == cudaSuccess) e = launch_dot(s, r, d, npad, part, c->d_scalars + 7);
+    if (e == cudaSuccess) e = launch_dot(s, zp, x, npad, part, c->d_scalars + 8);
     if (e == cudaSuccess) e = launch_axpy(s, 1.0, d, x, npad);
     if (e == cudaSuccess) e = launch_dot(s, zp, d, npad, part, c->d_scalars + 4);
     if (e == cudaSuccess) e = launch_dot(s, zp, x, npad, part, c->d_scalars + 5);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->h_scalars + 4, c->d_scalars + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(c->h_scalars + 4, c->d_scalars + 4, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
     if ((st = read_status(c)) != EXA_OK) return st;
-    if (target < 0.0 && fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
-      q_done = true;
-      ++it;
-      break;
+    if (target < 0.0) {
+      const double q_hat = c->h_scalars[8] + c->h_scalars[6] + c->h_scalars[7];
+      if (fabs(c->h_scalars[7]) <= kIrQuadTol * fabs(q_hat)) {
+        q_var = q_hat;
+        q_done = true;
+        ++it;
+        break;
+      }
+      if (fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
+        q_done = true;
+        ++it;
+        break;
+      }
     }
   }
   e = launch_dot(s, zp, x, npad, part, c->d_scalars + 0);
@@ -571,7 +592,7 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   out->n_tiles = (int)(npad / kMixNB);
   out->ir_iters = it;
   out->ir_resid = rel;
-  out->quad = c->h_scalars[0];
+  out->quad = isnan(q_var) ? c->h_scalars[0] : q_var;
   out->logdet = 2.0 * c->h_scalars[1];
   out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * out->logdet - 0.5 * out->quad;
   if (!q_done && !(rel <= kIrFailTol))

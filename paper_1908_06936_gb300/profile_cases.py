@@ -11,6 +11,7 @@ kernel (``-s``) and capture one launch (``-c 1``).
   python -m paper_1908_06936_gb300.profile_cases potrf --n 16384
   python -m paper_1908_06936_gb300.profile_cases matern --m 128
   python -m paper_1908_06936_gb300.profile_cases timeline --m 300 --out timeline.json
+  python -m paper_1908_06936_gb300.profile_cases timeline --m 150 --far-margin 12 --fp64-check
 
 gemm-pair / gemm-oz: exa_gemm_update, C -= A B^T with C (c x c, FP64) and A, B
 (c x k, FP64, standard normal); gemm-pair is the CTA-pair TF32x3 trailing-update
@@ -55,6 +56,10 @@ def main(argv=None) -> dict:
                     help="timeline case: exa_ctx_set_panel_fusion(ROWS) before the evaluations")
     ap.add_argument("--lookahead", type=int, default=None,
                     help="timeline case: exa_ctx_set_lookahead(SMS) before the evaluations")
+    ap.add_argument("--far-margin", type=int, default=None,
+                    help="timeline case: exa_ctx_set_far_tile_margin(BITS) before the evaluations")
+    ap.add_argument("--fp64-check", action="store_true",
+                    help="timeline case: also evaluate in FP64 and report |dl|/|l| of the mixed result")
     ap.add_argument("--c", type=int, default=16384, help="rows and columns of C (gemm cases)")
     ap.add_argument("--k", type=int, default=512, help="inner dimension (gemm cases)")
     ap.add_argument("--m", type=int, default=128, help="grid side, n = m^2 (potrf, matern)")
@@ -95,12 +100,16 @@ def main(argv=None) -> dict:
             n = m * m
             locs = torch.as_tensor(synth.jittered_grid(m, 0), device="cuda")
             z = torch.as_tensor(synth.normals(n, 0), device="cuda")
+            if args.fp64_check:  # an exact realisation Z = L eps (FP64 factor) for the accuracy check
+                z = ctx.simulate(locs, z, args.theta, exa.EXA_FP64)
             if args.late:
                 ctx.check(exa.exa_ctx_set_lookahead_late(ctx.handle, args.late[0], args.late[1]))
             if args.fuse is not None:
                 ctx.check(exa.exa_ctx_set_panel_fusion(ctx.handle, args.fuse))
             if args.lookahead is not None:
                 ctx.check(exa.exa_ctx_set_lookahead(ctx.handle, args.lookahead))
+            if args.far_margin is not None:
+                ctx.check(exa.exa_ctx_set_far_tile_margin(ctx.handle, args.far_margin))
             ctx.loglik_ex(locs, z, args.theta, exa.EXA_MIXED_TF32X3)
             exa.exa_profile_enable(ctx.handle, 1)
             exa.exa_profile_timeline_enable(ctx.handle, 1)
@@ -116,9 +125,12 @@ def main(argv=None) -> dict:
                 busy.setdefault(st, 0.0)
                 busy[st] += b - a
             out.update({"n": n, "late": args.late, "fuse": args.fuse, "lookahead": args.lookahead,
-                        "loglik": r["loglik"], "records": len(tl), "ms_total": r["ms_total"],
-                        "ms_chol": r["ms_chol"],
+                        "far_margin": args.far_margin, "loglik": r["loglik"], "records": len(tl),
+                        "ms_total": r["ms_total"], "ms_chol": r["ms_chol"], "ir_iters": r["ir_iters"],
                         "busy_ms_by_stream": busy})
+            if args.fp64_check:
+                f = ctx.loglik_ex(locs, z, args.theta, exa.EXA_FP64)
+                out["rel_dl_vs_fp64"] = abs(r["loglik"] - f["loglik"]) / abs(f["loglik"])
         else:
             m = args.m
             n = m * m

@@ -59,7 +59,10 @@ def test_t3_product(ctx, m, n, k, store):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
 
 
-@pytest.mark.parametrize("m,n,k", [(128, 32, 64), (256, 96, 256), (128, 256, 128), (384, 32, 192)])
+# (128, 32), (256, 96), (384, 32): odd column-tile counts (single CTAs); (128, 256), (256, 64),
+# (2048, 512): CTA pairs sharing the A digits, the last with 128 tile pairs over 76 pairs of CTAs
+@pytest.mark.parametrize("m,n,k", [(128, 32, 64), (256, 96, 256), (128, 256, 128), (384, 32, 192), (256, 64, 512),
+                                   (2048, 512, 512)])
 @pytest.mark.parametrize("store", [0, 1])
 def test_oz_product(ctx, m, n, k, store):
     import paper_1908_06936_gb300 as exa
