@@ -114,14 +114,14 @@ exa_status exa_ctx_set_mixed_band(exa_ctx* ctx, int band);
 
 /* Mixed precision: SMs left to the look-ahead stream (which factors the next
  * diagonal block and runs the next panel solve) while the trailing update
- * runs on the others.  0 restores the default (16).                        */
+ * runs on the others.  0 restores the default (20).                        */
 exa_status exa_ctx_set_lookahead(exa_ctx* ctx, int sms);
 
 /* Mixed precision, one-panel phase: once the trailing matrix has fewer than `rows`
  * rows, the look-ahead stream's SM share grows linearly from exa_ctx_set_lookahead's
  * to `sms` (reached at rows / 3) and the trailing update's shrinks by as much, since
  * the look-ahead stream's panel then sets the pace.  rows = 0 turns the ramp off;
- * rows < 0 and sms = 0 restore the defaults (61440 rows, 76 SMs).            */
+ * rows < 0 and sms = 0 restore the defaults (61440 rows, 48 SMs).            */
 exa_status exa_ctx_set_lookahead_late(exa_ctx* ctx, int64_t rows, int sms);
 
 /* Mixed precision: while the trailing matrix still has at least min_rows rows,

@@ -224,7 +224,9 @@ __device__ __forceinline__ double table_node_value(const MaternParams& P, int id
   double centre, half;
   segment_geometry(sgi, centre, half);
   const double tk = cos(3.14159265358979323846 * (k + 0.5) / (kTabDeg + 1));
-  return matern_ratio(P, sqrt(centre + half * tk));  // f at the k-th Chebyshev point of s
+  // Sigma itself (sigma^2 folded in: one FP64 multiplication fewer per generated entry) at
+  // the k-th Chebyshev point of s
+  return P.sigma2 * matern_ratio(P, sqrt(centre + half * tk));
 }
 
 // Chebyshev coefficients of segment sgi from its nodes, then their monomial form in t.
@@ -260,20 +262,25 @@ __device__ __forceinline__ void table_segment_coefs(const double* __restrict__ n
   for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
 }
 
-// Sigma at squared distance r2 = r^2 from the table (exact routine outside its range).
+// Sigma at squared distance r2 = r^2 from the table (exact routine outside its range).  The
+// tests are integer work on the bit patterns: FP64 instructions are the scarce resource of the
+// generation (~2 per clock per SM on this part), FP64 comparisons included.
 __device__ __forceinline__ double matern_value_tab(const MaternParams& P, const MaternTable* __restrict__ T,
                                                    double r2) {
-  if (r2 == 0.0) return P.sigma2;
+  if (__double_as_longlong(r2) == 0) return P.sigma2;  // r2 >= 0: only +0 has all bits clear
   const double s = r2 * P.ib2;
   static_assert(kTabE0 == -8 && kTabE0 + kTabOct == 12, "table range below");
-  if (!(s >= 0x1p-8) || !(s < 0x1p12)) return matern_value(P, sqrt(r2));  // also NaN
+  // 2^-8 <= s < 2^12 exactly when the sign is clear and the biased exponent is in [1015, 1035)
+  // (negative, zero, subnormal, infinite and NaN values all fall outside)
+  const unsigned int se = (unsigned int)((unsigned long long)__double_as_longlong(s) >> 52);
+  if (se - (unsigned int)(1023 + kTabE0) >= (unsigned int)kTabOct) return matern_value(P, sqrt(r2));
   const int sgi = table_segment(s);
   const double t = fma(s, __ldg(&T->ih[sgi]), __ldg(&T->mc[sgi]));
   const double* c = T->a[sgi];
   double f = __ldg(&c[kTabDeg]);
 #pragma unroll
   for (int k = kTabDeg - 1; k >= 0; --k) f = fma(f, t, __ldg(&c[k]));
-  return P.sigma2 * f;
+  return f;  // the table holds Sigma, sigma^2 included
 }
 
 }  // namespace exa

@@ -98,7 +98,7 @@ struct MaternParams {
 // Host: fill the parameter block for theta (defined in matern.cu).
 void matern_params(const double theta[3], MaternParams* p);
 
-// Per-theta interpolation table of f(s) = Sigma / sigma^2 as a function of s = (r / beta)^2,
+// Per-theta interpolation table of f(s) = Sigma (sigma^2 included) as a function of s = (r / beta)^2,
 // so that an entry costs no square root, division or exponential.  Segments follow the
 // binary exponent of s: octave [2^e, 2^(e+1)), e in [kTabE0, kTabE0 + kTabOct), split into
 // kTabSub equal pieces; on each, f is a degree-kTabDeg polynomial in t = (s - centre) /

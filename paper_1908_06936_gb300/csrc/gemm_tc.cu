@@ -623,14 +623,53 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
 // OZ kernel: tile 128 x 32, K chunks of 64 BF16 digits, S = 5 slices, 2 stages.
 // ===========================================================================
 namespace oz {
-constexpr int TM = 128, TN = 32, KC = 64, STAGES = 2, S = kOzSlices;
+constexpr int TM = 128, KC = 64, STAGES = 2, S = kOzSlices;
 constexpr int A_BYTES = TM * KC * 2;   // 16 KB per slice
-constexpr int B_BYTES = TN * KC * 2;   // 4 KB per slice
-constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int GROUP_COLS = TN;          // one accumulator per slice-sum group
-constexpr int BUF_COLS = S * GROUP_COLS;
-constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a power of two
+constexpr int TMEM_COLS = 512;         // 2 accumulator buffers of S groups x TN columns
+// Per tile width TN (32, or 48 for the band of the trailing update: 27% fewer operand bytes per
+// output, and 2 x 5 x 48 = 480 TMEM columns still hold two accumulator buffers)
+template <int TN>
+struct Cfg {
+  static constexpr int B_BYTES = TN * KC * 2;  // per slice
+  static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int GROUP_COLS = TN;        // one accumulator per slice-sum group
+  static constexpr int BUF_COLS = S * GROUP_COLS;
+  static constexpr int CH = TN / 2;            // columns drained by one epilogue warp
+};
+static_assert(Cfg<48>::SMEM_BYTES <= 232448, "two 48-wide stages fit in shared memory");
+static_assert(2 * Cfg<48>::BUF_COLS <= TMEM_COLS, "two 48-wide accumulator buffers fit in TMEM");
+
+// Tile t of a launch: row block bi (128 rows), column offset cofs (from c_col0 / b_row0) and
+// the number of its TN columns inside the output (band tiles of width 48 end ragged at each
+// panel boundary: 512 = 10 x 48 + 32).  False: skip the tile.
+template <int TN>
+__device__ __forceinline__ bool oz_tile(const GemmArgs& g, long long t, int& bi, int& cofs, int& cvalid) {
+  if (g.enum_mode != kEnumBand) {  // kEnumFull (TN = 32)
+    bi = (int)(t / g.nt);
+    cofs = (int)(t % g.nt) * TN;
+    cvalid = TN;
+    return true;
+  }
+  const int SI = g.panel / TM, SJ = (g.panel + TN - 1) / TN;
+  const long long pair = t / (SI * SJ);
+  const int sub = (int)(t % (SI * SJ));
+  const int b = g.band;
+  const long long head = (long long)b * (b + 1) / 2;
+  int I, J;
+  if (pair < head) {
+    tile_tri_decode(pair, I, J);
+  } else {
+    I = b + (int)((pair - head) / (b + 1));
+    J = I - b + (int)((pair - head) % (b + 1));
+  }
+  bi = I * SI + sub / SJ;
+  const int sj = sub % SJ;
+  cofs = J * g.panel + sj * TN;
+  cvalid = g.panel - sj * TN < TN ? g.panel - sj * TN : TN;
+  // skip tiles strictly above the diagonal
+  return (long long)cofs <= (long long)bi * TM + TM - 1;
+}
 }  // namespace oz
 
 // CL = 2: the CTAs of a cluster pair take adjacent column tiles (bj even, bj + 1) of one row
@@ -639,11 +678,15 @@ constexpr int TMEM_COLS = 512;          // 2 buffers x 160 columns, rounded to a
 // fifths of a tile's operand bytes).  Each CTA's MMA commit releases the stage in both CTAs
 // (empty[] counts CL arrivals), since both write into both.  Band and full enumerations list
 // the two tiles of a pair consecutively and skip them together; tile counts are even.
-template <int CL>
+template <int CL, int TN>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_constant__ OzMaps ta,
                                                          const __grid_constant__ OzMaps tb,
                                                          const __grid_constant__ GemmArgs g) {
   using namespace oz;
+  using C_ = Cfg<TN>;
+  constexpr int B_BYTES = C_::B_BYTES, STAGE_BYTES = C_::STAGE_BYTES, GROUP_COLS = C_::GROUP_COLS,
+                BUF_COLS = C_::BUF_COLS, CH = C_::CH;
+  static_assert(CL == 1 || TN == 32, "CTA pairs take 32-wide tiles");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -693,9 +736,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
     for (int s = 0; s < STAGES; ++s) last_par[s] = -1;
     for (long long u = first; u < nunits && !*abort; u += step) {
       const long long t = u * CL + rank;
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
-      const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + bj * TN;
+      int bi, cofs, cvalid;
+      if (!oz_tile<TN>(g, t, bi, cofs, cvalid)) continue;
+      const int ya = g.a_row0 + bi * TM, yb = g.b_row0 + cofs;
       for (int kc = 0; kc < kchunks; ++kc) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) {
           *abort = 1;
@@ -733,8 +776,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
     int it = 0;
     for (long long u = first; u < nunits && !*abort; u += step) {
       const long long t = u * CL + rank;
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      int bi, cofs, cvalid;
+      if (!oz_tile<TN>(g, t, bi, cofs, cvalid)) continue;
       const int b = it & 1;
       const uint32_t ap = (it >> 1) & 1;
       if (!mbar_wait(&accempty[b], ap ^ 1, abort)) {
@@ -789,13 +832,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
     }
   } else if (warp >= 2) {
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;  // columns [16*half, 16*half + 16)
+    const int half = (warp - 2) >> 2;  // columns [CH half, CH half + CH) of the tile
     const int r = quad * 32 + lane;
     int it = 0;
     for (long long u = first; u < nunits && !*abort; u += step) {
       const long long t = u * CL + rank;
-      int bi, bj;
-      if (!decode_tile<TM, TN>(g, t, bi, bj)) continue;
+      int bi, cofs, cvalid;
+      if (!oz_tile<TN>(g, t, bi, cofs, cvalid)) continue;
       const int b = it & 1;
       const uint32_t ap = (it >> 1) & 1;
       if (!mbar_wait(&accfull[b], ap, abort)) {
@@ -805,32 +848,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_oz_kernel(const __grid_c
       }
       fence_after();
       const int64_t row = g.c_row0 + (int64_t)bi * TM + r;
-      const int64_t col0 = g.c_col0 + (int64_t)bj * TN + 16 * half;
+      const int lc0 = CH * half;  // first tile column of this warp
+      const int64_t col0 = g.c_col0 + (int64_t)cofs + lc0;
       double* cp = g.C + row + col0 * g.ldc;
-      double cv[16];
+      const bool lower = g.lower_mask != 0;
+      // columns of this warp inside the output (ragged tiles end early) and on or below the diagonal
+      bool live[CH];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) cv[j] = g.store ? 0.0 : __ldcs(cp + (int64_t)j * g.ldc);
+      for (int j = 0; j < CH; ++j) live[j] = lc0 + j < cvalid && !(lower && col0 + j > row);
+      double cv[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) cv[j] = (g.store || !live[j]) ? 0.0 : __ldcs(cp + (int64_t)j * g.ldc);
       // group g holds an exact integer a_g (|a_g| < 2^24) of weight 2^(-7(g+2)):
       // V = sum_g a_g 2^(7(4-g)) is an integer below 2^53, combined exactly in int64
-      long long V[16];
+      long long V[CH];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) V[j] = 0;
+      for (int j = 0; j < CH; ++j) V[j] = 0;
 #pragma unroll
       for (int gs = 0; gs < S; ++gs) {
-        uint32_t acc[16];
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS + 16 * half, acc);
+        uint32_t acc[CH];
+        const uint32_t ta0 = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS + gs * GROUP_COLS + lc0;
+        if constexpr (CH == 16) {
+          tmem_ld16(ta0, *reinterpret_cast<uint32_t(*)[16]>(acc));
+        } else {  // CH = 24: 16 + 8 columns (half 0) or 8 + 16 (half 1), each load aligned to its width
+          if (half == 0) {
+            tmem_ld16(ta0, *reinterpret_cast<uint32_t(*)[16]>(acc));
+            tmem_ld8(ta0 + 16, *reinterpret_cast<uint32_t(*)[8]>(acc + 16));
+          } else {
+            tmem_ld8(ta0, *reinterpret_cast<uint32_t(*)[8]>(acc));
+            tmem_ld16(ta0 + 8, *reinterpret_cast<uint32_t(*)[16]>(acc + 8));
+          }
+        }
         tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) V[j] = V[j] * 128 + (long long)__float2int_rn(__uint_as_float(acc[j]));
+        for (int j = 0; j < CH; ++j) V[j] = V[j] * 128 + (long long)__float2int_rn(__uint_as_float(acc[j]));
       }
       fence_before();
       mbar_arrive(&accempty[b]);
       const int er = g.ea[g.a_row0 + bi * TM + r];
-      const bool lower = g.lower_mask != 0;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (lower && col0 + j > row) continue;
-        const int ec = g.eb[g.b_row0 + bj * TN + 16 * half + j];
+      for (int j = 0; j < CH; ++j) {
+        if (!live[j]) continue;
+        const int ec = g.eb[g.b_row0 + cofs + lc0 + j];
         const double x = i53_to_f64_scaled(V[j], er + ec - 7 * (S + 1));
         __stcs(cp + (int64_t)j * g.ldc, g.store ? x : cv[j] - x);
       }
@@ -1045,6 +1104,7 @@ cudaError_t make_split_maps(SplitOperand& op) {
       if ((e = make_tmap(&op.oz_a.m[s], base, op.rows, op.K, 2, 64, 128)) != cudaSuccess) return e;
       if ((e = make_tmap(&op.oz_b.m[s], base, op.rows, op.K, 2, 64, 32)) != cudaSuccess) return e;
       if ((e = make_tmap(&op.oz_ah.m[s], base, op.rows, op.K, 2, 64, 64)) != cudaSuccess) return e;
+      if ((e = make_tmap(&op.oz_b48.m[s], base, op.rows, op.K, 2, 64, 48)) != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -1144,9 +1204,14 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
   static PerDeviceOnce attr_once;
   {
     const cudaError_t e = attr_once([] {
-      cudaError_t r = cudaFuncSetAttribute(gemm_oz_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+      cudaError_t r = cudaFuncSetAttribute(gemm_oz_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           oz::Cfg<32>::SMEM_BYTES);
       if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(gemm_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES);
+        r = cudaFuncSetAttribute(gemm_oz_kernel<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 oz::Cfg<32>::SMEM_BYTES);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(gemm_oz_kernel<1, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 oz::Cfg<48>::SMEM_BYTES);
       return r;
     });
     if (e != cudaSuccess) return e;
@@ -1156,16 +1221,25 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
   GemmArgs g2 = g;
   g2.ea = A.ex;
   g2.eb = B.ex;
+  if (g.enum_mode == kEnumBand && g.panel % 128 == 0) {
+    // band tiles 128 x 48 (the caller counts 128 x 32 sub-tiles per panel pair)
+    const long long per32 = (long long)(g.panel / 128) * (g.panel / 32);
+    const long long per48 = (long long)(g.panel / 128) * ((g.panel + 47) / 48);
+    g2.ntiles = g.ntiles / per32 * per48;
+    const int grid = (int)(g2.ntiles < cap ? g2.ntiles : cap);
+    gemm_oz_kernel<1, 48><<<grid, kGemmThreads, oz::Cfg<48>::SMEM_BYTES, s>>>(A.oz_a, B.oz_b48, g2);
+    return cudaGetLastError();
+  }
   // CTA pairs sharing the A digits when the tiles pair up (even counts) and the launch may use
   // most of the GPU: a cluster needs two free SMs of one GPC at once, which a small SM share
   // beside other running kernels may not offer (the launch would then wait for them)
-  if (g.ntiles % 2 == 0 && cap >= 64 && (g.enum_mode == kEnumBand || g.enum_mode == kEnumFull) && g.nt % 2 == 0) {
+  if (g.ntiles % 2 == 0 && cap >= 64 && g.enum_mode == kEnumFull && g.nt % 2 == 0) {
     const long long pairs = g.ntiles / 2;
     const int grid = 2 * (int)(pairs < cap / 2 ? pairs : cap / 2);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kGemmThreads);
-    cfg.dynamicSmemBytes = oz::SMEM_BYTES;
+    cfg.dynamicSmemBytes = oz::Cfg<32>::SMEM_BYTES;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1174,10 +1248,10 @@ cudaError_t launch_gemm_oz(cudaStream_t s, const SplitOperand& A, const SplitOpe
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, gemm_oz_kernel<2>, A.oz_ah, B.oz_b, g2);
+    return cudaLaunchKernelEx(&cfg, gemm_oz_kernel<2, 32>, A.oz_ah, B.oz_b, g2);
   }
   const int grid = (int)(g.ntiles < cap ? g.ntiles : cap);
-  gemm_oz_kernel<1><<<grid, kGemmThreads, oz::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
+  gemm_oz_kernel<1, 32><<<grid, kGemmThreads, oz::Cfg<32>::SMEM_BYTES, s>>>(A.oz_a, B.oz_b, g2);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ struct SplitOperand {
   OzMaps oz_a;                // boxes 64 x 128 (A role)
   OzMaps oz_b;                // boxes 64 x 32  (B role)
   OzMaps oz_ah;               // boxes 64 x 64  (A role, half a tile: multicast by a CTA pair)
+  OzMaps oz_b48;              // boxes 64 x 48  (B role, 48-wide band tiles)
 };
 
 cudaError_t make_split_maps(SplitOperand& op);

@@ -4,7 +4,7 @@
 // Per theta the host precomputes every quantity that depends only on nu
 // (Gamma values, Temme's Gamma_1/Gamma_2, reciprocal tables) for the exact
 // routine, and the device builds from it an interpolation table of
-// Sigma / sigma^2 in s = (r / beta)^2, so that most entries cost a squared
+// Sigma in s = (r / beta)^2, so that most entries cost a squared
 // distance, a segment lookup on the bit pattern and a degree-8 polynomial.
 #include <math.h>
 
@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
   int ti, tj;
   tri_decode(blockIdx.x, ti, tj);
   const int64_t i = (int64_t)ti * 64 + (threadIdx.x & 63);
-  double vmax = 0.0;  // largest off-diagonal |Sigma_ij| of this thread (for the precision map)
+  // largest off-diagonal |Sigma_ij| of this thread (for the precision map), as a bit pattern:
+  // non-negative doubles order like their bits, so an integer maximum replaces an FP64 one
+  unsigned long long vmax = 0;
   if (i < npad) {
   double xi = 0.0, yi = 0.0;
   if (i < n) {
@@ -61,7 +63,8 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
     } else {
       const double r2 = model_dist2(P, xi, yi, __ldg(locs + 2 * j), __ldg(locs + 2 * j + 1));
       v = tab ? matern_value_tab(P, tab, r2) : matern_value(P, sqrt(r2));
-      vmax = fmax(vmax, fabs(v));
+      const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+      vmax = vb > vmax && vb <= 0x7FF0000000000000ull ? vb : vmax;  // NaN skipped, as fmax does
     }
     a[i + j * ld] = v;
     if (a2) a2[i + j * ld] = v;
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
   }
   if (offmax) {
     // non-negative doubles order like their bit patterns: one atomicMax per warp
-    unsigned long long b = (unsigned long long)__double_as_longlong(vmax);
+    unsigned long long b = vmax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);

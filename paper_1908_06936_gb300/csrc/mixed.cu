@@ -15,11 +15,11 @@ namespace exa {
 constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
-constexpr double kIrQuadTol = 1e-10;  // refinement stops once |z^T d| <= kIrQuadTol |z^T x|
-constexpr int kLookaheadSMs = 16;         // SMs left to the look-ahead stream during a trailing update
+constexpr double kIrQuadTol = 1e-10;  // refinement stops once q is final to this (relative)
+constexpr int kLookaheadSMs = 20;         // SMs left to the look-ahead stream during a trailing update
 constexpr int64_t kFuseMinRows = 40960;   // two panels per trailing pass down to this many rows
 constexpr int64_t kLateRows = 61440;      // one-panel phase: the look-ahead share grows below this many rows
-constexpr int kLateSMs = 76;              // ... up to this many SMs
+constexpr int kLateSMs = 48;              // ... up to this many SMs
 constexpr double kExactThreshold = 0.8;  // tiles holding |Sigma_ij| >= 0.8 sigma^2 get exact products
 constexpr double kSmoothNu = 1.2;        // above this smoothness every tile gets exact products
 constexpr double kWideBandNu = 0.75;     // from this smoothness one more panel of the band is exact

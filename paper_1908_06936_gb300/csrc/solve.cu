@@ -243,10 +243,11 @@ __global__ void __launch_bounds__(256) symv_tile_kernel(const double* __restrict
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) v[u][rr] = __ldcs(col + lane + 32 * rr);
     }
+    double cs[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + u;
-      double cs = 0.0;
+      cs[u] = 0.0;
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int r = lane + 32 * rr;
@@ -254,12 +255,22 @@ __global__ void __launch_bounds__(256) symv_tile_kernel(const double* __restrict
         const double er = (!diag || c <= r) ? e : 0.0;  // the upper half of a diagonal tile is not data
         const double ec = (!diag || r > c) ? e : 0.0;
         ra[rr] = fma(er, xj[c], ra[rr]);
-        cs = fma(ec, xi[r], cs);
+        cs[u] = fma(ec, xi[r], cs[u]);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-      if (lane == 0) colpart[(J * T + I) * kSymvNB + c] = cs;
     }
+    // the four column sums over the warp's 32 lanes, reduced together: halves of the set are
+    // exchanged at the first two levels (lanes 0-15 keep columns 0-1, 16-31 columns 2-3; then
+    // lanes with bit 3 clear keep the first), so 6 FP64 additions per lane instead of 20
+    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+    const double k0 = up16 ? cs[2] : cs[0], k1 = up16 ? cs[3] : cs[1];
+    const double s0 = up16 ? cs[0] : cs[2], s1 = up16 ? cs[1] : cs[3];
+    const double h0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const double h1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+    double q = (up8 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, up8 ? h0 : h1, 8);
+    q += __shfl_xor_sync(0xffffffffu, q, 4);
+    q += __shfl_xor_sync(0xffffffffu, q, 2);
+    q += __shfl_xor_sync(0xffffffffu, q, 1);
+    if ((lane & 7) == 0) colpart[(J * T + I) * kSymvNB + c0 + (up16 ? 2 : 0) + (up8 ? 1 : 0)] = q;
   }
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr) racc[warp][lane + 32 * rr] = ra[rr];
@@ -628,6 +639,8 @@ static int ptrsv_grid() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trsv_fwd_persistent_kernel, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, trsv_bwd_persistent_kernel, 256, 0);
     if (per2 < per) per = per2;
+    // two CTAs per SM: the off-chain updates need the loads in flight (one per SM, which would
+    // give the chain's CTA its SM's FP64 pipe to itself, measured 40 -> 54 ms per solve pair)
     if (per > 2) per = 2;
     return (per < 1 ? 1 : per) * (sms > 0 ? sms : 1);
   });
