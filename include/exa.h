@@ -87,6 +87,8 @@ typedef struct {
   float ms_chol;      /* device time of the Cholesky factorisation (ms) */
   float ms_solve;     /* device time of log-det + solve (+ refinement) (ms) */
   float ms_total;     /* device time of the whole evaluation (ms) */
+  double quad_err;    /* mixed: estimated relative error of quad (see exa_ctx_set_refinement_quad);
+                         FP64: 0 */
 } exa_result;
 
 /* Create a context on the current CUDA device.
@@ -136,13 +138,23 @@ exa_status exa_ctx_set_panel_fusion(exa_ctx* ctx, int64_t min_rows);
 /* Mixed precision: refinement stopping rule.  resid_target > 0: refine
  * x = Sigma^-1 z until ||z - Sigma x||_2 / ||z||_2 <= resid_target (or the
  * residual stops halving, or 10 steps); 0 (the default): stop once q is final
- * to 1e-10 relative, that is once a correction d = (L L^T)^-1 r of the residual
- * r = z - Sigma x changes z^T x by less than that, or once r^T d, the
- * second-order term of the variational estimate q = z^T x + x^T r + r^T d
- * (off by r^T (Sigma^-1 - (L L^T)^-1) r), is below it; q is then that estimate.
- * exa_result.ir_resid reports the last residual computed.
+ * to the tolerance of exa_ctx_set_refinement_quad.  exa_result.ir_resid reports
+ * the last residual computed.
  * EXA_ERR_ARG for a negative or non-finite target.                          */
 exa_status exa_ctx_set_refinement(exa_ctx* ctx, double resid_target);
+
+/* Mixed precision: relative accuracy to which the quadratic form is refined
+ * when exa_ctx_set_refinement's target is 0 (default 1e-8, far below the
+ * log-determinant's error of the mixed factor; 0 restores it).  With
+ * r = z - Sigma x and d = (L L^T)^-1 r, the variational estimate
+ * q = z^T x + x^T r + r^T d is off by r^T (Sigma^-1 - (L L^T)^-1) r, estimated
+ * as 100 rho |r^T d| with rho = ||r|| / ||r_prev|| the contraction of the last
+ * step (||r_prev|| = ||z|| at the first; the factor 100 covers the 3 to 40 times
+ * by which rho |r^T d| fell short of the true error on smooth fields); the
+ * refinement stops once that estimate, or 100 rho |z^T d| for the plain
+ * q = z^T (x + d), is at most tol |q|, and reports it relative to q in
+ * exa_result.quad_err.  EXA_ERR_ARG for tol < 0, tol >= 1e-3 or NaN.        */
+exa_status exa_ctx_set_refinement_quad(exa_ctx* ctx, double tol);
 
 /* Message describing the last error on this context ("" if none).  The
  * string is owned by the context and valid until its next call.           */

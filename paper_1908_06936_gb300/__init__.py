@@ -19,7 +19,7 @@ __all__ = [
     "EXA_ERR_IR_NOCONV", "EXA_FP64", "EXA_MIXED_TF32X3", "EXA_MIXED_BF16X3", "EXA_MIXED_FP32", "ExaError", "Context", "lib",
     "exa_ctx_create", "exa_ctx_destroy", "exa_ctx_set_stream", "exa_last_error", "exa_last_pivot",
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
-    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_ctx_set_lookahead_late", "exa_ctx_set_refinement", "exa_profile_enable",
+    "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_ctx_set_lookahead_late", "exa_ctx_set_refinement", "exa_ctx_set_refinement_quad", "exa_profile_enable",
     "exa_profile_read", "KernelStat", "exa_profile_timeline_enable", "exa_profile_timeline", "TimelineRec", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_probe_fp64_rate", "exa_predict", "exa_fisher", "exa_ctx_set_model",
 ]
 
@@ -56,7 +56,7 @@ class ExaResult(ctypes.Structure):
     _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
                 ("ir_resid", ctypes.c_double), ("ir_iters", ctypes.c_int32), ("tile_nb", ctypes.c_int32),
                 ("exact_band", ctypes.c_int32), ("n_tiles", ctypes.c_int32), ("ms_gen", ctypes.c_float), ("ms_chol", ctypes.c_float), ("ms_solve", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("quad_err", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
                 "exa_ctx_set_panel_fusion": (ctypes.c_int, [_P, ctypes.c_int64]),
                 "exa_ctx_set_lookahead_late": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int]),
                 "exa_ctx_set_refinement": (ctypes.c_int, [_P, ctypes.c_double]),
+                "exa_ctx_set_refinement_quad": (ctypes.c_int, [_P, ctypes.c_double]),
                 "exa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
                 "exa_loglik_noalloc": (ctypes.c_int, [_P, _P, _P, _PD, _I64, _PD]),
                 "exa_ctx_set_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]),
@@ -257,6 +258,10 @@ def exa_ctx_set_lookahead(ctx: int, sms: int) -> int:
 
 def exa_ctx_set_refinement(ctx: int, resid_target: float) -> int:
     return lib().exa_ctx_set_refinement(_P(ctx), float(resid_target))
+
+
+def exa_ctx_set_refinement_quad(ctx: int, tol: float) -> int:
+    return lib().exa_ctx_set_refinement_quad(_P(ctx), float(tol))
 
 
 def exa_ctx_set_lookahead_late(ctx: int, rows: int, sms: int) -> int:

@@ -60,6 +60,7 @@ struct exa_ctx {
   int keep_block_inverses = 0;  // mixed factorisation: write block k's inverse to mx_wall + k 512^2
   int ir_tight = 0;         // mixed refinement: iterate to rounding level (the gradient needs Sigma^-1 z)
   double ir_target = 0.0;   // mixed refinement: relative residual to reach (0: quadratic-form rule)
+  double ir_quad_tol = 0.0; // mixed refinement: relative accuracy of q (0: the default)
   int grad_inverse_fp64 = 0;  // mixed gradient: Sigma^-1 of the mixed factor on FP64 DMMA instead of the tensor cores
   exa::DevBuf mx_offmax;    // per tile-row offset max |Sigma_ij| (precision map)
   exa::DevBuf mx_symv;      // partial sums of the tiled symmetric product

@@ -15,7 +15,11 @@ namespace exa {
 constexpr int kMixNB = kMixPanel;  // panel width = K of every tensor-core product
 constexpr int kMixSub = 128;     // FP64 sub-tile of the diagonal block
 constexpr double kIrFailTol = 1e-8;
-constexpr double kIrQuadTol = 1e-10;  // refinement stops once q is final to this (relative)
+constexpr double kIrQuadTol = 1e-8;   // refinement stops once q is final to this (relative), by default
+// The error estimates below use the contraction of the last step, which measured 3 to 40 times
+// below the true error of the quadratic form on smooth fields (the residual of a preconditioned
+// step gathers in the directions where Sigma^-1 is large); they are taken 100 times over.
+constexpr double kIrQuadSafety = 100.0;
 constexpr int kLookaheadSMs = 20;         // SMs left to the look-ahead stream during a trailing update
 constexpr int64_t kFuseMinRows = 40960;   // two panels per trailing pass down to this many rows
 constexpr int64_t kLateRows = 61440;      // one-panel phase: the look-ahead share grows below this many rows
@@ -528,7 +532,11 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     return st;
   double* sp = (double*)c->mx_symv.p;
   double rel = 0.0, prev = 1e300;
-  double q_var = NAN;  // the variational estimate, when it ended the refinement
+  double rel_prev = 1.0;  // ||r|| / ||z|| of the step before (the residual of x = 0 is z itself)
+  double rho = 1.0;       // contraction of the last step, ||r_k|| / ||r_k-1||
+  double q_var = NAN;     // the variational estimate, when it ended the refinement
+  double q_err = NAN;     // estimated relative error of the q returned
+  const double qtol = c->ir_quad_tol > 0.0 ? c->ir_quad_tol : kIrQuadTol;
   bool q_done = false;
   // stopping rule: a caller's residual target (exa_ctx_set_refinement), rounding level for the
   // gradient (which needs Sigma^-1 z itself), else the quadratic-form rule (target < 0)
@@ -546,6 +554,8 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     if (e != cudaSuccess) return cuda_err(c, e, "refinement launch");
     if ((st = read_status(c)) != EXA_OK) return st;  // synchronises
     rel = sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]);
+    rho = rel_prev > 0.0 ? rel / rel_prev : 1.0;
+    rel_prev = rel;
     if (!(rel > (target > 0.0 ? target : 1e-15)) || it >= kMaxIt || rel > 0.5 * prev) break;
     prev = rel;
     e = solve_llt(c, A, npad, npad, r, d, work, (int*)red);
@@ -564,14 +574,19 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     if (e != cudaSuccess) return cuda_err(c, e, "refinement solve");
     if ((st = read_status(c)) != EXA_OK) return st;
     if (target < 0.0) {
+      // q_hat is off by r^T (Sigma^-1 - (L L^T)^-1) r: about the step's contraction times r^T d
       const double q_hat = c->h_scalars[8] + c->h_scalars[6] + c->h_scalars[7];
-      if (fabs(c->h_scalars[7]) <= kIrQuadTol * fabs(q_hat)) {
+      const double e_var = kIrQuadSafety * rho * fabs(c->h_scalars[7]);
+      const double e_plain = kIrQuadSafety * rho * fabs(c->h_scalars[4]);
+      if (e_var <= qtol * fabs(q_hat)) {
         q_var = q_hat;
+        q_err = e_var / fabs(q_hat);
         q_done = true;
         ++it;
         break;
       }
-      if (fabs(c->h_scalars[4]) <= kIrQuadTol * fabs(c->h_scalars[5])) {
+      if (e_plain <= qtol * fabs(c->h_scalars[5])) {  // z^T (x + d) is off by about rho |z^T d|
+        q_err = e_plain / fabs(c->h_scalars[5]);
         q_done = true;
         ++it;
         break;
@@ -579,7 +594,11 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     }
   }
   e = launch_dot(s, zp, x, npad, part, c->d_scalars + 0);
+  // x^T r for the error estimate of a refinement that stopped on its residual (r then belongs to x)
+  if (e == cudaSuccess && isnan(q_err)) e = launch_dot(s, x, r, npad, part, c->d_scalars + 9);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && isnan(q_err))
+    e = cudaMemcpyAsync(c->h_scalars + 9, c->d_scalars + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_err(c, e, "quadratic form");
   cudaEventRecord(c->ev[3], s);
   if ((st = read_status(c)) != EXA_OK) return st;
@@ -593,6 +612,9 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   out->ir_iters = it;
   out->ir_resid = rel;
   out->quad = isnan(q_var) ? c->h_scalars[0] : q_var;
+  // stopped on the residual (a caller's target, rounding level or stalling): x^T r, the first-order
+  // term q lacks, measured against q
+  out->quad_err = !isnan(q_err) ? q_err : fabs(c->h_scalars[9]) / fabs(out->quad);
   out->logdet = 2.0 * c->h_scalars[1];
   out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * out->logdet - 0.5 * out->quad;
   if (!q_done && !(rel <= kIrFailTol))
@@ -607,6 +629,13 @@ using namespace exa;
 extern "C" exa_status exa_ctx_set_far_tile_margin(exa_ctx* c, int bits) {
   if (!c || bits < 0) return c ? set_err(c, EXA_ERR_ARG, "far-tile margin must be >= 0") : EXA_ERR_ARG;
   c->far_tile_margin = bits;
+  return EXA_OK;
+}
+
+extern "C" exa_status exa_ctx_set_refinement_quad(exa_ctx* c, double tol) {
+  if (!c) return EXA_ERR_ARG;
+  if (!(tol >= 0.0) || !(tol < 1e-3)) return set_err(c, EXA_ERR_ARG, "quadratic-form tolerance must be in [0, 1e-3)");
+  c->ir_quad_tol = tol;
   return EXA_OK;
 }
 

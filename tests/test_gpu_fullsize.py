@@ -55,7 +55,8 @@ def test_fullsize_mixed_scaling_and_repeatability():
         a2 = c.loglik_ex(dl, dz, THETA, exa.EXA_MIXED_TF32X3)
         b = c.loglik_ex(dl, dz, (4.0, THETA[1], THETA[2]), exa.EXA_MIXED_TF32X3)
     assert a["loglik"] == a2["loglik"] and a["logdet"] == a2["logdet"] and a["quad"] == a2["quad"]
-    # (the refinement stops on the quadratic form, so the last residual may stay well above 1e-8)
-    assert a["n_tiles"] == 176 and 1 <= a["exact_band"] <= a["n_tiles"] and a["ir_resid"] <= 1e-5
+    # (the refinement stops on the quadratic form, so the last residual may stay near 1e-4)
+    assert a["n_tiles"] == 176 and 1 <= a["exact_band"] <= a["n_tiles"] and a["ir_resid"] <= 1e-3
+    assert 0.0 < a["quad_err"] <= 1e-8
     assert abs(b["logdet"] - (a["logdet"] + n * math.log(4.0))) <= 1e-12 * abs(a["logdet"]) + 1e-9
     assert abs(b["quad"] - a["quad"] / 4.0) <= 1e-10 * a["quad"]

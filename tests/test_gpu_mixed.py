@@ -35,9 +35,9 @@ def test_mixed_vs_oracle(ctx, m, theta):
     rel = abs(got["loglik"] - ref["l"]) / abs(ref["l"])
     print("m=%d theta=%s |dl|/|l|=%.3e ir_iters=%d ir_resid=%.2e" % (m, theta, rel, got["ir_iters"], got["ir_resid"]))
     assert rel <= 1e-6
-    # the refinement stops once q is final to 1e-10 (its variational estimate is second order in
-    # the residual), so the last residual taken may stay near 1e-7; q itself is checked below
-    assert got["ir_resid"] <= 1e-5
+    # the refinement stops once q is final (its variational estimate is second order in the
+    # residual), so the last residual taken may stay near 1e-4; q itself is checked below
+    assert got["ir_resid"] <= 1e-3
     assert 1 <= got["exact_band"] <= got["n_tiles"]
     # the refined quadratic form is accurate far beyond the factor's precision
     assert abs(got["quad"] - ref["quad"]) <= 1e-9 * abs(ref["quad"])
@@ -265,18 +265,21 @@ def test_refinement_to_residual_target(ctx):
     assert abs(b["quad"] - ref["quad"]) <= 1e-12 * abs(ref["quad"])
     assert abs(b["loglik"] - ref["l"]) <= 1e-6 * abs(ref["l"])
     assert exa.exa_ctx_set_refinement(ctx.handle, -1.0) == exa.EXA_ERR_ARG
+    for bad in (-1e-9, 1e-3, float("nan")):
+        assert exa.exa_ctx_set_refinement_quad(ctx.handle, bad) == exa.EXA_ERR_ARG
     # the default rule's q (the variational estimate, when it ends the refinement) agrees with the
-    # q of a solution refined to rounding level, and with the oracle's
-    assert abs(a["quad"] - b["quad"]) <= 1e-10 * abs(b["quad"])
-    assert abs(a["quad"] - ref["quad"]) <= 1e-10 * abs(ref["quad"])
+    # q of a solution refined to rounding level within its reported error estimate, and with the
+    # oracle's
+    assert 0.0 < a["quad_err"] <= 1e-8
+    assert abs(a["quad"] - b["quad"]) <= a["quad_err"] * abs(b["quad"]) + 1e-12 * abs(b["quad"])
+    assert abs(a["quad"] - ref["quad"]) <= 1e-9 * abs(ref["quad"])
 
 
 @pytest.mark.parametrize("theta", [(1.0, 0.03, 0.5), (1.0, 0.1, 1.0), (1.0, 0.3, 0.5), (2.0, 0.05, 1.5)])
 def test_quadratic_form_stopping_rule_vs_oracle(ctx, theta):
     # short- and long-range, rough and smooth fields on a 70 x 70 grid (ten 512 panels): the
-    # quadratic form of the default stopping rule against the oracle's (to 1e-9, the bound the
-    # oracle's own rounding allows on these conditionings) and against the same factor's
-    # solution refined to rounding level (to 1e-10, the rule's target)
+    # quadratic form of the default stopping rule against the oracle's (to 1e-9) and against the
+    # same factor's solution refined to rounding level (within the reported error estimate)
     import paper_1908_06936_gb300 as exa
 
     locs, Z = workload(70, seed=31, theta0=theta)
@@ -286,10 +289,12 @@ def test_quadratic_form_stopping_rule_vs_oracle(ctx, theta):
         theta, got["ir_iters"], got["ir_resid"], abs(got["quad"] - ref["quad"]) / abs(ref["quad"])))
     assert abs(got["quad"] - ref["quad"]) <= 1e-9 * abs(ref["quad"])
     assert abs(got["loglik"] - ref["l"]) <= 1e-6 * abs(ref["l"])
-    # against the same factor's solution refined to rounding level (no oracle rounding involved)
+    # against the same factor's solution refined to rounding level (no oracle rounding involved):
+    # within the error estimate the call reports, itself within the 1e-8 default
     assert exa.exa_ctx_set_refinement(ctx.handle, 1e-14) == exa.EXA_OK
     try:
         tight = ctx.loglik_ex(to_dev(locs), to_dev(Z), theta, exa.EXA_MIXED_TF32X3)
     finally:
         exa.exa_ctx_set_refinement(ctx.handle, 0.0)
-    assert abs(got["quad"] - tight["quad"]) <= 1e-10 * abs(tight["quad"])
+    assert got["quad_err"] <= 1e-8
+    assert abs(got["quad"] - tight["quad"]) <= got["quad_err"] * abs(tight["quad"]) + 1e-12 * abs(tight["quad"])
