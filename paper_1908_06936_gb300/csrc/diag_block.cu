@@ -16,7 +16,7 @@
 //         is copied into the matrix; CTA 0 updates the next leaf first and runs its (a) meanwhile
 //   Inverse W = L^-1 by doubling: the 64-inverses V_j are the leaves; a 2b block
 //   [[X_A, 0], [L_BA, X_B]] has inverse [[W_A, 0], [-W_B (L_BA W_A), W_B]], formed for
-//   b = 64, 128, 256 as two rounds of 32 x 32 product tasks each.
+//   b = 64, 128, 256 as two steps of 32 x 32 product tasks each.
 //
 // Outputs: L in the block's lower triangle (upper triangle untouched), log L_ii summed in row
 // order per 128 sub-tile, the four 128 x 128 sub-tile inverses (row-major, zero above the
@@ -32,7 +32,7 @@ constexpr int kDW = 64;         // Cholesky step / inverse leaf
 constexpr int kDT = 32;         // product task tile
 constexpr int kDThreads = 256;
 constexpr int kDSteps = kDB / kDW;
-// scratch (doubles): the eight 64-inverses, the 256 x 256 product of the widest inverse round,
+// scratch (doubles): the eight 64-inverses, the 256 x 256 product of the widest inverse step,
 // then the current Cholesky step's panel (448 x 64)
 constexpr int64_t kDiagT = (int64_t)kDSteps * kDW * kDW;
 constexpr int64_t kDiagP = kDiagT + 256 * 256;
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_cons
   for (int h = kDW; h < kDB; h *= 2) {
     const int pairs = kDB / (2 * h);             // blocks of width 2h
     const int tiles = (h / kDT) * (h / kDT);     // 32 x 32 tiles of one h x h product
-    // round 1: T_p = L_BA W_A  (L_BA: rows p 2h + h .., columns p 2h ..; W_A lower, row-major in w2)
+    // first product: T_p = L_BA W_A  (L_BA: rows p 2h + h .., columns p 2h ..; W_A lower, row-major in w2)
     for (int t = b; t < pairs * tiles; t += G) {
       const int p = t / tiles, q = t % tiles, ti = q / (h / kDT), tj = q % (h / kDT);
       const int64_t o = (int64_t)p * 2 * h;  // block origin within the 512 block
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kDThreads) diag_block_kernel(const __grid_cons
         for (int v = 0; v < 2; ++v) Tp[(ti * kDT + 2 * ty + u) * h + tj * kDT + 2 * tx + v] = acc[u][v];
     }
     sync_all();
-    // round 2: W_BA = -W_B T_p  (W_B lower, row-major in w2 at (o + h, o + h))
+    // second product: W_BA = -W_B T_p  (W_B lower, row-major in w2 at (o + h, o + h))
     for (int t = b; t < pairs * tiles; t += G) {
       const int p = t / tiles, q = t % tiles, ti = q / (h / kDT), tj = q % (h / kDT);
       const int64_t o = (int64_t)p * 2 * h;

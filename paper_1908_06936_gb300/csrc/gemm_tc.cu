@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       const bool diag = tl.diag;
       const int64_t ldc = tl.ldc;
       double* cp = tl.C + r;
-      // two rounds of 32 C loads in flight per thread (64 KB per SM), then drain TMEM
+      // two batches of 32 C loads in flight per thread (64 KB per SM), then drain TMEM
 #pragma unroll 1
       for (int h2 = 0; h2 < 2; ++h2) {
         const int cb = half * 64 + h2 * 32;
