@@ -225,8 +225,11 @@ exa_status exa_ctx_set_gradient_inverse(exa_ctx* ctx, int fp64);
  *             operands with FP32 accumulation over the tile and added to the
  *             FP64 tile (tiles within the band set by exa_ctx_set_batched_mixed
  *             stay FP64), then x = Sigma^-1 z refined in FP64 against an FP64
- *             copy of Sigma, q = z^T x; a replicate whose refinement stalls
- *             above a 1e-8 relative residual reports EXA_ERR_IR_NOCONV.
+ *             copy of Sigma until q is final to 1e-8 relative by the rule of
+ *             exa_ctx_set_refinement_quad (variational estimate, error taken as
+ *             100 x the last step's contraction x |r^T d|), else to rounding
+ *             level with q = z^T x; a replicate whose refinement stalls above a
+ *             1e-8 relative residual before that reports EXA_ERR_IR_NOCONV.
  *             EXA_MIXED_TF32X3: the same precision pattern on the tensor cores,
  *             step-synchronous over 128-wide tile columns: per step one launch
  *             factors every replicate's FP64 diagonal tile, then grouped tcgen05

@@ -559,6 +559,12 @@ __global__ void __launch_bounds__(256) batched_solve_kernel(int nrep, const BMet
 // ---------------------------------------------------------------------------
 constexpr int kIrThreads = 1024;
 constexpr double kIrFail = 1e-8;  // relative residual above which a replicate reports EXA_ERR_IR_NOCONV
+// The refinement ends once q is final to kIrQTol relative, by the variational estimate
+// q = z^T x + x^T r + r^T d (d = (L L^T)^-1 r), off by r^T (Sigma^-1 - (L L^T)^-1) r, whose
+// size is estimated as kIrQSafety times the last step's contraction times |r^T d| (the rule of
+// the single-field mixed path).
+constexpr double kIrQTol = 1e-8;
+constexpr double kIrQSafety = 100.0;
 
 // Block-wide sum, the same order on every call (warp shuffles, then warp 0).
 __device__ __forceinline__ double ir_block_sum(double v, double* red) {
@@ -729,24 +735,50 @@ __global__ void __launch_bounds__(kIrThreads) batched_ir_kernel(
   }
   const double zn2 = ir_block_sum(zz, red);
   double prev = 1e300, rel = 1e300;
+  double rel_cur = 1.0, rel_prev = 1.0;  // ||r|| / ||z|| of this step and the one before (r_0 = z)
+  double q = 0.0;
+  bool q_done = false;
   for (int it = 0; it < max_iter; ++it) {
     ir_forward<NB>(L, W, ld, T, rv, y, part, sv);
-    ir_backward<NB>(L, W, ld, T, npad, y, sv);
+    ir_backward<NB>(L, W, ld, T, npad, y, sv);  // y = d = (L L^T)^-1 r
+    if (it > 0) {  // at it = 0, x = 0 and r = z: the estimate is the plain first solve's
+      double xr = 0.0, rd = 0.0, zx0 = 0.0;
+      for (int64_t i = tid; i < npad; i += kIrThreads) {
+        xr = fma(x[i], rv[i], xr);
+        rd = fma(rv[i], y[i], rd);
+        if (i < n) zx0 = fma(m.z[i], x[i], zx0);
+      }
+      const double a = ir_block_sum(xr, red);
+      const double b = ir_block_sum(rd, red);
+      const double c0 = ir_block_sum(zx0, red);
+      const double q_hat = c0 + a + b;
+      const double rho = rel_prev > 0.0 ? rel_cur / rel_prev : 1.0;
+      if (kIrQSafety * rho * fabs(b) <= kIrQTol * fabs(q_hat)) {
+        q = q_hat;
+        q_done = true;
+        rel = rel_cur;
+        break;
+      }
+    }
     for (int64_t i = tid; i < npad; i += kIrThreads) x[i] += y[i];
     __syncthreads();
     const double rn2 = ir_residual(S, ld, n, npad, m.z, x, rv, red);
     rel = zn2 > 0.0 ? sqrt(rn2 / zn2) : 0.0;
     if (!(rel > 1e-15) || rel > 0.5 * prev) break;  // converged, or no longer contracting
     prev = rel;
+    rel_prev = rel_cur;
+    rel_cur = rel;
   }
-  double zx = 0.0;
-  for (int64_t i = tid; i < n; i += kIrThreads) zx = fma(m.z[i], x[i], zx);
-  const double q = ir_block_sum(zx, red);
+  if (!q_done) {
+    double zx = 0.0;
+    for (int64_t i = tid; i < n; i += kIrThreads) zx = fma(m.z[i], x[i], zx);
+    q = ir_block_sum(zx, red);
+  }
   if (tid == 0) {
     double ldet = 0.0;
     for (int k = 0; k < T; ++k) ldet += ldpart[m.lo + k];
     ldet *= 2.0;
-    if (rel <= kIrFail) {
+    if (q_done || rel <= kIrFail) {
       loglik[r] = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * ldet - 0.5 * q;
     } else {
       loglik[r] = NAN;
