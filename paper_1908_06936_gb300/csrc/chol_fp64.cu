@@ -604,39 +604,4 @@ cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double al
   return cudaGetLastError();
 }
 
-// W (2nb x 2nb, row-major, lower) <- [W00 0; 0 W11] from two inverted nb x nb
-// diagonal tiles; the W10 block is filled by two small products afterwards.
-__global__ void assemble_w2_kernel(const double* __restrict__ w00, const double* __restrict__ w11, int nb,
-                                   double* __restrict__ w) {
-  const int n2 = 2 * nb;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2 * n2; idx += gridDim.x * blockDim.x) {
-    const int r = idx / n2, c = idx % n2;
-    double v = 0.0;
-    if (r < nb && c < nb)
-      v = w00[r * nb + c];
-    else if (r >= nb && c >= nb)
-      v = w11[(r - nb) * nb + (c - nb)];
-    w[idx] = v;
-  }
-}
-
-__global__ void assemble_wblocks_kernel(const double* __restrict__ wk, int nb, int sub, double* __restrict__ w) {
-  const int n2 = nb * sub;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2 * n2; idx += gridDim.x * blockDim.x) {
-    const int r = idx / n2, c = idx % n2;
-    const int bi = r / nb, bj = c / nb;
-    w[idx] = (bi == bj) ? wk[(int64_t)bi * nb * nb + (r % nb) * nb + (c % nb)] : 0.0;
-  }
-}
-
-cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w) {
-  assemble_wblocks_kernel<<<128, 256, 0, s>>>(wk, nb, sub, w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w) {
-  assemble_w2_kernel<<<64, 256, 0, s>>>(w00, w11, nb, w);
-  return cudaGetLastError();
-}
-
 }  // namespace exa

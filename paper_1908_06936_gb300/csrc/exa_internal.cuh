@@ -143,8 +143,6 @@ struct DevStatus {
 cudaError_t launch_matern_gen(cudaStream_t s, const double* locs, int64_t n, int64_t npad, const MaternParams& p,
                               double* a, int64_t ld, unsigned long long* offmax = nullptr,
                               const MaternTable* tab = nullptr, int panel = 256, double* a2 = nullptr);
-// W (sub*nb square, row-major) <- block diagonal of `sub` inverted nb x nb tiles, zero elsewhere.
-cudaError_t launch_assemble_wblocks(cudaStream_t s, const double* wk, int nb, int sub, double* w);
 // One diagonal tile of a batched factorisation: FP64 Cholesky of the 128 x 128 tile at (k0, k0) of a
 // (column-major, ld), its log sum to *logdet and its inverse (row-major) to w; failures to *st.
 struct DiagTileTask {
@@ -188,7 +186,6 @@ cudaError_t launch_sum(cudaStream_t s, const double* v, int64_t n, double* parti
 cudaError_t launch_dgemm_nt_small(cudaStream_t s, int M, int N, int K, double alpha, const double* a, int64_t ar,
                                   int64_t ac, const double* b, int64_t br, int64_t bc, double beta, double* c,
                                   int64_t cr, int64_t cc, const DevStatus* st);
-cudaError_t launch_assemble_w2(cudaStream_t s, const double* w00, const double* w11, int nb, double* w);
 // Persistent forward + backward solve with 128-wide tiles: x = (L L^T)^-1 rhs.  The
 // strictly upper off-diagonal tiles of a must hold L^T (launch_transpose_lower_to_upper).
 // rhs_work (npad, overwritten) and flags (2 npad/128 + 1 ints) are scratch.
@@ -197,9 +194,8 @@ cudaError_t launch_llt_solve_persistent(cudaStream_t s, const double* a, int64_t
 // Writes L^T into the strictly upper off-diagonal 128-tiles of a (npad % 128 == 0).
 cudaError_t launch_transpose_lower_to_upper(cudaStream_t s, double* a, int64_t ld, int64_t npad);
 // Refinement helpers.
-cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y);
-// Same product in one pass over 128 x 128 tiles (npad % 128 == 0); partials holds
-// symv_tiled_partials(npad) doubles.  Fixed summation order.
+// y = Sigma x from the lower triangle of Sigma (column-major, ld) in one pass over 128 x 128
+// tiles (npad % 128 == 0); partials holds symv_tiled_partials(npad) doubles.  Fixed summation order.
 int64_t symv_tiled_partials(int64_t npad);
 cudaError_t launch_symv_lower_tiled(cudaStream_t s, const double* a, int64_t ld, int64_t npad, const double* x,
                                     double* y, double* partials);

@@ -183,28 +183,6 @@ namespace exa {
 // two deterministic passes that each stream the triangle once:
 //   pass 1 (thread per row i):  y_i  = sum_{j <= i} S_ij x_j
 //   pass 2 (warp per column i): y_i += sum_{j > i}  S_ji x_j
-__global__ void __launch_bounds__(256) symv_lower_rows_kernel(const double* __restrict__ s, int64_t ld, int64_t n,
-                                                              const double* __restrict__ x, double* __restrict__ y) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int64_t j = 0; j <= i; ++j) acc = fma(s[i + j * ld], x[j], acc);
-  y[i] = acc;
-}
-
-__global__ void __launch_bounds__(256) symv_lower_cols_kernel(const double* __restrict__ s, int64_t ld, int64_t n,
-                                                              const double* __restrict__ x, double* __restrict__ y) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + warp;
-  if (i >= n) return;
-  const double* col = s + i * ld;
-  double acc = 0.0;
-  for (int64_t j = i + 1 + lane; j < n; j += 32) acc = fma(col[j], x[j], acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[i] += acc;
-}
-
 // One pass over the lower triangle in 128 x 128 tiles: tile (I, J), I >= J, is read
 // once and gives both of its contributions,
 //   rowpart[I][J][r] = sum_c S_IJ(r, c) x_J(c)          (to y_I)
@@ -336,11 +314,6 @@ __global__ void __launch_bounds__(kRedThreads) dot_stage1(const double* __restri
   if (threadIdx.x == 0) partial[blockIdx.x] = r;
 }
 
-cudaError_t launch_symv_lower(cudaStream_t s, const double* a, int64_t ld, int64_t n, const double* x, double* y) {
-  symv_lower_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, ld, n, x, y);
-  symv_lower_cols_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(a, ld, n, x, y);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_residual(cudaStream_t s, const double* z, const double* y, double* r, int64_t n) {
   residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, y, r, n);
