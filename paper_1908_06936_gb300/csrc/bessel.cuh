@@ -262,6 +262,10 @@ __device__ __forceinline__ void table_segment_coefs(const double* __restrict__ n
   for (int i = 0; i < N; ++i) T->a[sgi][i] = a[i];
 }
 
+// The exact routine as an out-of-line call for the table's rare out-of-range entries, so that
+// its registers and stack stay out of the generators' per-entry loops.
+static __device__ __noinline__ double matern_value_exact(const MaternParams& P, double r) { return matern_value(P, r); }
+
 // Sigma at squared distance r2 = r^2 from the table (exact routine outside its range).  The
 // tests are integer work on the bit patterns: FP64 instructions are the scarce resource of the
 // generation (~2 per clock per SM on this part), FP64 comparisons included.
@@ -273,7 +277,7 @@ __device__ __forceinline__ double matern_value_tab(const MaternParams& P, const 
   // 2^-8 <= s < 2^12 exactly when the sign is clear and the biased exponent is in [1015, 1035)
   // (negative, zero, subnormal, infinite and NaN values all fall outside)
   const unsigned int se = (unsigned int)((unsigned long long)__double_as_longlong(s) >> 52);
-  if (se - (unsigned int)(1023 + kTabE0) >= (unsigned int)kTabOct) return matern_value(P, sqrt(r2));
+  if (se - (unsigned int)(1023 + kTabE0) >= (unsigned int)kTabOct) return matern_value_exact(P, sqrt(r2));
   const int sgi = table_segment(s);
   const double t = fma(s, __ldg(&T->ih[sgi]), __ldg(&T->mc[sgi]));
   const double* c = T->a[sgi];

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) matern_gen_kernel(const double* __restric
       v = P.sigma2 + P.nugget;
     } else {
       const double r2 = model_dist2(P, xi, yi, __ldg(locs + 2 * j), __ldg(locs + 2 * j + 1));
-      v = tab ? matern_value_tab(P, tab, r2) : matern_value(P, sqrt(r2));
+      v = tab ? matern_value_tab(P, tab, r2) : matern_value_exact(P, sqrt(r2));
       const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
       vmax = vb > vmax && vb <= 0x7FF0000000000000ull ? vb : vmax;  // NaN skipped, as fmax does
     }
