@@ -634,6 +634,24 @@ def aggregate_over_ranks(ms_total: float, units_per_rank: float, world: int, dev
     return ms_max, world * units_per_rank / (ms_max / 1e3)
 
 
+def record_steps(step, k: int, stream, event_cls) -> tuple[list, object]:
+    """Runs step() k times with a timing event recorded on `stream` before the first step and after
+    each one (k + 1 events, no synchronisation between steps).  Returns (events, last result)."""
+    evs = [event_cls(enable_timing=True) for _ in range(k + 1)]
+    evs[0].record(stream)
+    res = None
+    for i in range(k):
+        res = step()
+        evs[i + 1].record(stream)
+    return evs, res
+
+
+def step_times(evs) -> tuple[float, list[float]]:
+    """(ms from the first event to the last, ms of each step) of events from record_steps, once the
+    stream has been synchronised."""
+    return evs[0].elapsed_time(evs[-1]), [evs[i].elapsed_time(evs[i + 1]) for i in range(len(evs) - 1)]
+
+
 def run_ours(args, rank: int, world: int) -> dict | None:
     import numpy as np
     import torch
@@ -661,17 +679,11 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         tdist.barrier()
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    res = None
-    for _ in range(args.steps):
-        res = ctx.loglik_ex(dl, dz, THETA0, prec)
-    e1.record(s)
+    evs, res = record_steps(lambda: ctx.loglik_ex(dl, dz, THETA0, prec), args.steps, s, torch.cuda.Event)
     torch.cuda.synchronize()
     if dist:
         tdist.barrier()
-    ms_total = e0.elapsed_time(e1)
+    ms_total, ms_steps = step_times(evs)
     clk = clocks.stop()
     stats = exa.exa_profile_read(ctx.handle, reset=1)
     exa.exa_profile_enable(ctx.handle, 0)
@@ -749,7 +761,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "mixed": {"evals_per_s": value / world, "chol_tflops": chol_tflops, "ms_gen": res["ms_gen"],
                       "ms_chol": res["ms_chol"], "ms_solve": res["ms_solve"], "ir_iters": res["ir_iters"],
                       "ir_resid": res["ir_resid"], "exact_band": res["exact_band"], "n_tiles": res["n_tiles"],
-                      "loglik": res["loglik"]},
+                      "loglik": res["loglik"], "ms_steps": ms_steps, "ms_step_best": min(ms_steps),
+                      "ms_step_median": statistics.median(ms_steps)},
             "fp64": fp64,
             "rel_dl_vs_fp64": (abs(res["loglik"] - fp64["loglik"]) / abs(fp64["loglik"])) if fp64 else None,
             "speedup_mixed_vs_fp64": (fp64["ms_per_eval"] / (ms_max / args.steps)) if fp64 else None,

@@ -71,3 +71,42 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
             bench.main()
         assert buf.getvalue() == expect
     assert len(called) == 1
+
+
+class _Clock:
+    t = 0.0
+
+
+class _FakeEvent:
+    """Stands in for torch.cuda.Event: record() reads a host clock that the fake steps advance."""
+
+    def __init__(self, enable_timing=False):
+        assert enable_timing
+        self.t = None
+
+    def record(self, stream):
+        assert stream == "stream"
+        self.t = _Clock.t
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+@pytest.mark.parametrize("durations", [[5.0], [3.0, 7.0, 4.0], [2.0, 2.0, 9.0, 1.0, 2.5]])
+def test_timed_steps_give_each_step_and_the_whole_region(durations):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    _Clock.t = 100.0
+    it = iter(durations)
+
+    def step():
+        d = next(it)
+        _Clock.t += d
+        return d
+
+    evs, last = bench.record_steps(step, len(durations), "stream", _FakeEvent)
+    assert len(evs) == len(durations) + 1 and last == durations[-1]
+    total, per = bench.step_times(evs)
+    assert per == durations
+    assert total == pytest.approx(sum(durations))
