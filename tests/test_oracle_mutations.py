@@ -62,6 +62,15 @@ MUTANTS = [
      [MODEL], "sin(0.5 * (p2 - p1))", "sin(p2 - p1)", 1),
     ("nugget added off the diagonal",
      [MODEL], "oracle_dist(locs, i, j)) + (i == j ? g_nugget : 0.0);", "oracle_dist(locs, i, j)) + g_nugget;", 1),
+    ("great circle: latitude and longitude swapped",
+     [MODEL], "const double p1 = y1 * rad, p2 = y2 * rad;\n    const double sp = sin(0.5 * (p2 - p1)), "
+              "sl = sin(0.5 * (x2 - x1) * rad);",
+     "const double p1 = x1 * rad, p2 = x2 * rad;\n    const double sp = sin(0.5 * (p2 - p1)), "
+     "sl = sin(0.5 * (y2 - y1) * rad);", 1),
+    ("nugget dropped",
+     [MODEL], "oracle_dist(locs, i, j)) + (i == j ? g_nugget : 0.0);", "oracle_dist(locs, i, j));", 1),
+    ("kriging: variance reduction halved",
+     [PREDICT], "var[i] = theta[0] - ww;", "var[i] = theta[0] - 0.5 * ww;", 1),
     ("kriging: sign of the variance reduction",
      [PREDICT], "var[i] = theta[0] - ww;", "var[i] = theta[0] + ww;", 1),
     ("kriging: mean from L^-1 Z instead of Sigma^-1 Z",
