@@ -154,6 +154,7 @@ def gpu_id_for_smi() -> str | None:
 
 # ----------------------------------------------------------------------------- CPU oracle
 CPU_CURVE_SIDES = (40, 50, 60, 70)  # oracle timed at n = 1,600 ... 4,900 (jittered m x m grids)
+BATCH_REPLICATES, BATCH_SIDES_SEED = 256, 5  # the batched leg's replicates: m_i = replicate_sides(256, seed 5)
 
 
 def oracle_curve(n: int, sides=CPU_CURVE_SIDES) -> dict:
@@ -199,6 +200,22 @@ def oracle_check(m: int, curve: dict) -> dict:
     dt = time.perf_counter() - t0
     pred = curve["a_n2"] * float(m * m) ** 2 + curve["b_n3"] * float(m * m) ** 3
     return {"n": m * m, "seconds": dt, "predicted_seconds": pred, "measured_over_predicted": dt / pred}
+
+
+def batched_oracle_estimate(curve: dict, nrep: int = None, seed: int = None) -> dict:
+    """Oracle time for one batch of the batched leg's replicates (n_i = m_i^2, m_i from
+    synth.replicate_sides), each replicate predicted by the fitted t = a n^2 + b n^3 law and summed.
+    The replicates' n_i = 400 ... 6,400 lie around the fitted range (1,600 ... 4,900)."""
+    from paper_1908_06936_gb300 import synth
+
+    nrep = BATCH_REPLICATES if nrep is None else nrep
+    seed = BATCH_SIDES_SEED if seed is None else seed
+    ns = [int(m) ** 2 for m in synth.replicate_sides(nrep, seed=seed)]
+    t = float(sum(curve["a_n2"] * n ** 2 + curve["b_n3"] * n ** 3 for n in ns))
+    return {"seconds_per_batch": t, "replicate_evals_per_s": nrep / t, "unit": "replicate-evals/s",
+            "cores": curve["threads"], "kind": "oracle",
+            "sample": "the oracle curve of cpu_baseline (t = a n^2 + b n^3) summed over the %d replicates "
+                      "(sum n_i = %d)" % (nrep, sum(ns))}
 
 
 def cpu_baseline_entry(n: int, curve: dict) -> dict:
@@ -288,8 +305,8 @@ def batched_leg(args, ctx) -> dict:
     import paper_1908_06936_gb300 as exa
     from paper_1908_06936_gb300 import synth
 
-    nrep = 256
-    sides = synth.replicate_sides(nrep, seed=5)
+    nrep = BATCH_REPLICATES
+    sides = synth.replicate_sides(nrep, seed=BATCH_SIDES_SEED)
     ns = [int(m) ** 2 for m in sides]
     dl = [torch.as_tensor(synth.jittered_grid(int(m), 1000 + r), device="cuda") for r, m in enumerate(sides)]
     dz = [torch.as_tensor(synth.normals(int(m) ** 2, 1000 + r), device="cuda") for r, m in enumerate(sides)]
@@ -778,6 +795,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "peaks_measured_here": probes,
             "cpu_baseline_check": oracle_check(args.oracle_check_m, curve) if args.oracle_check_m else None,
             "cpu_baseline": cpu_baseline_entry(n, curve),
+            "batched_cpu_baseline": batched_oracle_estimate(curve) if batched else None,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
     ctx.close()

@@ -31,3 +31,19 @@ def test_reference_arm_json_line():
     n = d["config"]["n"]
     assert abs(cv["a_n2"] * n ** 2 + cv["b_n3"] * n ** 3 - cv["seconds_at_n"]) <= 1e-9 * cv["seconds_at_n"]
     assert abs(d["ms_per_step"] / 1e3 - 1.0 / d["value"]) <= 1e-9 * d["ms_per_step"] / 1e3
+
+
+def test_batched_oracle_estimate_sums_the_law_over_the_batched_replicates():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1908_06936_gb300 import synth
+
+    curve = {"a_n2": 2.0e-9, "b_n3": 3.0e-12, "threads": 16}
+    est = bench.batched_oracle_estimate(curve)
+    sides = synth.replicate_sides(256, seed=5)  # the batched leg's replicates (m_i ~ U{20..80})
+    assert (bench.BATCH_REPLICATES, bench.BATCH_SIDES_SEED) == (256, 5)
+    want = sum(2.0e-9 * float(m) ** 4 + 3.0e-12 * float(m) ** 6 for m in sides)
+    assert abs(est["seconds_per_batch"] - want) <= 1e-12 * want
+    assert abs(est["replicate_evals_per_s"] - 256 / want) <= 1e-12 * 256 / want
+    assert est["kind"] == "oracle" and est["cores"] == 16 and "sum n_i = %d" % sum(int(m) ** 2 for m in sides) in est["sample"]
+    json.dumps(est)  # goes into the bench's JSON line
