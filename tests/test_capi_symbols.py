@@ -71,3 +71,64 @@ def test_binding_enums_match_the_header():
     assert prec == {"EXA_FP64": 0, "EXA_MIXED_FP32": 1, "EXA_MIXED_BF16X3": 2, "EXA_MIXED_TF32X3": 3}
     for k, v in list(prec.items()) + list(header_enum("exa_status").items()) + list(header_enum("exa_gemm_kind").items()):
         assert getattr(exa, k) == v, k
+
+
+def header_prototypes():
+    """{name: (return type, [parameter types])} of every function include/exa.h declares."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\b(exa_\w+)\s*\(([^;{)]*)\)\s*;", src):
+            ps = []
+            for p in params.split(","):
+                p = " ".join(p.split())
+                if not p or p == "void":
+                    continue
+                if "[" in p:  # an array parameter is a pointer
+                    ps.append("*")
+                    continue
+                ps.append(re.sub(r"\s*\b\w+$", "", p) if re.search(r"[\w\*]\s+\w+$|\*\s*\w+$", p) else p)
+            out[name] = (" ".join(ret.split()), ps)
+    return out
+
+
+def _c_kind(t):
+    """(kind, bytes) of a C type as the header spells it; kind is 'ptr', 'int', 'float' or None (void)."""
+    t = t.replace("const", "").strip()
+    if "*" in t:
+        return ("ptr", ctypes.sizeof(ctypes.c_void_p))
+    table = {"void": (None, 0), "int": ("int", 4), "int32_t": ("int", 4), "int64_t": ("int", 8),
+             "long long": ("int", 8), "size_t": ("int", 8), "double": ("float", 8), "float": ("float", 4),
+             "exa_status": ("int", 4), "exa_prec": ("int", 4), "exa_gemm_kind": ("int", 4)}
+    assert t in table, "type not mapped: %r" % t
+    return table[t]
+
+
+def _ctypes_kind(ct):
+    if ct is None:
+        return (None, 0)
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer):
+        return ("ptr", ctypes.sizeof(ctypes.c_void_p))
+    if ct in (ctypes.c_double, ctypes.c_float):
+        return ("float", ctypes.sizeof(ct))
+    return ("int", ctypes.sizeof(ct))
+
+
+def test_binding_signatures_match_the_header():
+    # every argument the binding marshals has the kind and width the prototype declares, in order,
+    # and the return types agree: a wrong width or a dropped argument would corrupt the call
+    import paper_1908_06936_gb300 as exa
+
+    L = exa.lib()
+    protos = header_prototypes()
+    assert len(protos) == len(declared_functions())
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        want = [_c_kind(p) for p in params]
+        got = [_ctypes_kind(a) for a in f.argtypes]
+        assert got == want, (name, params, f.argtypes)
+        assert _ctypes_kind(f.restype) == _c_kind(ret), (name, ret, f.restype)
