@@ -1,7 +1,9 @@
-"""The ctypes mirror of exa_result matches the C struct of include/exa.h field by field (size
-and offsets), checked by compiling a small C program against the header (CPU only)."""
+"""The ctypes mirrors of the structs include/exa.h passes across the boundary (exa_result,
+exa_kernel_stat, exa_timeline_rec) match the C structs field by field: names and order from the
+header's own definition, size and offsets from a small C program compiled against it (CPU only)."""
 import ctypes
 import os
+import re
 import shutil
 import subprocess
 
@@ -9,28 +11,39 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-FIELDS = ["loglik", "logdet", "quad", "ir_resid", "ir_iters", "tile_nb", "exact_band", "n_tiles", "ms_gen", "ms_chol",
-          "ms_solve", "ms_total", "quad_err"]
+
+def header_struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "exa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    return re.findall(r"\b(\w+)\s*(?:\[\d+\])?\s*;", body)
 
 
-def test_exa_result_layout(tmp_path):
+def _mirror(name):
+    import paper_1908_06936_gb300 as exa
+
+    return {"exa_result": exa.ExaResult, "exa_kernel_stat": exa.KernelStat, "exa_timeline_rec": exa.TimelineRec}[name]
+
+
+@pytest.mark.parametrize("name", ["exa_result", "exa_kernel_stat", "exa_timeline_rec"])
+def test_struct_layout(tmp_path, name):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    from paper_1908_06936_gb300 import ExaResult
-
+    mirror = _mirror(name)
+    fields = header_struct_fields(name)
+    assert [f for f, _ in mirror._fields_] == fields
     src = tmp_path / "layout.c"
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "exa.h"', "int main(void) {",
-             '  printf("size %zu\\n", sizeof(exa_result));']
-    for f in FIELDS:
-        lines.append('  printf("%s %%zu\\n", offsetof(exa_result, %s));' % (f, f))
+             '  printf("size %%zu\\n", sizeof(%s));' % name]
+    for f in fields:
+        lines.append('  printf("%s %%zu\\n", offsetof(%s, %s));' % (f, name, f))
     lines += ["  return 0;", "}"]
     src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "layout"
     subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
                                                    text=True).stdout.splitlines())
-    assert int(out["size"]) == ctypes.sizeof(ExaResult)
-    assert [f for f, _ in ExaResult._fields_] == FIELDS
-    for f in FIELDS:
-        assert int(out[f]) == getattr(ExaResult, f).offset, f
+    assert int(out["size"]) == ctypes.sizeof(mirror)
+    for f in fields:
+        assert int(out[f]) == getattr(mirror, f).offset, f
