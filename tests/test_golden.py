@@ -76,3 +76,22 @@ def test_oracle_matches_stored_gradient(data):
     r = oracle.loglik_grad(locs, Z, th)
     assert r["info"] == 0
     assert np.all(np.abs(r["grad"] - g) <= 1e-10 * np.max(np.abs(g))), (r["grad"], g)
+
+
+def test_oracle_is_bitwise_independent_of_the_thread_count(data):
+    """The oracle's OpenMP loops split only independent rows and columns, each computed in the serial order,
+    so one thread and many give the same bits (the stored values do not depend on the machine's core count)."""
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r); sys.path.insert(0, %r); import make_golden, oracle; "
+            "locs, Z = make_golden.workload(); r = oracle.loglik_grad(locs, Z, make_golden.THETA0); "
+            "print(oracle.max_threads(), *[float(v).hex() for v in (r['l'], r['logdet'], r['quad'], *r['grad'])])"
+            % (root, GOLDEN))
+    one = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                         capture_output=True, text=True, timeout=600, check=True).stdout.split()
+    assert one[0] == "1"
+    locs, Z = data
+    r = oracle.loglik_grad(locs, Z, make_golden.THETA0)
+    many = [float(v).hex() for v in (r["l"], r["logdet"], r["quad"], *r["grad"])]
+    assert one[1:] == many, (one, many, oracle.max_threads())
