@@ -50,7 +50,8 @@ extern "C" {
 
 typedef enum {
   EXA_OK = 0,
-  EXA_ERR_ARG = 1,        /* bad argument: n < 1, null pointer, theta <= 0 or non-finite, bad enum */
+  EXA_ERR_ARG = 1,        /* bad argument: n < 1, null pointer, theta <= 0 or non-finite, bad enum,
+                             z with a non-finite entry (single-field log-likelihood and gradient) */
   EXA_ERR_NOT_SPD = 2,    /* Cholesky pivot <= 0 or non-finite: Sigma(theta) not numerically SPD */
   EXA_ERR_NOMEM = 3,      /* workspace would exceed the context limit, or cudaMalloc failed */
   EXA_ERR_CUDA = 4,       /* a CUDA runtime or driver call failed */
@@ -181,7 +182,10 @@ exa_status exa_covariance(exa_ctx* ctx, const double* d_locs, int64_t n, const d
 exa_status exa_potrf(exa_ctx* ctx, double* d_a, int64_t n, int64_t ld);
 
 /* Steps a1-a5: log-likelihood l(theta) (Eq. 2) at host theta {sigma^2, beta, nu}.
- * *loglik (host) receives l, or NaN with EXA_ERR_NOT_SPD.                  */
+ * *loglik (host) receives l, or NaN with EXA_ERR_NOT_SPD.  A z holding a
+ * non-finite entry gives EXA_ERR_ARG with loglik = NaN; it is found from
+ * z^T Sigma^-1 z (FP64) or ||z||^2 (mixed, before any refinement step), at
+ * no extra pass over z.  z = 0 is valid: q = 0 exactly.                     */
 exa_status exa_loglik(exa_ctx* ctx, const double* d_locs, const double* d_z, const double theta[3], int64_t n,
                       exa_prec prec, double* loglik);
 
@@ -425,8 +429,8 @@ exa_status exa_probe_fp64_rate(void* cuda_stream, int kind, double* tflops);
  * call before any stream capture.  All calls on a device share the one array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  Returns EXA_ERR_NOT_SPD for a
- * non-positive pivot (no pivot index is kept) and EXA_ERR_CUDA if a CUDA call
- * fails.                                                                     */
+ * non-positive pivot (no pivot index is kept), EXA_ERR_ARG for a z holding a
+ * non-finite entry, and EXA_ERR_CUDA if a CUDA call fails.                   */
 exa_status exa_loglik_noalloc(void* cuda_stream, const double* d_locs, const double* d_z, const double theta[3],
                               int64_t n, double* loglik);
 

@@ -390,6 +390,9 @@ exa_status loglik_fp64(exa_ctx* c, const double* d_locs, const double* d_z, cons
   out->quad = quad;
   out->logdet = logdet;
   out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * logdet - 0.5 * quad;
+  // Sigma passed every pivot, so L^-1 is finite: a non-finite y^T y comes from z itself
+  if (!isfinite(quad))
+    return set_err(c, EXA_ERR_ARG, "z^T Sigma^-1 z = %g: z holds a non-finite entry (or its squares overflow)", quad);
   if (keep_y) *keep_y = y;
   return EXA_OK;
 }

@@ -556,7 +556,11 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_err(c, e, "refinement launch");
     if ((st = read_status(c)) != EXA_OK) return st;  // synchronises
-    rel = sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]);
+    if (!isfinite(c->h_scalars[2]))
+      return set_err(c, EXA_ERR_ARG, "||z||^2 = %g: z holds a non-finite entry (or its squares overflow)",
+                     c->h_scalars[2]);
+    // z = 0: x = 0 and q = 0 are exact, nothing to refine
+    rel = c->h_scalars[2] > 0.0 ? sqrt(c->h_scalars[3]) / sqrt(c->h_scalars[2]) : 0.0;
     rho = rel_prev > 0.0 ? rel / rel_prev : 1.0;
     rel_prev = rel;
     if (!(rel > (target > 0.0 ? target : 1e-15)) || it >= kMaxIt || rel > 0.5 * prev) break;
@@ -617,7 +621,8 @@ exa_status loglik_mixed(exa_ctx* c, const double* d_locs, const double* d_z, con
   out->quad = isnan(q_var) ? c->h_scalars[0] : q_var;
   // stopped on the residual (a caller's target, rounding level or stalling): x^T r, the first-order
   // term q lacks, measured against q
-  out->quad_err = !isnan(q_err) ? q_err : fabs(c->h_scalars[9]) / fabs(out->quad);
+  const double xr = fabs(c->h_scalars[9]);
+  out->quad_err = !isnan(q_err) ? q_err : (xr == 0.0 ? 0.0 : xr / fabs(out->quad));
   out->logdet = 2.0 * c->h_scalars[1];
   out->loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * out->logdet - 0.5 * out->quad;
   if (!q_done && !(rel <= kIrFailTol))

@@ -117,5 +117,6 @@ extern "C" exa_status exa_loglik_noalloc(void* cuda_stream, const double* d_locs
   if (hs.info) return EXA_ERR_NOT_SPD;
   const double logdet = 2.0 * h[1];
   *loglik = -0.5 * (double)n * 1.8378770664093454836 - 0.5 * logdet - 0.5 * h[0];
+  if (!isfinite(h[0])) return EXA_ERR_ARG;  // Sigma passed every pivot: z holds a non-finite entry
   return EXA_OK;
 }
