@@ -248,7 +248,9 @@ exa_status exa_ctx_set_gradient_inverse(exa_ctx* ctx, int fp64);
  *   d_theta   DEVICE array nrep x 3 (sigma^2, beta, nu per replicate), read at execution time,
  *             so a captured graph can be replayed with new parameters.
  *   d_loglik  DEVICE output, nrep values (NaN where the replicate's status is not EXA_OK).
- *   d_status  DEVICE output, nrep exa_status codes.
+ *   d_status  DEVICE output, nrep exa_status codes.  z is not inspected: a
+ *             replicate whose z holds a non-finite entry gets loglik = NaN
+ *             without a status of its own; z = 0 gives q = 0.
  * Stream-asynchronous: returns once the work is enqueued; device memory is
  * allocated on the first call for a shape set, so make that call before any
  * CUDA-graph capture, after which the sequence can be captured and replayed
