@@ -20,6 +20,16 @@
  * extensions of the same evaluation (the paper's optimiser, BOBYQA of Section
  * II-B, needs no derivatives).
  *
+ * The steps of an evaluation, by the names the sources use for them:
+ *   a1  covariance generation (Eq. 3);
+ *   a2  tiled Cholesky factorisation Sigma = L L^T;
+ *   a3  log|Sigma| = 2 sum log L_ii;
+ *   a4  y = L^-1 z and the quadratic form q = y^T y;
+ *   a5  assembly of l (Eq. 2);
+ *   a6  mixed precision: iterative refinement of Sigma^-1 z against the FP64 Sigma;
+ *   a7  the gradient of l with respect to theta;
+ *   a8  a1-a6 for many replicate fields in one batched launch.
+ *
  * Conventions for every entry point:
  *   - Pointers prefixed d_ are DEVICE pointers on the context's device; h_
  *     or unprefixed pointers are HOST pointers.  The caller owns all inputs
