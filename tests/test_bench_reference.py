@@ -47,3 +47,30 @@ def test_batched_oracle_estimate_sums_the_law_over_the_batched_replicates():
     assert abs(est["replicate_evals_per_s"] - 256 / want) <= 1e-12 * 256 / want
     assert est["kind"] == "oracle" and est["cores"] == 16 and "sum n_i = %d" % sum(int(m) ** 2 for m in sides) in est["sample"]
     json.dumps(est)  # goes into the bench's JSON line
+
+
+def test_roofline_by_kernel_covers_every_timed_class():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    pk = {"hbm_gbs": 6000.0, "bf16": 1800.0, "tf32": 880.0, "fp64": 1.0, "source": "measured"}
+    stats = [  # timed flops / bytes over event-timed ms, as exa_profile_read reports them
+        {"name": "gemm_tf32x3_pair", "launches": 4, "timed_launches": 4, "ms": 8.0, "flops": 2.2e12,
+         "bytes": 1e10, "timed_flops": 2.2e12, "timed_bytes": 1e10},
+        {"name": "split_rows", "launches": 10, "timed_launches": 5, "ms": 2.0, "flops": 0.0, "bytes": 6e9,
+         "timed_flops": 0.0, "timed_bytes": 3e9},
+        {"name": "symv_residual", "launches": 1, "timed_launches": 1, "ms": 4.0, "flops": 2e9, "bytes": 8e9,
+         "timed_flops": 2e9, "timed_bytes": 8e9},
+        {"name": "other", "launches": 2, "timed_launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 1e6,
+         "timed_flops": 0.0, "timed_bytes": 0.0},
+    ]
+    rows = bench.roofline_by_kernel(stats, pk)
+    assert [r["kernel"] for r in rows] == ["gemm_tf32x3_pair", "symv_residual", "split_rows"]  # untimed dropped
+    pair, symv, split = rows
+    assert pair["bound"] == "tensor" and abs(pair["achieved"] - 2.2e12 / 8e-3 / 1e12) < 1e-9
+    assert abs(pair["frac"] - pair["achieved"] / 880.0) < 1e-12
+    assert symv["bound"] == "alu" and abs(symv["achieved"] - 0.5) < 1e-12 and symv["unit"] == "TFLOP/s"
+    assert split["bound"] == "hbm" and abs(split["achieved"] - 3e9 / 2e-3 / 1e9) < 1e-9 and "look-ahead" in split["note"]
+    # the headline object is the dominant class's
+    assert bench.roofline(stats, pk) == bench.class_roofline(stats[0], pk)
+    json.dumps(rows)
