@@ -9,16 +9,70 @@ Example 2).  Two drivers are offered over the same bounds:
   gradient (exa_loglik_grad).
 
 Evaluations that are not SPD return l = -inf (the optimiser steps away).
+
+With ``history_path`` every evaluation is also appended to that file as one JSON
+line, so a fit that was interrupted restarts from the best theta recorded there.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 import time
 
 import numpy as np
 
 from . import EXA_FP64, Context, ExaError
 from .synth import THETA_LOWER, THETA_UPPER
+
+
+class EvalHistory:
+    """The (theta, l) of every evaluation of one fit, in order.  With a path, each evaluation is also
+    appended to that file as a JSON line {"theta": [...], "loglik": l} (null where l is not finite) and
+    flushed at once, so the record survives an interrupted run."""
+
+    def __init__(self, path: str | None = None):
+        self.rows: list = []
+        self.path = path
+
+    def append(self, row) -> None:
+        theta, l = row
+        self.rows.append((list(theta), l))
+        if self.path:
+            with open(self.path, "a") as f:
+                f.write(json.dumps({"theta": [float(v) for v in theta],
+                                    "loglik": float(l) if math.isfinite(l) else None}) + "\n")
+
+    def __len__(self) -> int:
+        return len(self.rows)
+
+
+def load_history(path: str) -> list:
+    """The (theta, l) rows of a history file, in order (l = -inf where none was recorded)."""
+    rows = []
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                if line.strip():
+                    d = json.loads(line)
+                    rows.append((d["theta"], -math.inf if d["loglik"] is None else float(d["loglik"])))
+    return rows
+
+
+def best_in_history(path: str):
+    """(theta, l) with the largest finite l in a history file, or None."""
+    rows = [r for r in load_history(path) if math.isfinite(r[1])]
+    return max(rows, key=lambda r: r[1]) if rows else None
+
+
+def _start(x0, history_path):
+    """The starting theta: x0 if given, else the best theta of an existing history, else the lower bounds."""
+    if x0 is not None:
+        return np.asarray(x0, dtype=np.float64), None
+    best = best_in_history(history_path) if history_path else None
+    if best is not None:
+        return np.asarray(best[0], dtype=np.float64), best[0]
+    return np.asarray(THETA_LOWER, dtype=np.float64), None
 
 
 def _objective(ctx, locs, z, prec, history):
@@ -37,12 +91,12 @@ def _objective(ctx, locs, z, prec, history):
 
 
 def fit_derivative_free(locs, z, x0=None, prec=EXA_FP64, method="Nelder-Mead", maxfev=100, ftol_abs=1e-4,
-                        ctx: Context | None = None) -> dict:
+                        ctx: Context | None = None, history_path: str | None = None) -> dict:
     from scipy.optimize import minimize
 
     c = ctx or Context()
-    hist: list = []
-    x0 = np.asarray(THETA_LOWER if x0 is None else x0, dtype=np.float64)
+    hist = EvalHistory(history_path)
+    x0, resumed = _start(x0, history_path)
     t0 = time.perf_counter()
     opts = {"maxfev": maxfev, "fatol": ftol_abs, "xatol": 1e-6} if method == "Nelder-Mead" else \
         {"maxfev": maxfev, "ftol": 1e-10}
@@ -52,10 +106,12 @@ def fit_derivative_free(locs, z, x0=None, prec=EXA_FP64, method="Nelder-Mead", m
     if ctx is None:
         c.close()
     return {"theta": np.clip(r.x, THETA_LOWER, THETA_UPPER).tolist(), "loglik": -r.fun, "evals": len(hist),
-            "seconds": dt, "time_per_eval": dt / max(1, len(hist)), "history": hist, "method": method}
+            "seconds": dt, "time_per_eval": dt / max(1, len(hist)), "history": hist.rows, "method": method,
+            "resumed_from": resumed}
 
 
-def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec=EXA_FP64) -> dict:
+def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec=EXA_FP64,
+                 history_path: str | None = None) -> dict:
     """L-BFGS-B with the library's analytic gradient, in u = log(theta) (the three parameters span
     orders of magnitude between the bounds; the chain rule gives dl/du = theta * dl/dtheta) on the
     objective -l / n.  Evaluations that are not SPD (or whose refinement stalls) return a large
@@ -63,7 +119,7 @@ def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec
     from scipy.optimize import minimize
 
     c = ctx or Context()
-    hist: list = []
+    hist = EvalHistory(history_path)
     n = float(locs.shape[0])
     lo, hi = np.log(THETA_LOWER), np.log(THETA_UPPER)
 
@@ -79,7 +135,7 @@ def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec
         hist.append((th.tolist(), l))
         return -l / n, -(th * np.asarray(g)) / n
 
-    x0 = np.asarray(THETA_LOWER if x0 is None else x0, dtype=np.float64)
+    x0, resumed = _start(x0, history_path)
     t0 = time.perf_counter()
     r = minimize(fg, np.log(x0), jac=True, method="L-BFGS-B", bounds=list(zip(lo, hi)),
                  options={"maxiter": maxiter})
@@ -88,8 +144,9 @@ def fit_gradient(locs, z, x0=None, maxiter=100, ctx: Context | None = None, prec
         c.close()
     th = np.exp(np.clip(r.x, lo, hi))
     return {"theta": th.tolist(), "loglik": -r.fun * n, "evals": len(hist), "seconds": dt,
-            "time_per_eval": dt / max(1, len(hist)), "history": hist,
-            "method": "L-BFGS-B in log(theta) + analytic gradient", "message": str(r.message)}
+            "time_per_eval": dt / max(1, len(hist)), "history": hist.rows,
+            "method": "L-BFGS-B in log(theta) + analytic gradient", "message": str(r.message),
+            "resumed_from": resumed}
 
 
 # ---------------------------------------------------------------------------

@@ -87,3 +87,58 @@ def test_oracle_fit_is_a_local_maximum():
             t = th.copy()
             t[k] = min(max(t[k] * f, lo[k]), hi[k])
             assert oracle.loglik(locs, z, t)["l"] <= l0 + 1e-9
+
+
+class _OracleCtx:
+    """Stands in for a library context in the single-field drivers: the same calls, answered by the oracle."""
+
+    def loglik(self, locs, z, theta, prec=0):
+        import paper_1908_06936_gb300 as exa
+
+        r = oracle.loglik(locs, z, theta)
+        if r["info"] != 0:
+            raise exa.ExaError(exa.EXA_ERR_NOT_SPD, "not SPD")
+        return r["l"]
+
+    def loglik_grad(self, locs, z, theta, prec=0):
+        r = oracle.loglik_grad(locs, z, theta)
+        return r["l"], np.asarray(r["grad"])
+
+
+@pytest.mark.parametrize("driver", ["derivative_free", "gradient"])
+def test_history_file_records_every_evaluation_and_resumes_from_its_best(tmp_path, driver):
+    from paper_1908_06936_gb300 import mle
+
+    locs = synth.jittered_grid(8, seed=3)
+    z = oracle.simulate(locs, (1.0, 0.1, 0.5), synth.normals(64, 3))
+    path = str(tmp_path / "fit.jsonl")
+    if driver == "derivative_free":
+        fit = lambda: mle.fit_derivative_free(locs, z, maxfev=25, ctx=_OracleCtx(), history_path=path)
+    else:
+        fit = lambda: mle.fit_gradient(locs, z, maxiter=4, ctx=_OracleCtx(), history_path=path)
+    a = fit()
+    assert a["resumed_from"] is None
+    rows = mle.load_history(path)
+    assert len(rows) == a["evals"] == len(a["history"]) > 0
+    for (th_f, l_f), (th_m, l_m) in zip(rows, a["history"]):
+        assert np.allclose(th_f, th_m, rtol=0, atol=0) and (l_f == l_m or (math.isinf(l_f) and math.isinf(l_m)))
+    best = mle.best_in_history(path)
+    assert best[1] == max(l for _, l in rows if math.isfinite(l))
+    # a second run on the same file starts from that best theta and appends its own evaluations
+    b = fit()
+    assert b["resumed_from"] == best[0]
+    assert np.allclose(b["history"][0][0], best[0], rtol=1e-12, atol=0)
+    assert len(mle.load_history(path)) == a["evals"] + b["evals"]
+    assert b["loglik"] >= best[1] - 1e-9
+
+
+def test_history_keeps_non_finite_evaluations(tmp_path):
+    from paper_1908_06936_gb300 import mle
+
+    path = str(tmp_path / "h.jsonl")
+    h = mle.EvalHistory(path)
+    h.append(([1.0, 0.1, 0.5], -12.5))
+    h.append(([2.0, 0.3, 1.0], -math.inf))
+    assert mle.load_history(path) == [([1.0, 0.1, 0.5], -12.5), ([2.0, 0.3, 1.0], -math.inf)]
+    assert mle.best_in_history(path) == ([1.0, 0.1, 0.5], -12.5)
+    assert mle.best_in_history(str(tmp_path / "absent.jsonl")) is None
