@@ -21,6 +21,7 @@ __all__ = [
     "exa_workspace_bytes", "exa_covariance", "exa_potrf", "exa_loglik", "exa_loglik_ex", "exa_loglik_grad",
     "exa_loglik_batched", "exa_simulate", "ExaResult", "PREC", "exa_gemm_update", "exa_ctx_set_mixed_band", "exa_ctx_set_lookahead", "exa_ctx_set_panel_fusion", "exa_ctx_set_lookahead_late", "exa_ctx_set_refinement", "exa_ctx_set_refinement_quad", "exa_profile_enable",
     "exa_profile_read", "KernelStat", "exa_profile_timeline_enable", "exa_profile_timeline", "TimelineRec", "exa_ctx_set_batched", "exa_ctx_set_batched_mixed", "exa_batched_autotune", "exa_loglik_noalloc", "EXA_GEMM_T3", "EXA_GEMM_OZ", "EXA_GEMM_T3_PAIR", "exa_ctx_set_tc_pairs", "exa_ctx_set_far_tile_margin", "exa_ctx_set_gradient_inverse", "exa_probe_fp64_rate", "exa_predict", "exa_fisher", "exa_ctx_set_model",
+    "default_prec", "default_tile",
 ]
 
 EXA_OK, EXA_ERR_ARG, EXA_ERR_NOT_SPD, EXA_ERR_NOMEM, EXA_ERR_CUDA, EXA_ERR_TIMEOUT, EXA_ERR_IR_NOCONV = range(7)
@@ -149,16 +150,46 @@ def _dev_ptr(t, name: str, n_expected: int | None = None) -> int:
     return t.data_ptr()
 
 
-class Context:
-    """Owns an exa_ctx bound to a CUDA stream (default: torch's current stream)."""
+def default_prec() -> int:
+    """Precision of a Context evaluation whose caller names none: the environment variable EXA_PREC
+    (fp64, tf32x3, bf16x3 or fp32, or the numeric code), else EXA_FP64."""
+    v = os.environ.get("EXA_PREC", "").strip().lower()
+    if not v:
+        return EXA_FP64
+    if v in PREC:
+        return PREC[v]
+    if v.isdigit() and int(v) in PREC.values():
+        return int(v)
+    raise ValueError("EXA_PREC=%r: expected one of %s or its code" % (v, ", ".join(sorted(PREC))))
 
-    def __init__(self, stream=None, workspace_bytes: int = 0, tile_nb: int = 0):
+
+def default_tile() -> int:
+    """FP64 tile of a new Context whose caller names none: the environment variable EXA_TILE (64 or 128),
+    else 0 (the library's default)."""
+    v = os.environ.get("EXA_TILE", "").strip()
+    if not v:
+        return 0
+    if v not in ("64", "128"):
+        raise ValueError("EXA_TILE=%r: expected 64 or 128" % v)
+    return int(v)
+
+
+def _prec(prec) -> int:
+    return default_prec() if prec is None else prec
+
+
+class Context:
+    """Owns an exa_ctx bound to a CUDA stream (default: torch's current stream).  tile_nb=None takes
+    EXA_TILE from the environment (else the library default); an evaluation with prec=None takes
+    EXA_PREC (else EXA_FP64)."""
+
+    def __init__(self, stream=None, workspace_bytes: int = 0, tile_nb: int | None = None):
         import torch
 
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
-        self.handle = exa_ctx_create(stream.cuda_stream, workspace_bytes, tile_nb)
+        self.handle = exa_ctx_create(stream.cuda_stream, workspace_bytes, default_tile() if tile_nb is None else tile_nb)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -189,21 +220,21 @@ class Context:
         self.check(exa_covariance(self.handle, locs, n, theta, out, n))
         return out
 
-    def loglik(self, locs, z, theta, prec=EXA_FP64) -> float:
+    def loglik(self, locs, z, theta, prec=None) -> float:
         return self.loglik_ex(locs, z, theta, prec)["loglik"]
 
-    def loglik_ex(self, locs, z, theta, prec=EXA_FP64) -> dict:
+    def loglik_ex(self, locs, z, theta, prec=None) -> dict:
         r = ExaResult()
-        st = exa_loglik_ex(self.handle, locs, z, theta, locs.shape[0], prec, r)
+        st = exa_loglik_ex(self.handle, locs, z, theta, locs.shape[0], _prec(prec), r)
         d = r.as_dict()
         d["status"] = st
         self.check(st)
         return d
 
-    def loglik_grad(self, locs, z, theta, prec=EXA_FP64):
+    def loglik_grad(self, locs, z, theta, prec=None):
         g = (ctypes.c_double * 3)()
         l = ctypes.c_double()
-        self.check(exa_loglik_grad(self.handle, locs, z, theta, locs.shape[0], prec, l, g))
+        self.check(exa_loglik_grad(self.handle, locs, z, theta, locs.shape[0], _prec(prec), l, g))
         return l.value, np.array(g[:])
 
     def predict(self, locs, z, theta, new_locs, variance=True):
@@ -222,11 +253,11 @@ class Context:
         self.check(exa_fisher(self.handle, locs, theta, locs.shape[0], out))
         return np.array(out[:]).reshape(3, 3)
 
-    def simulate(self, locs, eps, theta, prec=EXA_FP64):
+    def simulate(self, locs, eps, theta, prec=None):
         import torch
 
         z = torch.empty_like(eps)
-        self.check(exa_simulate(self.handle, locs, eps, theta, locs.shape[0], prec, z))
+        self.check(exa_simulate(self.handle, locs, eps, theta, locs.shape[0], _prec(prec), z))
         return z
 
 

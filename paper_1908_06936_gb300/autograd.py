@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import torch
 
-from . import EXA_FP64, Context
+from . import Context
 
 
 class MaternLogLik(torch.autograd.Function):
@@ -34,8 +34,9 @@ class MaternLogLik(torch.autograd.Function):
 
 
 def loglik(theta: torch.Tensor, locs: torch.Tensor, z: torch.Tensor, ctx: Context | None = None,
-           prec: int = EXA_FP64) -> torch.Tensor:
-    """l(theta) as a differentiable scalar tensor (theta: 3 float64 values)."""
+           prec: int | None = None) -> torch.Tensor:
+    """l(theta) as a differentiable scalar tensor (theta: 3 float64 values).  prec=None: the context's
+    default (EXA_PREC from the environment, else EXA_FP64)."""
     own = ctx is None
     c = Context() if own else ctx
     try:

@@ -15,6 +15,12 @@ import os
 import paper_1908_06936_gb300 as exa
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1908_06936_gb300", "batched_tiles.json")
+_FROM_ENV = object()
+
+
+def default_cache_path() -> str:
+    """The cache file when the caller names none: EXA_AUTOTUNE_CACHE from the environment, else DEFAULT_CACHE."""
+    return os.environ.get("EXA_AUTOTUNE_CACHE", "").strip() or DEFAULT_CACHE
 
 
 def workload_key(device_name: str, prec: int, band: int, ns) -> str:
@@ -32,13 +38,16 @@ def _load(path: str) -> dict:
 
 
 def autotune_batched(ctx, ns, locs_list, z_list, theta_dev, prec: int, loglik_dev, status_dev, band: int = 0,
-                     cache_path: str | None = DEFAULT_CACHE) -> dict:
+                     cache_path=_FROM_ENV) -> dict:
     """Pick the batched tile configuration for this workload and apply it to ``ctx``.
 
     Returns {"tile_nb", "ctas_per_sm", "ms", "cached"}.  ``band`` must match the value
     given to ``exa_ctx_set_batched_mixed`` (it selects the kernel variant).  With
-    ``cache_path=None`` nothing is read or written."""
+    ``cache_path=None`` nothing is read or written; without it the file is default_cache_path()."""
     import torch
+
+    if cache_path is _FROM_ENV:
+        cache_path = default_cache_path()
 
     key = workload_key(torch.cuda.get_device_name(), prec, band, ns)
     db = _load(cache_path) if cache_path else {}
