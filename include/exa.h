@@ -61,7 +61,7 @@ extern "C" {
 typedef enum {
   EXA_OK = 0,
   EXA_ERR_ARG = 1,        /* bad argument: n < 1, null pointer, theta <= 0 or non-finite, bad enum,
-                             z with a non-finite entry (single-field log-likelihood and gradient) */
+                             z with a non-finite entry (single-field log-likelihood, gradient, prediction) */
   EXA_ERR_NOT_SPD = 2,    /* Cholesky pivot <= 0 or non-finite: Sigma(theta) not numerically SPD */
   EXA_ERR_NOMEM = 3,      /* workspace would exceed the context limit, or cudaMalloc failed */
   EXA_ERR_CUDA = 4,       /* a CUDA runtime or driver call failed */
