@@ -50,6 +50,18 @@ def test_matern_small_distance_limit(nu):
     assert rel(oracle.matern(th, 1e-9), 2.5) < 1e-6
 
 
+@pytest.mark.parametrize("nu", NUS)
+def test_matern_decreasing_and_within_sigma2(nu):
+    # d/dx [x^nu K_nu(x)] = -x^nu K_{nu-1}(x) < 0 (DLMF 10.29.4) and x^nu K_nu(x) -> 2^(nu-1) Gamma(nu)
+    # as x -> 0: Eq. 3 falls strictly from sigma^2 towards 0 as the distance grows
+    th = [1.7, 0.2, nu]
+    r = np.geomspace(1e-6, 12.0, 400)  # x = r / beta from 5e-6 to 60
+    v = np.array([oracle.matern(th, float(t)) for t in r])
+    assert np.all(v > 0.0) and np.all(v <= 1.7 * (1 + 1e-15))
+    assert np.all(np.diff(v) < 0.0)
+    assert oracle.matern(th, 0.0) == 1.7
+
+
 def test_besselk_vs_mpmath():
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
